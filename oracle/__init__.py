@@ -1,0 +1,23 @@
+"""Plain FP64 CPU oracle for the IIM Poisson solver (test infrastructure only).
+
+This package is the reference the CUDA path is checked against.  It is slow
+on purpose: numpy for vector work, LAPACK QR / dense solves as library steps,
+Python loops over control points.  It shares no code with the CUDA library
+and must never be imported by the product path; only ``tests/``, the smoke
+check and the bench's CPU-baseline leg use it.
+
+Layout
+  geometry.py  level sets, grid-line crossings, normals, curvature   (Sec. 2.1)
+  stencils.py  centred second-derivative coefficients, sigma_max     (Sec. 2.5, Tab. 1)
+  fits.py      least-squares interpolants, ghost / Neumann / jump rows (Sec. 2.1-2.2)
+  operator.py  the (n,k) IIM operator L_Omega and data term           (Sec. 2.3, Eq. 7)
+  sw.py        Shortley-Weller operators and 1D formulas              (Sec. 3.1, Eqs. 12-15)
+  mg.py        geometric multigrid V-cycle                           (Sec. 3.3)
+  fgmres.py    right-preconditioned flexible GMRES(m)                (Sec. 4.1)
+  problem.py   glue: build everything for one problem, solve it
+
+Parity-unpinned readings (no printed value pins them; only the invariants in
+tests/ do): the half-ellipse semi-axes of the least-squares region, the
+cell-centred restriction/prolongation weights, the outer-box closure, the
+coarsest-grid size rule.
+"""

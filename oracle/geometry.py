@@ -1,0 +1,217 @@
+"""Geometry for the oracle: level set phi, crossings, normals, curvature.
+
+Paper Sec. 2.1: a *control point* x_c is the intersection of a 1D stencil
+(a grid line) with the surface Gamma; the surface must satisfy the curvature
+condition |kappa dx| < 1/4 (Eq. 3), kappa being the largest principal
+curvature.
+
+Conventions (paper Eqs. 1, 5): Omega+ = {phi >= 0}; the normal n points out of
+Omega+ towards Omega-, so n = -grad(phi)/|grad(phi)|.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from workloads import CIRCLE, ELLIPSE, STAR, SPHERE, ELLIPSOID
+
+
+class LevelSet:
+    """phi(x) for an analytic body; ``g`` is negative inside the body."""
+
+    def __init__(self, geometry):
+        self.geom = geometry
+        self.kind = geometry.kind
+        self.p = tuple(float(v) for v in geometry.params)
+        self.sign = -1.0 if geometry.plus_inside else 1.0   # phi = sign * g
+        self.dim = geometry.dim
+
+    # body function g and its gradient / Hessian -------------------------------------
+    def g(self, X):
+        p = self.p
+        if self.kind == CIRCLE:
+            return np.hypot(X[..., 0] - p[0], X[..., 1] - p[1]) - p[2]
+        if self.kind == SPHERE:
+            d = X - np.array(p[:3])
+            return np.sqrt(np.sum(d * d, axis=-1)) - p[3]
+        if self.kind == ELLIPSE:
+            y = self._ellipse_local(X)
+            return (y[..., 0] / p[2]) ** 2 + (y[..., 1] / p[3]) ** 2 - 1.0
+        if self.kind == ELLIPSOID:
+            d = X - np.array(p[:3])
+            return np.sum((d / np.array(p[3:6])) ** 2, axis=-1) - 1.0
+        if self.kind == STAR:
+            dx, dy = X[..., 0] - p[0], X[..., 1] - p[1]
+            rho = np.hypot(dx, dy)
+            th = np.arctan2(dy, dx)
+            return rho - (p[2] + p[3] * np.sin(p[4] * th + p[5]))
+        raise ValueError("unknown geometry kind")
+
+    def phi(self, X):
+        return self.sign * self.g(X)
+
+    def grad_g(self, X):
+        p = self.p
+        if self.kind in (CIRCLE, SPHERE):
+            c = np.array(p[:self.dim])
+            d = X - c
+            return d / np.sqrt(np.sum(d * d, axis=-1))[..., None]
+        if self.kind == ELLIPSE:
+            y = self._ellipse_local(X)
+            gy = np.stack([2 * y[..., 0] / p[2] ** 2, 2 * y[..., 1] / p[3] ** 2], axis=-1)
+            c, s = math.cos(p[4]), math.sin(p[4])
+            # x = c0 + R y with R = [[c,-s],[s,c]]  ->  grad_x = R grad_y
+            return np.stack([c * gy[..., 0] - s * gy[..., 1], s * gy[..., 0] + c * gy[..., 1]], axis=-1)
+        if self.kind == ELLIPSOID:
+            d = X - np.array(p[:3])
+            return 2 * d / np.array(p[3:6]) ** 2
+        if self.kind == STAR:
+            dx, dy = X[..., 0] - p[0], X[..., 1] - p[1]
+            rho = np.hypot(dx, dy)
+            th = np.arctan2(dy, dx)
+            rp = p[3] * p[4] * np.cos(p[4] * th + p[5])          # r'(theta)
+            er = np.stack([dx / rho, dy / rho], axis=-1)
+            et = np.stack([-dy / rho, dx / rho], axis=-1)
+            return er - (rp / rho)[..., None] * et
+        raise ValueError
+
+    def normal(self, X):
+        """Unit normal pointing out of Omega+ (towards Omega-)."""
+        gphi = self.sign * self.grad_g(X)
+        return -gphi / np.linalg.norm(gphi, axis=-1, keepdims=True)
+
+    def curvature(self, X):
+        """Largest |principal curvature| of the level surface through X."""
+        p = self.p
+        if self.kind == CIRCLE:
+            return np.full(X.shape[:-1], 1.0 / p[2])
+        if self.kind == SPHERE:
+            return np.full(X.shape[:-1], 1.0 / p[3])
+        if self.kind == STAR:
+            dx, dy = X[..., 0] - p[0], X[..., 1] - p[1]
+            th = np.arctan2(dy, dx)
+            r = p[2] + p[3] * np.sin(p[4] * th + p[5])
+            r1 = p[3] * p[4] * np.cos(p[4] * th + p[5])
+            r2 = -p[3] * p[4] ** 2 * np.sin(p[4] * th + p[5])
+            # curvature of the polar curve r(theta)
+            return np.abs(r * r + 2 * r1 * r1 - r * r2) / (r * r + r1 * r1) ** 1.5
+        # quadrics: shape operator P H P / |grad g| on the tangent space
+        if self.kind == ELLIPSE:
+            c, s = math.cos(p[4]), math.sin(p[4])
+            R = np.array([[c, -s], [s, c]])
+            H = R @ np.diag([2 / p[2] ** 2, 2 / p[3] ** 2]) @ R.T
+        else:
+            H = np.diag(2 / np.array(p[3:6]) ** 2)
+        G = self.grad_g(X)
+        gn = np.linalg.norm(G, axis=-1)
+        n = G / gn[..., None]
+        out = np.zeros(X.shape[:-1])
+        flat_n = n.reshape(-1, self.dim)
+        flat_g = gn.reshape(-1)
+        res = out.reshape(-1)
+        for k in range(flat_n.shape[0]):
+            P = np.eye(self.dim) - np.outer(flat_n[k], flat_n[k])
+            S = P @ H @ P / flat_g[k]
+            res[k] = np.max(np.abs(np.linalg.eigvalsh(S)))
+        return res.reshape(X.shape[:-1])
+
+    def _ellipse_local(self, X):
+        p = self.p
+        c, s = math.cos(p[4]), math.sin(p[4])
+        dx, dy = X[..., 0] - p[0], X[..., 1] - p[1]
+        return np.stack([c * dx + s * dy, -s * dx + c * dy], axis=-1)
+
+
+def grid_x(n):
+    """Cell-centred node coordinates along one axis of [-1,1]: -1 + (i+1/2) h."""
+    h = 2.0 / n
+    return -1.0 + (np.arange(n) + 0.5) * h
+
+
+def phase_plus(ls: LevelSet, n: int) -> np.ndarray:
+    """Boolean grid, True on Omega+ = {phi >= 0} (a node with phi == 0 is in Omega+)."""
+    x = grid_x(n)
+    X = np.stack(np.meshgrid(*([x] * ls.dim), indexing="ij"), axis=-1)
+    return ls.phi(X) >= 0.0
+
+
+class Crossings:
+    """Control points: one per axis-aligned grid edge whose end nodes differ in phase.
+
+    Canonical order: by axis, then by the flat index (i0 fastest) of the lower
+    node of the edge.  Fields (K = number of crossings):
+      axis[K], lo[K] (flat index of the lower node), t[K] (fraction of h from
+      the lower node), x[K,d], normal[K,d] (out of Omega+), kappa[K],
+      lo_plus[K] (True if the lower node is in Omega+).
+    """
+
+    def __init__(self, ls: LevelSet, n: int, plus: np.ndarray):
+        d = ls.dim
+        h = 2.0 / n
+        x = grid_x(n)
+        axes, los, ts, lo_plus = [], [], [], []
+        for ax in range(d):
+            sl_lo = [slice(None)] * d
+            sl_hi = [slice(None)] * d
+            sl_lo[ax] = slice(0, n - 1)
+            sl_hi[ax] = slice(1, n)
+            a, b = plus[tuple(sl_lo)], plus[tuple(sl_hi)]
+            cut = a != b
+            idx = np.argwhere(cut)                   # lower-node multi-indices, C order
+            if idx.size == 0:
+                continue
+            flat = np.zeros(idx.shape[0], dtype=np.int64)
+            for k in range(d):
+                flat += idx[:, k] * n ** k
+            order = np.argsort(flat, kind="stable")
+            idx, flat = idx[order], flat[order]
+            P0 = x[idx]                              # lower node coordinates
+            t = self._bisect(ls, P0, ax, h)
+            axes.append(np.full(idx.shape[0], ax))
+            los.append(flat)
+            ts.append(t)
+            lo_plus.append(a[tuple(idx.T)])
+        if axes:
+            self.axis = np.concatenate(axes)
+            self.lo = np.concatenate(los)
+            self.t = np.concatenate(ts)
+            self.lo_plus = np.concatenate(lo_plus)
+        else:
+            self.axis = np.zeros(0, dtype=np.int64)
+            self.lo = np.zeros(0, dtype=np.int64)
+            self.t = np.zeros(0)
+            self.lo_plus = np.zeros(0, dtype=bool)
+        K = self.axis.size
+        self.n, self.dim, self.h = n, d, h
+        self.count = K
+        self.lo_idx = np.stack(np.unravel_index(self.lo, (n,) * d, order="F"), axis=-1) if K else np.zeros((0, d), dtype=np.int64)
+        X = x[self.lo_idx].astype(float) if K else np.zeros((0, d))
+        if K:
+            X[np.arange(K), self.axis] += self.t * h
+        self.x = X
+        self.normal = ls.normal(X) if K else np.zeros((0, d))
+        self.kappa = ls.curvature(X) if K else np.zeros(0)
+        # lookup: (axis, lower flat index) -> crossing id
+        self.lookup = {(int(a), int(l)): k for k, (a, l) in enumerate(zip(self.axis, self.lo))}
+
+    @staticmethod
+    def _bisect(ls, P0, ax, h):
+        """Root of phi on each edge [P0, P0 + h e_ax] by bisection (60 halvings)."""
+        lo = np.zeros(P0.shape[0])
+        hi = np.ones(P0.shape[0])
+
+        def f(t):
+            X = P0.astype(float).copy()
+            X[:, ax] += t * h
+            return ls.phi(X)
+
+        f_lo = f(lo)
+        s_lo = f_lo >= 0.0
+        for _ in range(60):
+            mid = 0.5 * (lo + hi)
+            s_mid = f(mid) >= 0.0
+            same = s_mid == s_lo
+            lo = np.where(same, mid, lo)
+            hi = np.where(same, hi, mid)
+        return 0.5 * (lo + hi)

@@ -1,0 +1,57 @@
+"""One IIM Poisson problem end to end in the oracle: operator, data, MG, FGMRES."""
+from __future__ import annotations
+
+import numpy as np
+
+import workloads as W
+from .fgmres import fgmres
+from .mg import Multigrid
+from .operator import IIMOperator
+
+
+class OracleProblem:
+    def __init__(self, spec, nu1=2, nu2=2, check_curvature=True):
+        self.spec = spec
+        self.op = IIMOperator(spec, check_curvature=check_curvature)
+        self.n, self.d = spec.n, spec.dim
+        self.plus_flat = self.op.plus.ravel(order="F")
+        self.unk_flat = self.op.unknown.ravel(order="F")
+        self._mg = None
+        self.nu1, self.nu2 = nu1, nu2
+
+    @property
+    def mg(self):
+        if self._mg is None:
+            s = self.spec
+            self._mg = Multigrid(self.op.ls, s.n, s.bc, s.box_bc, s.beta_plus, s.beta_minus, self.nu1, self.nu2)
+        return self._mg
+
+    def data(self, spec=None):
+        """Manufactured data at this oracle's own control points and box points."""
+        spec = spec or self.spec
+        xc, nc = self.op.control_points()
+        g, j0, j1 = W.boundary_data(spec, xc, nc)
+        X = W.node_coords(spec.n, spec.dim)
+        f = W.to_flat(W.source_term(spec, X, self.op.plus))
+        return f, {"g": g, "j0": j0, "j1": j1, "box": W.box_data(spec)}
+
+    def exact(self, spec=None):
+        spec = spec or self.spec
+        X = W.node_coords(spec.n, spec.dim)
+        up = spec.solution.u_plus(X)
+        if spec.bc == W.INTERFACE:
+            u = np.where(self.op.plus, up, spec.solution.u_minus(X))
+        else:
+            u = np.where(self.op.plus, up, 0.0)
+        return W.to_flat(u)
+
+    def apply(self, u):
+        return self.op.apply(u)
+
+    def precondition(self, v):
+        return self.mg.precondition(v, self.plus_flat)
+
+    def solve(self, f, data, tol=1e-13, restart=10, max_iter=1000):
+        b = self.op.rhs(f, data)
+        x, info = fgmres(self.op.apply, self.precondition, b, tol=tol, restart=restart, max_iter=max_iter)
+        return x, info, b
