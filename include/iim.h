@@ -1,0 +1,181 @@
+/*
+ * iim.h -- C ABI of the GB300 immersed-interface Poisson solver.
+ *
+ * Solves  div(beta grad u) = f  on a uniform cell-centred grid of [-1,1]^d
+ * (d = 2 or 3, n cells per axis, h = 2/n, node i at -1 + (i + 1/2) h) with an
+ * immersed boundary or interface Gamma = {phi = 0} (Gabbard, Paris & van Rees,
+ * "A high order multigrid-preconditioned immersed interface solver for the
+ * Poisson equation with boundary and interface conditions", JCP 2025):
+ *   Sec. 2.1, Eq. 1   boundary problems on Omega+ = {phi >= 0}:
+ *                     u = ubar (Dirichlet) or beta+ du/dn = qbar (Neumann) on Gamma,
+ *   Sec. 2.2, Eq. 8   interface problems: [u] = j0, [beta du/dn] = j1 on Gamma,
+ * with n pointing out of Omega+ (towards Omega-) and [a] = a(+) - a(-).
+ * The discretisation is the (n, n+1) IIM operator of Sec. 2.3 (Eq. 12): a 4th
+ * or 6th order centred stencil with ghost values from least-squares
+ * polynomials fitted at every control point (Eqs. 4-11).  The linear system
+ * is solved by right-preconditioned FGMRES(m) (Sec. 4.1) with one
+ * Shortley-Weller multigrid V-cycle as preconditioner (Sec. 3.1, 3.3).
+ * An optional Dirichlet outer box closes the domain at the faces x_k = +-1.
+ *
+ * Memory and ownership
+ *   Every pointer named *_dev is device memory owned by the caller and only
+ *   borrowed for the duration of the call (asynchronous calls: until the work
+ *   enqueued on the problem's stream has finished).  Every *_host pointer is
+ *   host memory, borrowed likewise.  A problem owns its device workspace; it is
+ *   allocated by iim_problem_create and released by iim_problem_destroy.
+ *   Grid vectors are FP64, n^d entries, x0 fastest (flat index
+ *   i0 + n i1 + n^2 i2).  Entries at nodes that are not unknowns (nodes of
+ *   Omega- for boundary problems) are ignored on input and written as 0.
+ *
+ * Errors
+ *   Every call returns an iim_status and never aborts; iim_last_error() gives
+ *   a message for the calling thread.  Device-side failures (rank-deficient
+ *   fits, NaN in the Krylov recurrence, ...) are recorded in a status word on
+ *   the device and reported by the next call that synchronises
+ *   (iim_problem_create, iim_problem_setup_sync, iim_solve, iim_status_get).
+ */
+#ifndef IIM_H
+#define IIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IIM_OK = 0,
+  IIM_ERR_INVALID_ARG = 1,   /* bad descriptor, option or pointer */
+  IIM_ERR_CURVATURE = 2,     /* |kappa h| >= 1/4 at a control point (Sec. 2.1, Eq. 3) */
+  IIM_ERR_RANK = 3,          /* least-squares fit rank deficient after growing its region */
+  IIM_ERR_SINGULAR = 4,      /* Neumann s_c ~ 0 (Eq. 6) or interface denominator ~ 0 (Eq. 11) */
+  IIM_ERR_NOT_CONVERGED = 5, /* FGMRES reached max_iter above tol */
+  IIM_ERR_BREAKDOWN = 6,     /* NaN/Inf in the Krylov recurrence */
+  IIM_ERR_BUDGET = 7,        /* device memory budget exceeded */
+  IIM_ERR_TIMEOUT = 8,       /* a bounded device wait ran out */
+  IIM_ERR_CUDA = 9,          /* CUDA runtime error */
+  IIM_ERR_GEOMETRY = 10,     /* body too close to the outer box, or box missing */
+  IIM_ERR_CAPACITY = 11      /* re-setup needs more workspace than allocated */
+} iim_status;
+
+enum { IIM_GEOM_CIRCLE = 0, IIM_GEOM_ELLIPSE = 1, IIM_GEOM_STAR = 2, IIM_GEOM_SPHERE = 3, IIM_GEOM_ELLIPSOID = 4 };
+enum { IIM_BC_DIRICHLET = 0, IIM_BC_NEUMANN = 1, IIM_BC_INTERFACE = 2 };
+enum { IIM_BOX_NONE = 0, IIM_BOX_DIRICHLET = 1 };
+enum { IIM_MG_FP32 = 0, IIM_MG_FP64 = 1 };
+
+/* Problem statement (paper Sec. 2.1-2.2).
+ * geom_params by kind (phi = -g if plus_inside else g, g < 0 inside the body):
+ *   CIRCLE    cx cy R                 g = |x - c| - R
+ *   ELLIPSE   cx cy a0 a1 angle       g = (y0/a0)^2 + (y1/a1)^2 - 1, y = Rot(-angle)(x - c)
+ *   STAR      cx cy r0 amp m phase    g = |x - c| - (r0 + amp sin(m theta + phase))
+ *   SPHERE    cx cy cz R
+ *   ELLIPSOID cx cy cz a0 a1 a2       axis aligned
+ */
+typedef struct {
+  int dim;               /* 2 or 3 */
+  int n;                 /* cells per axis */
+  int geom_kind;
+  int plus_inside;       /* 1: Omega+ is the inside of the body */
+  double geom_params[8];
+  int bc;                /* IIM_BC_* */
+  int box_bc;            /* IIM_BOX_*; interface problems need IIM_BOX_DIRICHLET */
+  double beta_plus, beta_minus;
+  int order;             /* 4 -> (4,5) scheme, 6 -> (6,7) scheme (Sec. 2.4) */
+} iim_problem_desc;
+
+typedef struct {
+  double tol;            /* true relative residual |b - A x| / |b| (Sec. 4.3: 1e-10) */
+  int restart;           /* FGMRES restart m (Sec. 4.1: 10), 1..16 */
+  int max_iter;          /* total FGMRES iterations */
+  int nu1, nu2;          /* pre/post red-black Gauss-Seidel sweeps */
+  int mg_precision;      /* IIM_MG_FP32 or IIM_MG_FP64 */
+  int use_graph;         /* 1: the solve runs as one CUDA graph with device-side control */
+  int reorth;            /* 1: second Gram-Schmidt pass when |w| drops by more than 1/sqrt(2) */
+} iim_options;
+
+typedef struct {
+  int status;            /* iim_status of the solve */
+  int iters;             /* FGMRES iterations */
+  int restarts;          /* completed restart cycles */
+  int converged;
+  double relres;         /* final true relative residual */
+  double solve_ms;       /* device time of the solve */
+} iim_solve_info;
+
+typedef struct iim_problem iim_problem;
+
+/* Fill *opt with the defaults: tol 1e-10, restart 10, max_iter 500, V(2,2), FP32 MG, graph on, reorth on. */
+void iim_default_options(iim_options* opt);
+
+/* Create a problem: validate, allocate the workspace and run the whole set-up
+ * on the device (crossings, curvature check, least-squares fits, correction
+ * records, Shortley-Weller levels, coarse LU).  ``stream`` is a cudaStream_t
+ * (NULL = legacy default stream); all later work of this problem is enqueued
+ * on it.  Synchronises.  On failure *out is NULL. */
+iim_status iim_problem_create(const iim_problem_desc* desc, const iim_options* opt, void* stream,
+                              iim_problem** out);
+
+/* Re-run the set-up in place (same dim, n, bc, order, box), optionally with new
+ * geometry parameters (params may be NULL).  Asynchronous: no allocation and no
+ * host synchronisation; the workspace must be large enough (device-checked,
+ * IIM_ERR_CAPACITY is reported by the next synchronising call). */
+iim_status iim_problem_setup(iim_problem* p, const double* geom_params);
+
+/* Synchronise the problem's stream and return the device status word. */
+iim_status iim_status_get(iim_problem* p);
+
+void iim_problem_destroy(iim_problem* p);
+
+/* Sizes: number of control points K, box data points B (2 d n^(d-1) or 0),
+ * grid nodes N = n^d, unknowns. */
+iim_status iim_problem_sizes(iim_problem* p, int* K, int* B, int64_t* N, int64_t* n_unknowns);
+
+/* Control points in canonical order (axis, then flat index of the lower node
+ * of the cut grid edge): xc_dev [K][dim], normal_dev [K][dim] (out of Omega+).
+ * Either pointer may be NULL.  Asynchronous. */
+iim_status iim_control_points(iim_problem* p, double* xc_dev, double* normal_dev);
+
+/* Phase of every node (1 = Omega+) as bytes, n^d entries.  Asynchronous. */
+iim_status iim_phase(iim_problem* p, uint8_t* phase_dev);
+
+/* Data of Eq. 12 (L_Gamma u_Gamma): f_dev [N] source; g_dev [K] ubar (Dirichlet)
+ * or qbar (Neumann); j0_dev, j1_dev [K] interface jumps; box_dev [B] outer-box
+ * Dirichlet values, faces (-x0,+x0,-x1,+x1,-x2,+x2), each face flat over the
+ * remaining node indices (lowest axis fastest).  Unused pointers may be NULL.
+ * Computes b = f - L_Gamma u_Gamma on the device.  Asynchronous. */
+iim_status iim_set_data(iim_problem* p, const double* f_dev, const double* g_dev, const double* j0_dev,
+                        const double* j1_dev, const double* box_dev);
+
+/* w = L_Omega u (+ L_Gamma u_Gamma of the last iim_set_data if include_data). Asynchronous. */
+iim_status iim_apply(iim_problem* p, const double* u_dev, double* w_dev, int include_data);
+
+/* b of the last iim_set_data.  Asynchronous. */
+iim_status iim_rhs(iim_problem* p, double* b_dev);
+
+/* z = one V-cycle of the Shortley-Weller multigrid applied to v / beta_sigma (Sec. 3.3). Asynchronous. */
+iim_status iim_precondition(iim_problem* p, const double* v_dev, double* z_dev);
+
+/* FGMRES solve of L_Omega x = b (Sec. 4.1).  x_dev: in x0, out x.  Synchronises. */
+iim_status iim_solve(iim_problem* p, double* x_dev, iim_solve_info* info);
+
+/* Same as iim_set_data + iim_solve with host buffers: copies f, g, j0, j1, box
+ * host -> device, solves, and copies x back to x_host.  Synchronises. */
+iim_status iim_solve_host(iim_problem* p, const double* f_host, const double* g_host, const double* j0_host,
+                          const double* j1_host, const double* box_host, double* x_host, iim_solve_info* info);
+
+/* Many independent problems (each created beforehand, each with its data set):
+ * enqueues every solve graph on a pool of streams so that their kernels overlap
+ * on the device, then waits.  infos may be NULL. */
+iim_status iim_batch_solve(iim_problem** probs, double** x_devs, int count, iim_solve_info* infos);
+
+/* Kernel launches issued by this library in the calling process so far. */
+int64_t iim_launch_count(void);
+
+const char* iim_last_error(void);
+const char* iim_status_string(iim_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IIM_H */

@@ -10,8 +10,8 @@ Layout
   geometry.py  level sets, grid-line crossings, normals, curvature   (Sec. 2.1)
   stencils.py  centred second-derivative coefficients, sigma_max     (Sec. 2.5, Tab. 1)
   fits.py      least-squares interpolants, ghost / Neumann / jump rows (Sec. 2.1-2.2)
-  operator.py  the (n,k) IIM operator L_Omega and data term           (Sec. 2.3, Eq. 7)
-  sw.py        Shortley-Weller operators and 1D formulas              (Sec. 3.1, Eqs. 12-15)
+  operator.py  the (n,k) IIM operator L_Omega and data term           (Sec. 2.3, Eq. 12)
+  sw.py        Shortley-Weller operators and 1D formulas              (Sec. 3.1, Eqs. 18-21)
   mg.py        geometric multigrid V-cycle                           (Sec. 3.3)
   fgmres.py    right-preconditioned flexible GMRES(m)                (Sec. 4.1)
   problem.py   glue: build everything for one problem, solve it

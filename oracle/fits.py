@@ -6,10 +6,10 @@ set X_c (Sec. 2.1): the phase-sigma nodes inside a half-ellipse (half-ellipsoid
 in 3D) on the sigma side of Gamma, minus the phase-sigma node closest to x_c.
 
 Every quantity the operator needs is a row of the pseudo-inverse V^+ = R^-1 Q^T
-of the Vandermonde matrix V (one QR per control point, Eq. 8 and the remark
-after Eq. 10):
-  ghost row    p_c(x_g)            = v(xi_g)^T V^+ [u_c; u_X]          (Eq. 8)
-  derivative   n . grad p_c(x_c)   = (1/h) sum_k n_k (V^+)_{e_k,:} [u_c; u_X]  (Eq. 9)
+of the Vandermonde matrix V (one QR per control point, as remarked after
+Eq. 6):
+  ghost row    p_c(x_g)            = v(xi_g)^T V^+ [u_c; u_X]          (Eq. 4)
+  derivative   n . grad p_c(x_c)   = (1/h) sum_k n_k (V^+)_{e_k,:} [u_c; u_X]  (Eq. 5)
 
 Readings (the half-ellipse sizes are defined in a companion paper that is not
 reproduced here; parity unpinned against the paper's numbers):

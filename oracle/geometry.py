@@ -5,7 +5,7 @@ Paper Sec. 2.1: a *control point* x_c is the intersection of a 1D stencil
 condition |kappa dx| < 1/4 (Eq. 3), kappa being the largest principal
 curvature.
 
-Conventions (paper Eqs. 1, 5): Omega+ = {phi >= 0}; the normal n points out of
+Conventions (paper Eqs. 1, 8): Omega+ = {phi >= 0}; the normal n points out of
 Omega+ towards Omega-, so n = -grad(phi)/|grad(phi)|.
 """
 from __future__ import annotations

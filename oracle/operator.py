@@ -1,21 +1,21 @@
-"""The (n,k) immersed-interface Laplacian L_Omega u + L_Gamma u_Gamma (paper Sec. 2.3, Eq. 7).
+"""The (n,k) immersed-interface Laplacian L_Omega u + L_Gamma u_Gamma (paper Sec. 2.3, Eq. 12).
 
 At every unknown node i of phase sigma the operator is the dimension-split
 centred stencil (Sec. 2.1)
 
     (L u)_i = beta_sigma / h^2  sum_axes sum_{j=-w..w} a_j  u~_{i + j e_axis}
 
-applied to the extended function of Eq. 4: u~ = u at nodes of phase sigma, and
+applied to the extended function of Eq. 2: u~ = u at nodes of phase sigma, and
 at nodes outside phase sigma the ghost value p_c(x) of the *first* control
-point c met when walking from i along the axis (Eq. 8).  A node further along
+point c met when walking from i along the axis (Eq. 4).  A node further along
 the walk that is back in phase sigma uses u.
 
 Control-point values (the affine data enter here):
   Dirichlet  u_c = ubar                                               (Eq. 1)
-  Neumann    u_c = (qbar - sum_i s_i u_i) / s_c, s = beta+ * derivative row (Eqs. 9-10)
+  Neumann    u_c = (qbar - sum_i s_i u_i) / s_c, s = beta+ * derivative row (Eqs. 5-6)
   interface  u+ = ubar + (j1 - beta- s-_c j0)/S,  u- = ubar + (j1 - beta+ s+_c j0)/S,
              ubar = -(beta+ sum s+_i u_i - beta- sum s-_i u_i)/S,
-             S = beta+ s+_c - beta- s-_c                               (Eqs. 11-13)
+             S = beta+ s+_c - beta- s-_c                               (Eqs. 9-11)
 
 Outer box (reading; the paper's domains are periodic or unbounded): with a
 Dirichlet box the faces sit half a cell outside the first/last nodes, and

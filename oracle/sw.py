@@ -1,22 +1,22 @@
 """Shortley-Weller low-order discretisation (paper Sec. 3.1).
 
 1D formulas with psi = (distance to the wall) / dx:
-  Dirichlet, Eq. 12 (case (c); a regular side uses psi = 1 and its neighbour):
+  Dirichlet, Eq. 18 (case (c); a regular side uses psi = 1 and its neighbour):
      u'' = [2 uw-/(psi-(psi-+psi+)) - 2 u_i/(psi- psi+) + 2 uw+/(psi+(psi-+psi+))] / dx^2
-  Neumann, Eq. 13 (a) wall on the left, (b) wall on the right, (c) both:
+  Neumann, Eq. 19 (a) wall on the left, (b) wall on the right, (c) both:
      (a) [-2 dx dUw-/(2psi-+psi+) - 2u_i/(psi+(2psi-+psi+)) + 2u_{i+1}/(psi+(2psi-+psi+))] / dx^2
      (b) [ 2u_{i-1}/(psi-(psi-+2psi+)) - 2u_i/(psi-(psi-+2psi+)) + 2 dx dUw+/(psi-+2psi+)] / dx^2
      (c) [dUw+ - dUw-] / (dx (psi- + psi+))
   Reading: the printed case (b) carries psi+ in the first two denominators;
   the mirror image of case (a) and exactness on quadratics (the property that
   defines these stencils) both require psi-, which is what is used here.
-  Interface wall values, Eq. 15, with alpha = psi/beta and x_i on the minus side:
+  Interface wall values, Eq. 21, with alpha = psi/beta and x_i on the minus side:
      uw+ = ub + alpha+ [u]/(alpha+ + alpha-),  uw- = ub - alpha- [u]/(alpha+ + alpha-),
      ub  = (alpha+ u_i + alpha- u_{i+1})/(alpha+ + alpha-)
            - dx alpha+ alpha- [beta u']/(alpha+ + alpha-),
-  Reading: these values satisfy uw+ - uw- = [u], the convention of Eq. 5
-  ([u] = u+ - u-), and the flux balance of Eq. 14; the "[u] = uw- - uw+"
-  printed in Eq. 14 is taken as a sign slip.  Only the homogeneous form,
+  Reading: these values satisfy uw+ - uw- = [u], the convention of Sec. 2.2
+  ([u] = u+ - u-, stated before Eq. 9), and the flux balance of Eq. 20; the
+  "[u] = uw- - uw+" printed in Eq. 20 is taken as a sign slip.  Only the homogeneous form,
   the same under either sign, enters the preconditioner.
 Shift (Sec. 3.1, last paragraph): boundary psi is clamped to >= 1/2; interface
 psi+ = psi- = 1/2.  Multi-D: the 1D stencils are applied along each axis.
@@ -52,7 +52,7 @@ def sw_neumann_both(dum, dup, pm, pp, dx):
 
 
 def sw_interface_walls(ui, uip1, jump_u, jump_flux, pm, pp, beta_m, beta_p, dx):
-    """Wall values (uw+, uw-) of Eq. 15; x_i on the minus side, x_{i+1} on the plus side."""
+    """Wall values (uw+, uw-) of Eq. 21; x_i on the minus side, x_{i+1} on the plus side."""
     ap, am = pp / beta_p, pm / beta_m
     ub = (ap * ui + am * uip1) / (ap + am) - dx * ap * am * jump_flux / (ap + am)
     return ub + ap * jump_u / (ap + am), ub - am * jump_u / (ap + am)
@@ -70,7 +70,7 @@ class SWLevel:
     Per node and axis the left/right side is one of: a regular neighbour
     (psi = 1), a Dirichlet wall (immersed boundary, psi clamped >= 1/2, or a box
     face at psi = 1/2, value 0), a Neumann wall (psi clamped >= 1/2, zero flux),
-    or an interface wall (psi = 1/2, value = the Eq. 15 wall value, which
+    or an interface wall (psi = 1/2, value = the Eq. 21 wall value, which
     couples the node with its neighbour across the interface).
     """
 
@@ -90,7 +90,7 @@ class SWLevel:
         # crossing fraction t on the edge (lower node, axis)
         t_edge = np.full((d, N), np.nan)
         t_edge[cr.axis, cr.lo] = cr.t
-        # interface wall weights (homogeneous Eq. 15 with psi = 1/2):
+        # interface wall weights (homogeneous Eq. 21 with psi = 1/2):
         # uw = lam_minus * u(minus node) + lam_plus * u(plus node)
         lam_minus, _ = sw_interface_walls(1.0, 0.0, 0.0, 0.0, 0.5, 0.5, beta_m, beta_p, 1.0)
         lam_plus, _ = sw_interface_walls(0.0, 1.0, 0.0, 0.0, 0.5, 0.5, beta_m, beta_p, 1.0)

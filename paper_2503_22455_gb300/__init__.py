@@ -1,0 +1,262 @@
+"""Python binding of the GB300 IIM Poisson solver library (``_lib/libiim.so``).
+
+Argument marshalling only: every computation runs in the CUDA kernels behind
+the C ABI declared in ``include/iim.h``.  PyTorch provides device memory and
+streams.  Importing this module does not need a GPU; creating a problem does,
+and fails loudly when the compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libiim.so")
+
+IIM_OK = 0
+STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "curvature", 3: "rank", 4: "singular", 5: "not converged",
+                6: "breakdown", 7: "budget", 8: "timeout", 9: "cuda", 10: "geometry", 11: "capacity"}
+GEOM = {"circle": 0, "ellipse": 1, "star": 2, "sphere": 3, "ellipsoid": 4}
+BC = {"dirichlet": 0, "neumann": 1, "interface": 2}
+MG_FP32, MG_FP64 = 0, 1
+
+
+class IIMError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"iim status {status} ({STATUS_NAMES.get(status, '?')}): {msg}")
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("geom_kind", ctypes.c_int),
+                ("plus_inside", ctypes.c_int), ("geom_params", ctypes.c_double * 8), ("bc", ctypes.c_int),
+                ("box_bc", ctypes.c_int), ("beta_plus", ctypes.c_double), ("beta_minus", ctypes.c_double),
+                ("order", ctypes.c_int)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("mg_precision", ctypes.c_int),
+                ("use_graph", ctypes.c_int), ("reorth", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("converged", ctypes.c_int), ("relres", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+SIGNATURES = {
+    "iim_default_options": (None, [ctypes.POINTER(Options)]),
+    "iim_problem_create": (ctypes.c_int, [ctypes.POINTER(Desc), ctypes.POINTER(Options), ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_void_p)]),
+    "iim_problem_setup": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "iim_status_get": (ctypes.c_int, [ctypes.c_void_p]),
+    "iim_problem_destroy": (None, [ctypes.c_void_p]),
+    "iim_problem_sizes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "iim_control_points": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "iim_phase": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "iim_set_data": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 5),
+    "iim_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "iim_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "iim_precondition": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "iim_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(SolveInfo)]),
+    "iim_solve_host": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 6 + [ctypes.POINTER(SolveInfo)]),
+    "iim_batch_solve": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                       ctypes.POINTER(SolveInfo)]),
+    "iim_launch_count": (ctypes.c_int64, []),
+    "iim_last_error": (ctypes.c_char_p, []),
+    "iim_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"IIM CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status, what=""):
+    if status != IIM_OK:
+        msg = load().iim_last_error().decode(errors="replace")
+        raise IIMError(status, f"{what}: {msg}")
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load().iim_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def make_desc(dim, n, geom_kind, geom_params, plus_inside, bc, box_bc, beta_plus=1.0, beta_minus=1.0, order=4):
+    d = Desc()
+    d.dim, d.n, d.geom_kind, d.plus_inside = int(dim), int(n), int(geom_kind), int(bool(plus_inside))
+    p = list(geom_params) + [0.0] * (8 - len(geom_params))
+    for k in range(8):
+        d.geom_params[k] = float(p[k])
+    d.bc, d.box_bc = int(bc), int(box_bc)
+    d.beta_plus, d.beta_minus = float(beta_plus), float(beta_minus)
+    d.order = int(order)
+    return d
+
+
+def desc_from_spec(spec) -> Desc:
+    """Descriptor from any object with the fields of a problem statement (n, geometry, bc, ...)."""
+    g = spec.geometry
+    return make_desc(g.dim, spec.n, g.kind, g.params, g.plus_inside, spec.bc, spec.box_bc,
+                     spec.beta_plus, spec.beta_minus, spec.order)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a):
+    """Host buffer pointer (numpy array or pinned/pageable CPU tensor of float64)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    import numpy as np
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class Problem:
+    """One immersed-interface Poisson problem resident on the device."""
+
+    def __init__(self, desc: Desc, options: Options | None = None, stream=None):
+        import torch
+        lib = load()
+        self.desc = desc
+        self.options = options or default_options()
+        self.stream = stream or torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        st = lib.iim_problem_create(ctypes.byref(desc), ctypes.byref(self.options),
+                                    ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        _check(st, "iim_problem_create")
+        self.h = h
+        K, B = ctypes.c_int(), ctypes.c_int()
+        N, U = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib.iim_problem_sizes(self.h, ctypes.byref(K), ctypes.byref(B), ctypes.byref(N), ctypes.byref(U)))
+        self.K, self.B, self.N, self.n_unknowns = K.value, B.value, N.value, U.value
+        self.dim, self.n = desc.dim, desc.n
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().iim_problem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _empty(self, *shape, dtype=None):
+        import torch
+        return torch.empty(*shape, dtype=dtype or torch.float64, device="cuda")
+
+    def setup(self, geom_params=None):
+        arr = None
+        if geom_params is not None:
+            arr = (ctypes.c_double * 8)(*(list(geom_params) + [0.0] * (8 - len(geom_params))))
+        _check(load().iim_problem_setup(self.h, arr), "iim_problem_setup")
+
+    def refresh_sizes(self):
+        K = ctypes.c_int()
+        _check(load().iim_problem_sizes(self.h, ctypes.byref(K), None, None, None))
+        self.K = K.value
+        return self.K
+
+    def status(self):
+        return load().iim_status_get(self.h)
+
+    def control_points(self):
+        xc = self._empty(max(self.K, 1), self.dim)
+        nc = self._empty(max(self.K, 1), self.dim)
+        _check(load().iim_control_points(self.h, _ptr(xc), _ptr(nc)))
+        return xc[:self.K], nc[:self.K]
+
+    def phase(self):
+        import torch
+        ph = torch.empty(self.N, dtype=torch.uint8, device="cuda")
+        _check(load().iim_phase(self.h, ctypes.c_void_p(ph.data_ptr())))
+        return ph
+
+    def set_data(self, f, g=None, j0=None, j1=None, box=None):
+        _check(load().iim_set_data(self.h, _ptr(f), _ptr(g), _ptr(j0), _ptr(j1), _ptr(box)), "iim_set_data")
+
+    def apply(self, u, include_data=False, out=None):
+        w = out if out is not None else self._empty(self.N)
+        _check(load().iim_apply(self.h, _ptr(u), _ptr(w), int(include_data)), "iim_apply")
+        return w
+
+    def rhs(self):
+        b = self._empty(self.N)
+        _check(load().iim_rhs(self.h, _ptr(b)))
+        return b
+
+    def precondition(self, v, out=None):
+        z = out if out is not None else self._empty(self.N)
+        _check(load().iim_precondition(self.h, _ptr(v), _ptr(z)), "iim_precondition")
+        return z
+
+    def solve(self, x=None, check=True):
+        import torch
+        if x is None:
+            x = torch.zeros(self.N, dtype=torch.float64, device="cuda")
+        info = SolveInfo()
+        st = load().iim_solve(self.h, _ptr(x), ctypes.byref(info))
+        if check:
+            _check(st, "iim_solve")
+        return x, info
+
+    def solve_host(self, f, g=None, j0=None, j1=None, box=None, x=None, check=True):
+        import numpy as np
+        if x is None:
+            x = np.zeros(self.N)
+        info = SolveInfo()
+        st = load().iim_solve_host(self.h, _hptr(f), _hptr(g), _hptr(j0), _hptr(j1), _hptr(box), _hptr(x),
+                                   ctypes.byref(info))
+        if check:
+            _check(st, "iim_solve_host")
+        return x, info
+
+
+def batch_solve(problems, xs, check=True):
+    lib = load()
+    n = len(problems)
+    hs = (ctypes.c_void_p * n)(*[p.h.value for p in problems])
+    ps = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+    infos = (SolveInfo * n)()
+    st = lib.iim_batch_solve(hs, ps, n, infos)
+    if check:
+        _check(st, "iim_batch_solve")
+    return [infos[i] for i in range(n)], st
+
+
+def launch_count() -> int:
+    return int(load().iim_launch_count())

@@ -1,0 +1,599 @@
+// C ABI of the library (declared in include/iim.h): problem life cycle, data,
+// operator / preconditioner calls, the FGMRES solve and the batched solve.
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "kernels.cuh"
+
+namespace iim {
+
+static std::atomic<int64_t> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+
+void* dev_alloc(Problem& P, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc failed for " + std::to_string(bytes) + " bytes");
+    return nullptr;
+  }
+  P.allocs.push_back(p);
+  P.bytes += bytes;
+  return p;
+}
+
+static void free_all(Problem& P) {
+  for (void* p : P.allocs) cudaFree(p);
+  P.allocs.clear();
+  if (P.graph_exec) cudaGraphExecDestroy(P.graph_exec);
+  if (P.graph) cudaGraphDestroy(P.graph);
+  if (P.ev0) cudaEventDestroy(P.ev0);
+  if (P.ev1) cudaEventDestroy(P.ev1);
+  P.graph_exec = nullptr;
+  P.graph = nullptr;
+}
+
+static int binom(int a, int b) {
+  int r = 1;
+  for (int k = 1; k <= b; ++k) r = r * (a - b + k) / k;
+  return r;
+}
+
+// centred second-derivative stencils a_{-w..w}: the unique symmetric stencils exact
+// for polynomials of degree <= n+1 (Sec. 2.1; their sigma_max is Tab. 1)
+static void stencil(int order, double* a) {
+  if (order == 4) {
+    const double h[3] = {-5.0 / 2.0, 4.0 / 3.0, -1.0 / 12.0};
+    for (int j = -2; j <= 2; ++j) a[j + 2] = h[j < 0 ? -j : j];
+  } else {
+    const double h[4] = {-49.0 / 18.0, 3.0 / 2.0, -3.0 / 20.0, 1.0 / 90.0};
+    for (int j = -3; j <= 3; ++j) a[j + 3] = h[j < 0 ? -j : j];
+  }
+}
+
+// outer-box closure: Lagrange weights of the degree-q polynomial through the face
+// value (position 0) and the nodes m = 2..q+1 from the face (positions -(m - 1/2)),
+// evaluated at the ghosts k = 1..w (positions k - 1/2)
+static void box_weights(int q, int w, double out[kMaxW][8]) {
+  double pts[8];
+  pts[0] = 0.0;
+  for (int m = 2; m <= q + 1; ++m) pts[m - 1] = -(m - 0.5);
+  for (int k = 0; k < kMaxW; ++k)
+    for (int a = 0; a < 8; ++a) out[k][a] = 0.0;
+  for (int k = 1; k <= w; ++k) {
+    double x = k - 0.5;
+    for (int a = 0; a <= q; ++a) {
+      double num = 1, den = 1;
+      for (int b = 0; b <= q; ++b)
+        if (b != a) { num *= x - pts[b]; den *= pts[a] - pts[b]; }
+      out[k - 1][a] = num / den;
+    }
+  }
+}
+
+// max rows of a least-squares set: lattice points of the half-ellipse (half
+// ellipsoid) at the largest growth, with a one-cell margin on every semi-axis
+static int rows_cap(int dim, int q) {
+  double an = q + 1.0 + 1.5 + 1.0, at = q / 2 + 1.0 + 1.5 + 1.0;
+  double v = dim == 2 ? M_PI * an * at / 2.0 : 2.0 / 3.0 * M_PI * an * at * at;
+  int cap = (int)std::ceil(v) + 8;
+  return (cap + 7) / 8 * 8;
+}
+
+static std::vector<int> level_sizes(int n, int dim) {
+  const int cmin = dim == 2 ? 8 : 4;
+  std::vector<int> s{n};
+  while (s.back() % 2 == 0 && s.back() / 2 >= cmin) s.push_back(s.back() / 2);
+  return s;
+}
+
+static iim_status cuda_check(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return IIM_ERR_CUDA;
+  }
+  return IIM_OK;
+}
+
+static iim_status read_status(Problem& P) {
+  int st[2] = {0, 0};
+  if (cudaMemcpy(st, P.d_status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return cuda_check("status");
+  if (st[0]) return (iim_status)st[0];
+  return (iim_status)st[1];
+}
+
+static iim_status validate(const iim_problem_desc* d, const iim_options* o) {
+  if (!d || !o) return IIM_ERR_INVALID_ARG;
+  if (d->dim != 2 && d->dim != 3) return IIM_ERR_INVALID_ARG;
+  if (d->order != 4 && d->order != 6) return IIM_ERR_INVALID_ARG;
+  if (d->dim == 3 && d->order == 6) {
+    set_error("3D problems support the (4,5) scheme");
+    return IIM_ERR_INVALID_ARG;
+  }
+  if (d->n < 16 || d->n > (d->dim == 2 ? 32768 : 1024)) return IIM_ERR_INVALID_ARG;
+  bool k2 = d->geom_kind == IIM_GEOM_CIRCLE || d->geom_kind == IIM_GEOM_ELLIPSE || d->geom_kind == IIM_GEOM_STAR;
+  bool k3 = d->geom_kind == IIM_GEOM_SPHERE || d->geom_kind == IIM_GEOM_ELLIPSOID;
+  if ((d->dim == 2 && !k2) || (d->dim == 3 && !k3)) return IIM_ERR_INVALID_ARG;
+  if (d->bc < 0 || d->bc > 2 || d->box_bc < 0 || d->box_bc > 1) return IIM_ERR_INVALID_ARG;
+  if (d->bc == IIM_BC_INTERFACE && d->box_bc != IIM_BOX_DIRICHLET) {
+    set_error("interface problems need a Dirichlet outer box");
+    return IIM_ERR_INVALID_ARG;
+  }
+  if (!(d->beta_plus > 0) || (d->bc == IIM_BC_INTERFACE && !(d->beta_minus > 0))) return IIM_ERR_INVALID_ARG;
+  if (o->restart < 1 || o->restart > kMaxRestart || o->max_iter < 1 || !(o->tol > 0)) return IIM_ERR_INVALID_ARG;
+  if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 + o->nu2 < 1) return IIM_ERR_INVALID_ARG;
+  if (o->mg_precision != IIM_MG_FP32 && o->mg_precision != IIM_MG_FP64) return IIM_ERR_INVALID_ARG;
+  return IIM_OK;
+}
+
+static int read_count(Problem& P, int k) {
+  int v = 0;
+  cudaMemcpyAsync(&v, P.d_counts + k, sizeof(int), cudaMemcpyDeviceToHost, P.stream);
+  cudaStreamSynchronize(P.stream);
+  return v;
+}
+
+size_t fit_smem_bytes(const Problem& P);
+
+}  // namespace iim
+
+using namespace iim;
+
+struct iim_problem {
+  Problem P;
+};
+
+extern "C" {
+
+void iim_default_options(iim_options* o) {
+  if (!o) return;
+  o->tol = 1e-10;
+  o->restart = 10;
+  o->max_iter = 500;
+  o->nu1 = 2;
+  o->nu2 = 2;
+  o->mg_precision = IIM_MG_FP32;
+  o->use_graph = 1;
+  o->reorth = 1;
+}
+
+const char* iim_last_error(void) { return g_err.c_str(); }
+
+const char* iim_status_string(iim_status s) {
+  switch (s) {
+    case IIM_OK: return "ok";
+    case IIM_ERR_INVALID_ARG: return "invalid argument";
+    case IIM_ERR_CURVATURE: return "curvature condition |kappa h| < 1/4 violated";
+    case IIM_ERR_RANK: return "least-squares fit rank deficient";
+    case IIM_ERR_SINGULAR: return "singular control-point closure";
+    case IIM_ERR_NOT_CONVERGED: return "FGMRES did not converge";
+    case IIM_ERR_BREAKDOWN: return "NaN/Inf in the Krylov recurrence";
+    case IIM_ERR_BUDGET: return "device memory budget exceeded";
+    case IIM_ERR_TIMEOUT: return "device wait timed out";
+    case IIM_ERR_CUDA: return "CUDA error";
+    case IIM_ERR_GEOMETRY: return "geometry too close to the outer box";
+    case IIM_ERR_CAPACITY: return "workspace capacity exceeded";
+  }
+  return "unknown";
+}
+
+int64_t iim_launch_count(void) { return g_launches.load(); }
+
+iim_status iim_problem_create(const iim_problem_desc* desc, const iim_options* opt, void* stream,
+                              iim_problem** out) {
+  if (!out) return IIM_ERR_INVALID_ARG;
+  *out = nullptr;
+  iim_status vs = validate(desc, opt);
+  if (vs != IIM_OK) {
+    if (g_err.empty()) set_error("invalid problem descriptor or options");
+    return vs;
+  }
+  {
+    cudaError_t stale = cudaGetLastError();
+    if (stale != cudaSuccess) {
+      set_error(std::string("error pending before create: ") + cudaGetErrorString(stale));
+      return IIM_ERR_CUDA;
+    }
+  }
+  iim_problem* H = new iim_problem();
+  Problem& P = H->P;
+  P.desc = *desc;
+  P.opt = *opt;
+  P.stream = (cudaStream_t)stream;
+  const int d = desc->dim, n = desc->n;
+  P.g.dim = d;
+  P.g.n = n;
+  P.g.N = (int64_t)n * n * (d == 3 ? n : 1);
+  P.g.h = 2.0 / n;
+  P.w = desc->order / 2;
+  P.q = desc->order;
+  P.M = binom(P.q + d, d);
+  stencil(desc->order, P.a);
+  P.rcap = rows_cap(d, P.q);
+  P.box_active = desc->box_bc == IIM_BOX_DIRICHLET;
+  P.B = P.box_active ? 2 * d * (int)(P.g.N / n) : 0;
+  box_weights(P.q, P.w, P.box_w);
+  const int64_t N = P.g.N;
+  cudaEventCreate(&P.ev0);
+  cudaEventCreate(&P.ev1);
+  // monomials of total degree <= q, graded order
+  std::vector<int> mono;
+  for (int deg = 0; deg <= P.q; ++deg) {
+    if (d == 2) {
+      for (int a = deg; a >= 0; --a) { mono.push_back(a); mono.push_back(deg - a); mono.push_back(0); }
+    } else {
+      for (int a = deg; a >= 0; --a)
+        for (int b = deg - a; b >= 0; --b) { mono.push_back(a); mono.push_back(b); mono.push_back(deg - a - b); }
+    }
+  }
+  if (P.M > 40) { set_error("too many monomials"); free_all(P); delete H; return IIM_ERR_INVALID_ARG; }
+#define IIM_FAIL(code) do { free_all(P); delete H; return (code); } while (0)
+#define IIM_ALLOC(ptr, type, count)                                        \
+  do {                                                                     \
+    ptr = (type*)dev_alloc(P, sizeof(type) * (size_t)(count));             \
+    if (!ptr) IIM_FAIL(IIM_ERR_BUDGET);                                    \
+  } while (0)
+  IIM_ALLOC(P.d_monos, int, mono.size());
+  cudaMemcpy(P.d_monos, mono.data(), sizeof(int) * mono.size(), cudaMemcpyHostToDevice);
+  IIM_ALLOC(P.d_status, int, 4);
+  IIM_ALLOC(P.d_counts, int, 16 + 32);
+  cudaMemsetAsync(P.d_status, 0, sizeof(int) * 4, P.stream);
+  cudaMemsetAsync(P.d_counts, 0, sizeof(int) * 48, P.stream);
+  IIM_ALLOC(P.phase, uint8_t, N);
+  IIM_ALLOC(P.edge_flag, int32_t, N * d);
+  IIM_ALLOC(P.edge_id, int32_t, N * d);
+  IIM_ALLOC(P.aff_flag, int32_t, N);
+  IIM_ALLOC(P.aff_idx, int32_t, N);
+  P.scan_scratch_len = scan_scratch_ints(N * d) + 64;
+  IIM_ALLOC(P.scan_scratch, int, P.scan_scratch_len);
+  // pass 1: count crossings
+  setup_geometry(P, true);
+  int K = read_count(P, 0);
+  if (cuda_check("setup: crossing count") != IIM_OK) IIM_FAIL(IIM_ERR_CUDA);
+  P.K = K;
+  P.K_cap = K + K / 4 + 64;
+  IIM_ALLOC(P.cr_axis, int32_t, P.K_cap);
+  IIM_ALLOC(P.cr_lo, int32_t, P.K_cap);
+  IIM_ALLOC(P.cr_loplus, uint8_t, P.K_cap);
+  IIM_ALLOC(P.cr_t, double, P.K_cap);
+  IIM_ALLOC(P.cr_x, double, (size_t)P.K_cap * d);
+  IIM_ALLOC(P.cr_n, double, (size_t)P.K_cap * d);
+  IIM_ALLOC(P.cr_kappa, double, P.K_cap);
+  cudaMemsetAsync(P.cr_kappa, 0, sizeof(double) * P.K_cap, P.stream);
+  // pass 2: crossings, curvature, affected nodes
+  setup_geometry(P, false);
+  int n_aff = read_count(P, 1);
+  if (cuda_check("setup: crossings") != IIM_OK) IIM_FAIL(IIM_ERR_CUDA);
+  iim_status st = read_status(P);
+  if (st != IIM_OK) {
+    set_error(iim_status_string(st));
+    IIM_FAIL(st);
+  }
+  P.n_aff = n_aff;
+  P.aff_cap = n_aff + n_aff / 4 + 64;
+  IIM_ALLOC(P.aff_node, int32_t, P.aff_cap);
+  IIM_ALLOC(P.aff_fit, int32_t, (size_t)P.aff_cap * 2 * d);
+  IIM_ALLOC(P.aff_j, int32_t, (size_t)P.aff_cap * 2 * d);
+  const bool iface = desc->bc == IIM_BC_INTERFACE;
+  P.nfit_cap = iface ? 2 * P.K_cap : P.K_cap;
+  IIM_ALLOC(P.fit_R, int32_t, P.nfit_cap);
+  IIM_ALLOC(P.fit_nodes, int32_t, (size_t)P.nfit_cap * P.rcap);
+  IIM_ALLOC(P.fit_coef, double, (size_t)P.nfit_cap * (P.w + 1) * P.rcap);
+  IIM_ALLOC(P.fit_cdat, double, (size_t)P.nfit_cap * (P.w + 1));
+  IIM_ALLOC(P.G, double, (size_t)P.nfit_cap * P.w);
+  cudaMemsetAsync(P.fit_R, 0, sizeof(int32_t) * P.nfit_cap, P.stream);
+  if (fit_smem_bytes(P) > 227 * 1024) { set_error("least-squares workspace too large"); IIM_FAIL(IIM_ERR_INVALID_ARG); }
+  st = setup_fits(P);
+  if (st != IIM_OK) IIM_FAIL(st);
+  cudaStreamSynchronize(P.stream);
+  if (cuda_check("setup: fits") != IIM_OK) IIM_FAIL(IIM_ERR_CUDA);
+  // data arrays
+  IIM_ALLOC(P.d_g, double, P.K_cap);
+  IIM_ALLOC(P.d_j0, double, P.K_cap);
+  IIM_ALLOC(P.d_j1, double, P.K_cap);
+  IIM_ALLOC(P.d_box, double, P.B > 0 ? P.B : 1);
+  cudaMemsetAsync(P.d_g, 0, sizeof(double) * P.K_cap, P.stream);
+  cudaMemsetAsync(P.d_j0, 0, sizeof(double) * P.K_cap, P.stream);
+  cudaMemsetAsync(P.d_j1, 0, sizeof(double) * P.K_cap, P.stream);
+  cudaMemsetAsync(P.d_box, 0, sizeof(double) * (P.B > 0 ? P.B : 1), P.stream);
+  IIM_ALLOC(P.b, double, N);
+  cudaMemsetAsync(P.b, 0, sizeof(double) * N, P.stream);
+  // multigrid levels
+  std::vector<int> sizes = level_sizes(n, d);
+  const size_t esz = opt->mg_precision == IIM_MG_FP64 ? 8 : 4;
+  P.lv.resize(sizes.size());
+  for (size_t l = 0; l < sizes.size(); ++l) {
+    Level& L = P.lv[l];
+    L.g.dim = d;
+    L.g.n = sizes[l];
+    L.g.N = (int64_t)sizes[l] * sizes[l] * (d == 3 ? sizes[l] : 1);
+    L.g.h = 2.0 / sizes[l];
+    if (l == 0) L.phase = P.phase;
+    else IIM_ALLOC(L.phase, uint8_t, L.g.N);
+    IIM_ALLOC(L.aux, int32_t, L.g.N);
+    IIM_ALLOC(L.flag, int32_t, L.g.N);
+    IIM_ALLOC(L.idx, int32_t, L.g.N);
+    L.u = dev_alloc(P, esz * L.g.N);
+    L.f = dev_alloc(P, esz * L.g.N);
+    if (!L.u || !L.f) IIM_FAIL(IIM_ERR_BUDGET);
+    cudaMemsetAsync(L.u, 0, esz * L.g.N, P.stream);
+    cudaMemsetAsync(L.f, 0, esz * L.g.N, P.stream);
+  }
+  setup_levels(P, true);
+  cudaStreamSynchronize(P.stream);
+  if (cuda_check("setup: level classification") != IIM_OK) IIM_FAIL(IIM_ERR_CUDA);
+  for (size_t l = 0; l < P.lv.size(); ++l) {
+    Level& L = P.lv[l];
+    L.n_irr = read_count(P, 2 + (int)l);
+    L.irr_cap = L.n_irr + L.n_irr / 4 + 64;
+    const int D = 2 * d + 1;
+    IIM_ALLOC(L.tab64, double, (size_t)L.irr_cap * D);
+    IIM_ALLOC(L.tab32, float, (size_t)L.irr_cap * D);
+  }
+  setup_levels(P, false);
+  cudaStreamSynchronize(P.stream);
+  if (cuda_check("setup: level tables") != IIM_OK) IIM_FAIL(IIM_ERR_CUDA);
+  st = read_status(P);
+  if (st != IIM_OK) { set_error(iim_status_string(st)); IIM_FAIL(st); }
+  {
+    // unknown count of the coarsest level from its aux codes (copied to the host once)
+    Level& C = P.lv.back();
+    std::vector<int32_t> aux(C.g.N);
+    cudaMemcpy(aux.data(), C.aux, sizeof(int32_t) * C.g.N, cudaMemcpyDeviceToHost);
+    int nu = 0;
+    for (auto a : aux) nu += a != -2;
+    P.coarse_nu = nu;
+    IIM_ALLOC(P.coarse_map, int32_t, nu > 0 ? nu : 1);
+    IIM_ALLOC(P.coarse_piv, int32_t, nu > 0 ? nu : 1);
+    IIM_ALLOC(P.coarse_lu64, double, 2 * (size_t)nu * nu + 1);
+    IIM_ALLOC(P.coarse_lu32, float, 2 * (size_t)nu * nu + 1);
+  }
+  mg_coarse_factor(P, P.stream);
+  cudaStreamSynchronize(P.stream);
+  if (cuda_check("setup: coarse factor") != IIM_OK) IIM_FAIL(IIM_ERR_CUDA);
+  if (krylov_alloc(P) != IIM_OK) IIM_FAIL(IIM_ERR_BUDGET);
+  cudaStreamSynchronize(P.stream);
+  st = read_status(P);
+  if (st != IIM_OK) { set_error(iim_status_string(st)); IIM_FAIL(st); }
+  if (cuda_check("create") != IIM_OK) IIM_FAIL(IIM_ERR_CUDA);
+  *out = H;
+  return IIM_OK;
+#undef IIM_FAIL
+#undef IIM_ALLOC
+}
+
+iim_status iim_problem_setup(iim_problem* H, const double* params) {
+  if (!H) return IIM_ERR_INVALID_ARG;
+  Problem& P = H->P;
+  if (params)
+    for (int k = 0; k < 8; ++k) P.desc.geom_params[k] = params[k];
+  setup_geometry(P, false);
+  iim_status st = setup_fits(P);
+  if (st != IIM_OK) return st;
+  setup_levels(P, false);
+  mg_coarse_factor(P, P.stream);
+  return cuda_check("setup");
+}
+
+iim_status iim_status_get(iim_problem* H) {
+  if (!H) return IIM_ERR_INVALID_ARG;
+  cudaStreamSynchronize(H->P.stream);
+  iim_status c = cuda_check("status");
+  if (c != IIM_OK) return c;
+  return read_status(H->P);
+}
+
+void iim_problem_destroy(iim_problem* H) {
+  if (!H) return;
+  cudaStreamSynchronize(H->P.stream);
+  free_all(H->P);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) fprintf(stderr, "iim_problem_destroy: CUDA error %s\n", cudaGetErrorString(e));
+  delete H;
+}
+
+iim_status iim_problem_sizes(iim_problem* H, int* K, int* B, int64_t* N, int64_t* nunk) {
+  if (!H) return IIM_ERR_INVALID_ARG;
+  Problem& P = H->P;
+  P.K = read_count(P, 0);
+  if (K) *K = P.K;
+  if (B) *B = P.B;
+  if (N) *N = P.g.N;
+  if (nunk) {
+    if (P.desc.bc == IIM_BC_INTERFACE) *nunk = P.g.N;
+    else {
+      std::vector<uint8_t> ph(P.g.N);
+      cudaMemcpy(ph.data(), P.phase, P.g.N, cudaMemcpyDeviceToHost);
+      int64_t c = 0;
+      for (auto v : ph) c += v;
+      *nunk = c;
+    }
+  }
+  return cuda_check("sizes");
+}
+
+iim_status iim_control_points(iim_problem* H, double* xc, double* nrm) {
+  if (!H) return IIM_ERR_INVALID_ARG;
+  Problem& P = H->P;
+  int K = P.K = read_count(P, 0);
+  if (xc) cudaMemcpyAsync(xc, P.cr_x, sizeof(double) * (size_t)K * P.g.dim, cudaMemcpyDeviceToDevice, P.stream);
+  if (nrm) cudaMemcpyAsync(nrm, P.cr_n, sizeof(double) * (size_t)K * P.g.dim, cudaMemcpyDeviceToDevice, P.stream);
+  return cuda_check("control points");
+}
+
+iim_status iim_phase(iim_problem* H, uint8_t* phase) {
+  if (!H || !phase) return IIM_ERR_INVALID_ARG;
+  Problem& P = H->P;
+  cudaMemcpyAsync(phase, P.phase, P.g.N, cudaMemcpyDeviceToDevice, P.stream);
+  return cuda_check("phase");
+}
+
+// K (the control-point count) is the count of the last set-up whose size the
+// host has read (create, iim_problem_sizes, iim_control_points)
+static void copy_data(Problem& P, const double* g, const double* j0, const double* j1, const double* box,
+                      cudaMemcpyKind kind) {
+  const int Kn = P.K;
+  if (g) cudaMemcpyAsync(P.d_g, g, sizeof(double) * Kn, kind, P.stream);
+  if (j0) cudaMemcpyAsync(P.d_j0, j0, sizeof(double) * Kn, kind, P.stream);
+  if (j1) cudaMemcpyAsync(P.d_j1, j1, sizeof(double) * Kn, kind, P.stream);
+  if (box && P.B > 0) cudaMemcpyAsync(P.d_box, box, sizeof(double) * P.B, kind, P.stream);
+}
+
+iim_status iim_set_data(iim_problem* H, const double* f, const double* g, const double* j0, const double* j1,
+                        const double* box) {
+  if (!H || !f) return IIM_ERR_INVALID_ARG;
+  Problem& P = H->P;
+  copy_data(P, g, j0, j1, box, cudaMemcpyDeviceToDevice);
+  compute_rhs(P, f, P.stream);
+  return cuda_check("set_data");
+}
+
+iim_status iim_apply(iim_problem* H, const double* u, double* w, int include_data) {
+  if (!H || !u || !w) return IIM_ERR_INVALID_ARG;
+  ho_apply(H->P, u, w, include_data != 0, H->P.stream);
+  return cuda_check("apply");
+}
+
+iim_status iim_rhs(iim_problem* H, double* b) {
+  if (!H || !b) return IIM_ERR_INVALID_ARG;
+  cudaMemcpyAsync(b, H->P.b, sizeof(double) * H->P.g.N, cudaMemcpyDeviceToDevice, H->P.stream);
+  return cuda_check("rhs");
+}
+
+iim_status iim_precondition(iim_problem* H, const double* v, double* z) {
+  if (!H || !v || !z) return IIM_ERR_INVALID_ARG;
+  mg_precondition(H->P, v, nullptr, z, H->P.stream);
+  return cuda_check("precondition");
+}
+
+static iim_status solve_enqueue(Problem& P, cudaStream_t s) {
+  if (P.opt.use_graph) {
+    if (!P.graph_exec) {
+      iim_status st = krylov_build_graph(P, P.x);
+      if (st != IIM_OK) return st;
+    }
+    cudaMemsetAsync(P.d_status + 1, 0, sizeof(int), s);
+    cudaGraphLaunch(P.graph_exec, s);
+    note_launch();
+  } else {
+    cudaMemsetAsync(P.d_status + 1, 0, sizeof(int), s);
+    krylov_enqueue_solve(P, P.x, false);
+  }
+  return cuda_check("solve");
+}
+
+static iim_status finish_info(Problem& P, iim_solve_info* info) {
+  iim_solve_info tmp;
+  std::memset(&tmp, 0, sizeof(tmp));
+  krylov_read_info(P, &tmp);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, P.ev0, P.ev1);
+  tmp.solve_ms = ms;
+  iim_status st = read_status(P);
+  if (st == IIM_OK && !tmp.converged) st = IIM_ERR_NOT_CONVERGED;
+  tmp.status = st;
+  if (info) *info = tmp;
+  if (st != IIM_OK) set_error(iim_status_string(st));
+  return st;
+}
+
+iim_status iim_solve(iim_problem* H, double* x, iim_solve_info* info) {
+  if (!H || !x) return IIM_ERR_INVALID_ARG;
+  Problem& P = H->P;
+  cudaMemcpyAsync(P.x, x, sizeof(double) * P.g.N, cudaMemcpyDeviceToDevice, P.stream);
+  cudaEventRecord(P.ev0, P.stream);
+  iim_status st = solve_enqueue(P, P.stream);
+  if (st != IIM_OK) return st;
+  cudaEventRecord(P.ev1, P.stream);
+  cudaMemcpyAsync(x, P.x, sizeof(double) * P.g.N, cudaMemcpyDeviceToDevice, P.stream);
+  cudaStreamSynchronize(P.stream);
+  if (cuda_check("solve") != IIM_OK) return IIM_ERR_CUDA;
+  return finish_info(P, info);
+}
+
+iim_status iim_solve_host(iim_problem* H, const double* f, const double* g, const double* j0, const double* j1,
+                          const double* box, double* x, iim_solve_info* info) {
+  if (!H || !f || !x) return IIM_ERR_INVALID_ARG;
+  Problem& P = H->P;
+  // stage f in the last Krylov basis vector, which the solve overwrites only later
+  double* fst = P.V + (size_t)P.opt.restart * P.Npad;
+  cudaMemcpyAsync(fst, f, sizeof(double) * P.g.N, cudaMemcpyHostToDevice, P.stream);
+  copy_data(P, g, j0, j1, box, cudaMemcpyHostToDevice);
+  compute_rhs(P, fst, P.stream);
+  cudaMemsetAsync(P.x, 0, sizeof(double) * P.g.N, P.stream);
+  cudaEventRecord(P.ev0, P.stream);
+  iim_status st = solve_enqueue(P, P.stream);
+  if (st != IIM_OK) return st;
+  cudaEventRecord(P.ev1, P.stream);
+  cudaMemcpyAsync(x, P.x, sizeof(double) * P.g.N, cudaMemcpyDeviceToHost, P.stream);
+  cudaStreamSynchronize(P.stream);
+  if (cuda_check("solve_host") != IIM_OK) return IIM_ERR_CUDA;
+  return finish_info(P, info);
+}
+
+iim_status iim_batch_solve(iim_problem** probs, double** xs, int count, iim_solve_info* infos) {
+  if (count < 0 || (count > 0 && (!probs || !xs))) return IIM_ERR_INVALID_ARG;
+  static std::mutex mu;
+  static std::vector<cudaStream_t> pool;
+  static std::vector<cudaEvent_t> evs;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    while ((int)pool.size() < 16) {
+      cudaStream_t s;
+      cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+      pool.push_back(s);
+    }
+    while ((int)evs.size() < count) {
+      cudaEvent_t e;
+      cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+      evs.push_back(e);
+    }
+  }
+  iim_status worst = IIM_OK;
+  for (int i = 0; i < count; ++i) {
+    Problem& P = probs[i]->P;
+    if (P.opt.use_graph && !P.graph_exec) {
+      iim_status st = krylov_build_graph(P, P.x);
+      if (st != IIM_OK) return st;
+    }
+  }
+  for (int i = 0; i < count; ++i) {
+    Problem& P = probs[i]->P;
+    cudaStream_t s = pool[i % pool.size()];
+    cudaEventRecord(evs[i], P.stream);
+    cudaStreamWaitEvent(s, evs[i], 0);
+    cudaMemcpyAsync(P.x, xs[i], sizeof(double) * P.g.N, cudaMemcpyDeviceToDevice, s);
+    cudaEventRecord(P.ev0, s);
+    cudaMemsetAsync(P.d_status + 1, 0, sizeof(int), s);
+    if (P.opt.use_graph) {
+      cudaGraphLaunch(P.graph_exec, s);
+      note_launch();
+    }
+    cudaEventRecord(P.ev1, s);
+    cudaMemcpyAsync(xs[i], P.x, sizeof(double) * P.g.N, cudaMemcpyDeviceToDevice, s);
+  }
+  for (size_t k = 0; k < pool.size(); ++k) cudaStreamSynchronize(pool[k]);
+  if (cuda_check("batch") != IIM_OK) return IIM_ERR_CUDA;
+  for (int i = 0; i < count; ++i) {
+    Problem& P = probs[i]->P;
+    if (!P.opt.use_graph) {
+      cudaMemcpy(P.x, xs[i], sizeof(double) * P.g.N, cudaMemcpyDeviceToDevice);
+      cudaMemsetAsync(P.d_status + 1, 0, sizeof(int), P.stream);
+      krylov_enqueue_solve(P, P.x, false);
+      cudaMemcpyAsync(xs[i], P.x, sizeof(double) * P.g.N, cudaMemcpyDeviceToDevice, P.stream);
+      cudaStreamSynchronize(P.stream);
+    }
+    iim_status st = finish_info(P, infos ? &infos[i] : nullptr);
+    if (st != IIM_OK && worst == IIM_OK) worst = st;
+  }
+  return worst;
+}
+
+}  // extern "C"

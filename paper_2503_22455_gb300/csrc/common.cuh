@@ -1,0 +1,213 @@
+// Shared definitions of the GB300 IIM solver library (device code and host glue).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/iim.h"
+
+namespace iim {
+
+constexpr int kMaxDim = 3;
+constexpr int kMaxW = 3;              // stencil half width (6th order)
+constexpr int kMaxRestart = 16;       // FGMRES restart m
+constexpr int kNumSMs = 152;
+
+// status word bits written by device code (first error wins via atomicCAS)
+__host__ __device__ inline int status_code(int s) { return s; }
+
+// --------------------------------------------------------------------------- geometry
+struct Geom {
+  int kind;
+  int dim;
+  double sign;                         // phi = sign * g
+  double p[8];
+};
+
+// g(x) < 0 inside the body; the paper's Omega+ = {phi >= 0}, phi = sign * g
+__host__ __device__ inline double geom_g(const Geom& G, const double* x) {
+  const double* p = G.p;
+  switch (G.kind) {
+    case IIM_GEOM_CIRCLE: return hypot(x[0] - p[0], x[1] - p[1]) - p[2];
+    case IIM_GEOM_SPHERE: {
+      double a = x[0] - p[0], b = x[1] - p[1], c = x[2] - p[2];
+      return sqrt(a * a + b * b + c * c) - p[3];
+    }
+    case IIM_GEOM_ELLIPSE: {
+      double cs = cos(p[4]), sn = sin(p[4]);
+      double dx = x[0] - p[0], dy = x[1] - p[1];
+      double y0 = cs * dx + sn * dy, y1 = -sn * dx + cs * dy;
+      return (y0 / p[2]) * (y0 / p[2]) + (y1 / p[3]) * (y1 / p[3]) - 1.0;
+    }
+    case IIM_GEOM_ELLIPSOID: {
+      double a = (x[0] - p[0]) / p[3], b = (x[1] - p[1]) / p[4], c = (x[2] - p[2]) / p[5];
+      return a * a + b * b + c * c - 1.0;
+    }
+    case IIM_GEOM_STAR: {
+      double dx = x[0] - p[0], dy = x[1] - p[1];
+      double rho = hypot(dx, dy), th = atan2(dy, dx);
+      return rho - (p[2] + p[3] * sin(p[4] * th + p[5]));
+    }
+  }
+  return 0.0;
+}
+
+__host__ __device__ inline double geom_phi(const Geom& G, const double* x) { return G.sign * geom_g(G, x); }
+
+__host__ __device__ inline void geom_grad_g(const Geom& G, const double* x, double* gr) {
+  const double* p = G.p;
+  switch (G.kind) {
+    case IIM_GEOM_CIRCLE: {
+      double a = x[0] - p[0], b = x[1] - p[1], r = hypot(a, b);
+      gr[0] = a / r; gr[1] = b / r; return;
+    }
+    case IIM_GEOM_SPHERE: {
+      double a = x[0] - p[0], b = x[1] - p[1], c = x[2] - p[2], r = sqrt(a * a + b * b + c * c);
+      gr[0] = a / r; gr[1] = b / r; gr[2] = c / r; return;
+    }
+    case IIM_GEOM_ELLIPSE: {
+      double cs = cos(p[4]), sn = sin(p[4]);
+      double dx = x[0] - p[0], dy = x[1] - p[1];
+      double y0 = cs * dx + sn * dy, y1 = -sn * dx + cs * dy;
+      double g0 = 2 * y0 / (p[2] * p[2]), g1 = 2 * y1 / (p[3] * p[3]);
+      gr[0] = cs * g0 - sn * g1; gr[1] = sn * g0 + cs * g1; return;
+    }
+    case IIM_GEOM_ELLIPSOID: {
+      gr[0] = 2 * (x[0] - p[0]) / (p[3] * p[3]);
+      gr[1] = 2 * (x[1] - p[1]) / (p[4] * p[4]);
+      gr[2] = 2 * (x[2] - p[2]) / (p[5] * p[5]);
+      return;
+    }
+    case IIM_GEOM_STAR: {
+      double dx = x[0] - p[0], dy = x[1] - p[1];
+      double rho = hypot(dx, dy), th = atan2(dy, dx);
+      double rp = p[3] * p[4] * cos(p[4] * th + p[5]);
+      gr[0] = dx / rho + rp / rho * (dy / rho);
+      gr[1] = dy / rho - rp / rho * (dx / rho);
+      return;
+    }
+  }
+}
+
+// largest |principal curvature| of the level surface through x
+__host__ __device__ inline double geom_curvature(const Geom& G, const double* x) {
+  const double* p = G.p;
+  switch (G.kind) {
+    case IIM_GEOM_CIRCLE: return 1.0 / p[2];
+    case IIM_GEOM_SPHERE: return 1.0 / p[3];
+    case IIM_GEOM_STAR: {
+      double th = atan2(x[1] - p[1], x[0] - p[0]);
+      double s = sin(p[4] * th + p[5]), c = cos(p[4] * th + p[5]);
+      double r = p[2] + p[3] * s, r1 = p[3] * p[4] * c, r2 = -p[3] * p[4] * p[4] * s;
+      double den = r * r + r1 * r1;
+      return fabs(r * r + 2 * r1 * r1 - r * r2) / (den * sqrt(den));
+    }
+    case IIM_GEOM_ELLIPSE: {
+      // kappa = t^T H t / |grad g| for the unit tangent t
+      double gr[2];
+      geom_grad_g(G, x, gr);
+      double gn = hypot(gr[0], gr[1]);
+      double t0 = -gr[1] / gn, t1 = gr[0] / gn;
+      double cs = cos(p[4]), sn = sin(p[4]);
+      double l0 = 2 / (p[2] * p[2]), l1 = 2 / (p[3] * p[3]);
+      // H = R diag(l0,l1) R^T, R = [[cs,-sn],[sn,cs]]
+      double u0 = cs * t0 + sn * t1, u1 = -sn * t0 + cs * t1;
+      return fabs(l0 * u0 * u0 + l1 * u1 * u1) / gn;
+    }
+    case IIM_GEOM_ELLIPSOID: {
+      double gr[3];
+      geom_grad_g(G, x, gr);
+      double gn = sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+      double n[3] = {gr[0] / gn, gr[1] / gn, gr[2] / gn};
+      // orthonormal tangent basis
+      double a[3];
+      if (fabs(n[0]) < 0.9) { a[0] = 1; a[1] = 0; a[2] = 0; } else { a[0] = 0; a[1] = 1; a[2] = 0; }
+      double d = a[0] * n[0] + a[1] * n[1] + a[2] * n[2];
+      double t1[3] = {a[0] - d * n[0], a[1] - d * n[1], a[2] - d * n[2]};
+      double l = sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+      t1[0] /= l; t1[1] /= l; t1[2] /= l;
+      double t2[3] = {n[1] * t1[2] - n[2] * t1[1], n[2] * t1[0] - n[0] * t1[2], n[0] * t1[1] - n[1] * t1[0]};
+      double H[3] = {2 / (p[3] * p[3]), 2 / (p[4] * p[4]), 2 / (p[5] * p[5])};
+      double s11 = 0, s12 = 0, s22 = 0;
+      for (int k = 0; k < 3; ++k) {
+        s11 += H[k] * t1[k] * t1[k];
+        s12 += H[k] * t1[k] * t2[k];
+        s22 += H[k] * t2[k] * t2[k];
+      }
+      s11 /= gn; s12 /= gn; s22 /= gn;
+      double m = 0.5 * (s11 + s22), dd = sqrt(0.25 * (s11 - s22) * (s11 - s22) + s12 * s12);
+      return fmax(fabs(m + dd), fabs(m - dd));
+    }
+  }
+  return 0.0;
+}
+
+// FP32 pre-check of the phase: returns +1 / -1 when the sign is certain, 0 otherwise
+__device__ inline int geom_phase_fast(const Geom& G, const double* x) {
+  if (G.kind != IIM_GEOM_STAR) return 0;
+  float dx = (float)(x[0] - G.p[0]), dy = (float)(x[1] - G.p[1]);
+  float rho = hypotf(dx, dy), th = atan2f(dy, dx);
+  float g = rho - ((float)G.p[2] + (float)G.p[3] * sinf((float)G.p[4] * th + (float)G.p[5]));
+  float margin = 1e-4f * (1.0f + (float)G.p[4]);
+  if (g > margin) return G.sign > 0 ? 1 : -1;
+  if (g < -margin) return G.sign > 0 ? -1 : 1;
+  return 0;
+}
+
+__device__ inline bool phase_plus_at(const Geom& G, const double* x) {
+  int f = geom_phase_fast(G, x);
+  if (f != 0) return f > 0;
+  return geom_phi(G, x) >= 0.0;
+}
+
+// Root of phi on the edge [x0, x0 + h e_ax]: safeguarded Newton with bisection.
+// Returns t in [0,1] (fraction of h from x0).
+__device__ inline double edge_root(const Geom& G, const double* x0, int ax, double h, int dim) {
+  double x[3] = {x0[0], x0[1], dim > 2 ? x0[2] : 0.0};
+  double lo = 0.0, hi = 1.0;
+  bool s_lo = geom_phi(G, x) >= 0.0;
+  double t = 0.5;
+  for (int it = 0; it < 200; ++it) {
+    x[ax] = x0[ax] + t * h;
+    double f = geom_phi(G, x);
+    bool s = f >= 0.0;
+    if (s == s_lo) lo = t; else hi = t;
+    if (hi - lo <= 4e-16) break;
+    double gr[3];
+    geom_grad_g(G, x, gr);
+    double df = G.sign * gr[ax] * h;
+    double tn = (df != 0.0) ? t - f / df : 0.5 * (lo + hi);
+    if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+    if (fabs(tn - t) <= 1e-17) { t = tn; break; }
+    t = tn;
+  }
+  return t < 0 ? 0 : (t > 1 ? 1 : t);
+}
+
+// --------------------------------------------------------------------------- small helpers
+__device__ inline double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ inline float warp_sumf(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ inline void set_status(int* st, int code) { atomicCAS(st, 0, code); }
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// launch accounting (every kernel launch of the library goes through IIM_LAUNCH)
+void note_launch();
+#define IIM_LAUNCH(kernel, grid, block, smem, stream, ...)                \
+  do {                                                                    \
+    kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);           \
+    ::iim::note_launch();                                                 \
+  } while (0)
+
+}  // namespace iim

@@ -1,0 +1,138 @@
+// Problem workspace and the entry points shared between the library's translation units.
+#pragma once
+
+#include "common.cuh"
+
+namespace iim {
+
+// ---------------------------------------------------------------------------- device views
+// Flat grid: node (i0, i1, i2) -> i0 + n i1 + n^2 i2.  Node coordinate x = -1 + (i + 1/2) h.
+struct GridView {
+  int dim, n;
+  int64_t N;
+  double h;
+};
+
+// One Shortley-Weller level (Sec. 3.1): aux[i] = -2 (not an unknown), -1 (regular
+// unknown: standard 2d+1 point stencil), k >= 0 (irregular unknown, row k of the table).
+// Table rows hold (diag, c[-x0], c[+x0], c[-x1], c[+x1], [c[-x2], c[+x2]]) of the
+// homogeneous SW operator scaled by 1/h^2.
+struct Level {
+  GridView g;
+  uint8_t* phase = nullptr;
+  int32_t* aux = nullptr;
+  int32_t* flag = nullptr;        // scratch for the irregular-node scan
+  int32_t* idx = nullptr;
+  int n_irr = 0, irr_cap = 0;
+  float* tab32 = nullptr;
+  double* tab64 = nullptr;
+  void* u = nullptr;              // level vectors, float or double by mg precision
+  void* f = nullptr;
+};
+
+struct SolverScalars;             // device-side FGMRES state (krylov.cu)
+
+struct Problem {
+  iim_problem_desc desc;
+  iim_options opt;
+  cudaStream_t stream = nullptr;
+  Geom geom;
+  GridView g;
+  int w = 0, q = 0, M = 0;        // stencil half width, fit degree, monomials
+  double a[2 * kMaxW + 1];        // centred stencil a_{-w..w}
+  int rcap = 0;                   // max least-squares rows per fit (excluding the control point)
+  int box_active = 0;
+  // fine grid
+  uint8_t* phase = nullptr;       // 1 = Omega+
+  // crossings / control points
+  int32_t* edge_flag = nullptr;   // [dim * N]
+  int32_t* edge_id = nullptr;     // [dim * N] exclusive scan -> crossing id of a cut edge
+  int K = 0, K_cap = 0;
+  int32_t* cr_axis = nullptr;
+  int32_t* cr_lo = nullptr;
+  uint8_t* cr_loplus = nullptr;
+  double* cr_t = nullptr;
+  double* cr_x = nullptr;         // [K][dim]
+  double* cr_n = nullptr;         // [K][dim]
+  double* cr_kappa = nullptr;
+  // fits: boundary problems one per crossing (Omega+ side); interface two (2c: +, 2c+1: -)
+  int nfit = 0, nfit_cap = 0;
+  int32_t* fit_R = nullptr;       // [nfit]
+  int32_t* fit_nodes = nullptr;   // [nfit][rcap]
+  double* fit_coef = nullptr;     // [nfit][w+1][rcap]
+  double* fit_cdat = nullptr;     // [nfit][w+1]
+  double* G = nullptr;            // [nfit][w] ghost values of the current apply
+  int* d_monos = nullptr;         // [M][dim] exponents
+  // affected nodes (nodes whose stencil meets a control point or the box)
+  int32_t* aff_flag = nullptr;    // [N]
+  int32_t* aff_idx = nullptr;     // [N]
+  int n_aff = 0, aff_cap = 0;
+  int32_t* aff_node = nullptr;    // [aff_cap]
+  int32_t* aff_fit = nullptr;     // [aff_cap][2 dim]: fit id, -1 none, -2 box
+  int32_t* aff_j = nullptr;       // [aff_cap][2 dim]: first out-of-phase offset jstar
+  double box_w[kMaxW][8];         // box ghost Lagrange weights: [k][0] face, [k][m] node m+1
+  // data (Eq. 12)
+  double* d_g = nullptr;          // [K] ubar or qbar
+  double* d_j0 = nullptr;
+  double* d_j1 = nullptr;
+  double* d_box = nullptr;        // [B]
+  int B = 0;
+  double* b = nullptr;            // right-hand side f - L_Gamma u_Gamma
+  // Krylov
+  double* V = nullptr;            // [(m+1)][Npad]
+  double* Z = nullptr;            // [m][Npad]
+  double* x = nullptr;
+  double* tmp = nullptr;
+  int64_t Npad = 0;
+  SolverScalars* sc = nullptr;    // device
+  double* partial = nullptr;      // [red_blocks][kMaxRestart + 4] reduction scratch
+  unsigned int* counter = nullptr;
+  int red_blocks = 0;
+  // multigrid
+  std::vector<Level> lv;
+  int coarse_nu = 0;              // unknowns on the coarsest level
+  int32_t* coarse_map = nullptr;  // [coarse_nu] node of each coarse unknown
+  double* coarse_lu64 = nullptr;  // [nu][nu] LU factors (row major), FP64
+  float* coarse_lu32 = nullptr;
+  int32_t* coarse_piv = nullptr;
+  // status and scratch
+  int* d_status = nullptr;
+  int* d_counts = nullptr;        // [8] device counters (K, n_aff, irregular counts, ...)
+  int* scan_scratch = nullptr;
+  int64_t scan_scratch_len = 0;
+  // CUDA graph of the solve
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  size_t bytes = 0;               // device bytes held
+  std::vector<void*> allocs;
+};
+
+// scan.cu
+int64_t scan_scratch_ints(int64_t len);
+void scan_exclusive(const int* in, int* out, int64_t len, int* total, int* scratch, cudaStream_t s);
+
+// setup.cu
+iim_status setup_geometry(Problem& P, bool size_only);
+iim_status setup_fits(Problem& P);
+iim_status setup_levels(Problem& P, bool size_only);
+
+// operator.cu
+void ho_apply(Problem& P, const double* u, double* w, bool with_data, cudaStream_t s);
+void compute_rhs(Problem& P, const double* f, cudaStream_t s);
+
+// multigrid.cu
+void mg_precondition(Problem& P, const double* v, const double* vscale, double* z, cudaStream_t s);
+void mg_coarse_factor(Problem& P, cudaStream_t s);
+
+// krylov.cu
+iim_status krylov_alloc(Problem& P);
+void krylov_enqueue_solve(Problem& P, double* x, bool graph_mode);
+iim_status krylov_build_graph(Problem& P, double* x);
+void krylov_read_info(Problem& P, iim_solve_info* info);
+
+// api.cu
+void* dev_alloc(Problem& P, size_t bytes);
+void set_error(const std::string& msg);
+
+}  // namespace iim

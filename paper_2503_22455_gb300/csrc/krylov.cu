@@ -1,0 +1,465 @@
+// Right-preconditioned flexible GMRES(m) with device-side control (paper Sec. 4.1).
+//
+// Per iteration j (all on the device, no host round trip):
+//   z_j = M(v_j)                 one SW multigrid V-cycle      (multigrid.cu)
+//   w   = L z_j                  the IIM operator              (operator.cu)
+//   h   = V^T w, |w|^2           one fused pass over v_0..v_j  (k_multidot)
+//   w  -= V h, |w|^2             one fused pass                (k_update)
+//   optional second pass when |w| dropped below |w_old|/sqrt(2)   (classical
+//   Gram-Schmidt with re-orthogonalisation)
+//   Givens rotation, Arnoldi residual estimate, flags         (k_arnoldi_step)
+// v_{j+1} is kept unnormalised; 1/|v_{j+1}| is applied inside the kernels that
+// read it.  Reductions are deterministic: per-block partials in a fixed grid,
+// summed in block order by the last block to finish.  Convergence is decided on
+// the true residual |b - A x| / |b| at every restart (x += Z y).
+// The whole solve is one CUDA graph: WHILE(not done) { IF(active) iteration 0;
+// ...; IF(active) iteration m-1; restart }, with the conditions set by kernels.
+#include "kernels.cuh"
+
+namespace iim {
+
+struct SolverScalars {
+  double H[(kMaxRestart + 1) * kMaxRestart];   // H[i + (kMaxRestart+1) * j]
+  double g[kMaxRestart + 1];
+  double cs[kMaxRestart], sn[kMaxRestart];
+  double y[kMaxRestart];
+  double inv_norm[kMaxRestart + 1];            // 1/|v_i| for the unnormalised basis
+  double hcol[kMaxRestart + 2];
+  double w2_old, w2;
+  double bnorm, relres, est;
+  int iters, restarts, k, active, done, converged, reorth_needed, breakdown;
+  int m, max_iter, graph_mode, reorth;
+  double tol;
+  cudaGraphConditionalHandle h_while;
+  cudaGraphConditionalHandle h_if[kMaxRestart];
+};
+
+constexpr int kRedThreads = 256;
+
+template <int NV>
+__device__ inline void block_reduce_store(double (&acc)[NV], double* partial, int stride) {
+  __shared__ double red[kRedThreads / 32][NV > 0 ? NV : 1];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double v = warp_sum(acc[k]);
+    if (lane == 0) red[wid][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0;
+    for (int w = 0; w < kRedThreads / 32; ++w) s += red[w][threadIdx.x];
+    partial[(size_t)blockIdx.x * stride + threadIdx.x] = s;
+  }
+}
+
+// returns true in exactly one thread block: the last one to finish (all partials visible)
+__device__ inline bool last_block(unsigned int* counter) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int t = atomicAdd(counter, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last;
+}
+
+__device__ inline void sum_partials(const double* partial, int nblocks, int stride, int nv, double* out) {
+  // fixed order: threads k < nv sum column k over the blocks
+  if (threadIdx.x < nv) {
+    double s = 0;
+    for (int b = 0; b < nblocks; ++b) s += partial[(size_t)b * stride + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+__device__ inline void set_cond(SolverScalars* S, cudaGraphConditionalHandle h, int v) {
+  if (S->graph_mode) cudaGraphSetConditional(h, v ? 1u : 0u);
+}
+
+// restart / start: V0 = b - Ax (Ax in ax), |V0|^2, |b|^2
+__global__ void __launch_bounds__(kRedThreads) k_residual(const double* __restrict__ b, const double* __restrict__ ax,
+                                                          double* __restrict__ v0, int64_t N, double* partial,
+                                                          unsigned int* counter, SolverScalars* S, int first,
+                                                          int* status) {
+  double acc[2] = {0.0, 0.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    double bi = b[i];
+    double r = bi - ax[i];
+    v0[i] = r;
+    acc[0] = fma(r, r, acc[0]);
+    acc[1] = fma(bi, bi, acc[1]);
+  }
+  block_reduce_store<2>(acc, partial, 4);
+  if (!last_block(counter)) return;
+  __shared__ double tot[4];
+  sum_partials(partial, gridDim.x, 4, 2, tot);
+  if (threadIdx.x == 0) {
+    *counter = 0;
+    double rn = sqrt(tot[0]);
+    if (first) {
+      S->bnorm = sqrt(tot[1]);
+      S->iters = 0;
+      S->restarts = 0;
+      S->done = 0;
+      S->converged = 0;
+      S->breakdown = 0;
+    } else {
+      S->restarts += 1;
+    }
+    double bn = S->bnorm;
+    double rel = bn > 0 ? rn / bn : 0.0;
+    S->relres = rel;
+    bool bad = !(rn == rn) || isinf(rn);
+    if (bad) {
+      set_status(status, IIM_ERR_BREAKDOWN);
+      S->done = 1;
+    } else if (bn == 0.0 || rel <= S->tol) {
+      S->done = 1;
+      S->converged = 1;
+    } else if (S->iters >= S->max_iter) {
+      S->done = 1;
+    }
+    S->g[0] = rn;
+    for (int k = 1; k <= kMaxRestart; ++k) S->g[k] = 0.0;
+    S->inv_norm[0] = rn > 0 ? 1.0 / rn : 0.0;
+    S->k = 0;
+    S->active = !S->done;
+    set_cond(S, S->h_while, !S->done);
+    for (int k = 0; k < S->m; ++k) set_cond(S, S->h_if[k], k == 0 ? S->active : 0);
+  }
+}
+
+// h_i = inv_norm_i <V_i, w> (i <= j), |w|^2 ; w = V[j+1]
+template <int NV>
+__global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restrict__ V, int64_t Np, int j,
+                                                          double* partial, unsigned int* counter, SolverScalars* S,
+                                                          int second) {
+  if (second && !S->reorth_needed) return;
+  const double* w = V + (size_t)(j + 1) * Np;
+  double acc[NV + 1];
+#pragma unroll
+  for (int k = 0; k <= NV; ++k) acc[k] = 0.0;
+  const int64_t N2 = Np / 2;
+  const double2* w2 = reinterpret_cast<const double2*>(w);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N2; e += (int64_t)gridDim.x * blockDim.x) {
+    double2 wv = w2[e];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double2 vv = reinterpret_cast<const double2*>(V + (size_t)k * Np)[e];
+      acc[k] = fma(vv.x, wv.x, acc[k]);
+      acc[k] = fma(vv.y, wv.y, acc[k]);
+    }
+    acc[NV] = fma(wv.x, wv.x, acc[NV]);
+    acc[NV] = fma(wv.y, wv.y, acc[NV]);
+  }
+  block_reduce_store<NV + 1>(acc, partial, kMaxRestart + 4);
+  if (!last_block(counter)) return;
+  __shared__ double tot[kMaxRestart + 4];
+  sum_partials(partial, gridDim.x, kMaxRestart + 4, NV + 1, tot);
+  if (threadIdx.x == 0) {
+    *counter = 0;
+    if (!second) {
+      for (int k = 0; k < NV; ++k) S->hcol[k] = tot[k] * S->inv_norm[k];
+      S->w2_old = tot[NV];
+    } else {
+      // second pass: store the correction in y[] temporarily
+      for (int k = 0; k < NV; ++k) S->y[k] = tot[k] * S->inv_norm[k];
+    }
+  }
+}
+
+// w -= sum_i c_i V_i with c_i = h_i inv_norm_i ; |w|^2
+template <int NV>
+__global__ void __launch_bounds__(kRedThreads) k_update(double* __restrict__ V, int64_t Np, int j, double* partial,
+                                                        unsigned int* counter, SolverScalars* S, int second) {
+  if (second && !S->reorth_needed) return;
+  __shared__ double c[NV];
+  if (threadIdx.x < NV) c[threadIdx.x] = (second ? S->y[threadIdx.x] : S->hcol[threadIdx.x]) * S->inv_norm[threadIdx.x];
+  __syncthreads();
+  double* w = V + (size_t)(j + 1) * Np;
+  double acc[1] = {0.0};
+  const int64_t N2 = Np / 2;
+  double2* w2 = reinterpret_cast<double2*>(w);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N2; e += (int64_t)gridDim.x * blockDim.x) {
+    double2 wv = w2[e];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double2 vv = reinterpret_cast<const double2*>(V + (size_t)k * Np)[e];
+      wv.x = fma(-c[k], vv.x, wv.x);
+      wv.y = fma(-c[k], vv.y, wv.y);
+    }
+    w2[e] = wv;
+    acc[0] = fma(wv.x, wv.x, acc[0]);
+    acc[0] = fma(wv.y, wv.y, acc[0]);
+  }
+  block_reduce_store<1>(acc, partial, kMaxRestart + 4);
+  if (!last_block(counter)) return;
+  __shared__ double tot[kMaxRestart + 4];
+  sum_partials(partial, gridDim.x, kMaxRestart + 4, 1, tot);
+  if (threadIdx.x == 0) {
+    *counter = 0;
+    S->w2 = tot[0];
+    if (!second) {
+      S->reorth_needed = S->reorth && (tot[0] < 0.5 * S->w2_old);
+    } else {
+      for (int k = 0; k < NV; ++k) S->hcol[k] += S->y[k];
+      S->reorth_needed = 0;
+    }
+  }
+}
+
+// Givens rotations on column j, estimate, flags (one thread)
+__global__ void k_arnoldi_step(SolverScalars* S, int j, int* status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int L = kMaxRestart + 1;
+  double* H = S->H;
+  for (int i = 0; i <= j; ++i) H[i + L * j] = S->hcol[i];
+  double hn = sqrt(S->w2);
+  H[j + 1 + L * j] = hn;
+  S->inv_norm[j + 1] = hn > 0 ? 1.0 / hn : 0.0;
+  for (int i = 0; i < j; ++i) {
+    double a = H[i + L * j], b = H[i + 1 + L * j];
+    H[i + L * j] = S->cs[i] * a + S->sn[i] * b;
+    H[i + 1 + L * j] = -S->sn[i] * a + S->cs[i] * b;
+  }
+  double a = H[j + L * j], b = H[j + 1 + L * j];
+  double den = hypot(a, b);
+  double cs = den > 0 ? a / den : 1.0, sn = den > 0 ? b / den : 0.0;
+  S->cs[j] = cs;
+  S->sn[j] = sn;
+  H[j + L * j] = den;
+  H[j + 1 + L * j] = 0.0;
+  S->g[j + 1] = -sn * S->g[j];
+  S->g[j] = cs * S->g[j];
+  S->iters += 1;
+  S->k = j + 1;
+  double est = S->bnorm > 0 ? fabs(S->g[j + 1]) / S->bnorm : 0.0;
+  S->est = est;
+  bool bad = !(est == est) || !(hn == hn) || isinf(hn);
+  if (bad) {
+    set_status(status, IIM_ERR_BREAKDOWN);
+    S->breakdown = 1;
+  }
+  bool stop = bad || hn == 0.0 || est <= S->tol || S->iters >= S->max_iter || j + 1 >= S->m;
+  S->active = !stop;
+  if (j + 1 < S->m) set_cond(S, S->h_if[j + 1], !stop);
+}
+
+// y = H^-1 g (k x k upper triangular)
+__global__ void k_solve_y(SolverScalars* S) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int L = kMaxRestart + 1, k = S->k;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = S->g[i];
+    for (int c = i + 1; c < k; ++c) s -= S->H[i + L * c] * S->y[c];
+    double d = S->H[i + L * i];
+    S->y[i] = d != 0.0 ? s / d : 0.0;
+  }
+  for (int i = k; i < kMaxRestart; ++i) S->y[i] = 0.0;
+}
+
+// x += sum_{i<k} y_i Z_i
+__global__ void __launch_bounds__(256) k_xupdate(double* __restrict__ x, const double* __restrict__ Z, int64_t Np,
+                                                 int64_t N, const SolverScalars* S) {
+  __shared__ double y[kMaxRestart];
+  __shared__ int k;
+  if (threadIdx.x < kMaxRestart) y[threadIdx.x] = S->y[threadIdx.x];
+  if (threadIdx.x == 0) k = S->k;
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = x[i];
+    for (int c = 0; c < k; ++c) acc = fma(y[c], Z[(size_t)c * Np + i], acc);
+    x[i] = acc;
+  }
+}
+
+__global__ void k_init_scalars(SolverScalars* S, int m, int max_iter, double tol, int graph_mode, int reorth) {
+  S->m = m;
+  S->max_iter = max_iter;
+  S->tol = tol;
+  S->graph_mode = graph_mode;
+  S->reorth = reorth;
+  S->reorth_needed = 0;
+  S->k = 0;
+}
+
+__global__ void k_set_handles(SolverScalars* S, cudaGraphConditionalHandle hw, cudaGraphConditionalHandle* hif, int m) {
+  S->h_while = hw;
+  for (int k = 0; k < m; ++k) S->h_if[k] = hif[k];
+}
+
+// ---------------------------------------------------------------------------- host side
+iim_status krylov_alloc(Problem& P) {
+  P.Npad = ((P.g.N + 63) / 64) * 64;
+  const int m = P.opt.restart;
+  P.V = (double*)dev_alloc(P, sizeof(double) * (size_t)(m + 1) * P.Npad);
+  P.Z = (double*)dev_alloc(P, sizeof(double) * (size_t)m * P.Npad);
+  P.x = (double*)dev_alloc(P, sizeof(double) * P.Npad);
+  P.tmp = (double*)dev_alloc(P, sizeof(double) * P.Npad);
+  P.sc = (SolverScalars*)dev_alloc(P, sizeof(SolverScalars));
+  P.red_blocks = 2 * kNumSMs;
+  P.partial = (double*)dev_alloc(P, sizeof(double) * (size_t)P.red_blocks * (kMaxRestart + 4));
+  P.counter = (unsigned int*)dev_alloc(P, sizeof(unsigned int) * 4);
+  if (!P.V || !P.Z || !P.x || !P.tmp || !P.sc || !P.partial || !P.counter) return IIM_ERR_BUDGET;
+  cudaMemsetAsync(P.V, 0, sizeof(double) * (size_t)(m + 1) * P.Npad, P.stream);
+  cudaMemsetAsync(P.Z, 0, sizeof(double) * (size_t)m * P.Npad, P.stream);
+  cudaMemsetAsync(P.x, 0, sizeof(double) * P.Npad, P.stream);
+  cudaMemsetAsync(P.tmp, 0, sizeof(double) * P.Npad, P.stream);
+  cudaMemsetAsync(P.counter, 0, sizeof(unsigned int) * 4, P.stream);
+  return IIM_OK;
+}
+
+template <int NV>
+static void launch_orth(Problem& P, int j, cudaStream_t s, int second) {
+  IIM_LAUNCH(k_multidot<NV>, P.red_blocks, kRedThreads, 0, s, P.V, P.Npad, j, P.partial, P.counter, P.sc, second);
+  IIM_LAUNCH(k_update<NV>, P.red_blocks, kRedThreads, 0, s, P.V, P.Npad, j, P.partial, P.counter, P.sc, second);
+}
+
+static void orth(Problem& P, int j, cudaStream_t s, int second) {
+  switch (j + 1) {
+#define IIM_CASE(k) case k: launch_orth<k>(P, j, s, second); break;
+    IIM_CASE(1) IIM_CASE(2) IIM_CASE(3) IIM_CASE(4) IIM_CASE(5) IIM_CASE(6) IIM_CASE(7) IIM_CASE(8)
+    IIM_CASE(9) IIM_CASE(10) IIM_CASE(11) IIM_CASE(12) IIM_CASE(13) IIM_CASE(14) IIM_CASE(15) IIM_CASE(16)
+#undef IIM_CASE
+  }
+}
+
+static void enqueue_iteration(Problem& P, int j, cudaStream_t s) {
+  double* vj = P.V + (size_t)j * P.Npad;
+  double* zj = P.Z + (size_t)j * P.Npad;
+  double* w = P.V + (size_t)(j + 1) * P.Npad;
+  mg_precondition(P, vj, &P.sc->inv_norm[j], zj, s);
+  ho_apply(P, zj, w, false, s);
+  orth(P, j, s, 0);
+  if (P.opt.reorth) orth(P, j, s, 1);
+  IIM_LAUNCH(k_arnoldi_step, 1, 32, 0, s, P.sc, j, P.d_status);
+}
+
+static void enqueue_restart(Problem& P, cudaStream_t s) {
+  IIM_LAUNCH(k_solve_y, 1, 32, 0, s, P.sc);
+  IIM_LAUNCH(k_xupdate, 4 * kNumSMs, 256, 0, s, P.x, P.Z, P.Npad, P.g.N, P.sc);
+  ho_apply(P, P.x, P.tmp, false, s);
+  IIM_LAUNCH(k_residual, P.red_blocks, kRedThreads, 0, s, P.b, P.tmp, P.V, P.g.N, P.partial, P.counter, P.sc, 0,
+             P.d_status);
+}
+
+static void enqueue_start(Problem& P, cudaStream_t s, int graph_mode) {
+  IIM_LAUNCH(k_init_scalars, 1, 1, 0, s, P.sc, P.opt.restart, P.opt.max_iter, P.opt.tol, graph_mode, P.opt.reorth);
+  ho_apply(P, P.x, P.tmp, false, s);
+  IIM_LAUNCH(k_residual, P.red_blocks, kRedThreads, 0, s, P.b, P.tmp, P.V, P.g.N, P.partial, P.counter, P.sc, 1,
+             P.d_status);
+}
+
+struct HostFlags {
+  int active, done;
+};
+
+// host-driven loop (one synchronisation per iteration); used when graphs are off
+void krylov_enqueue_solve(Problem& P, double* x, bool graph_mode) {
+  cudaStream_t s = P.stream;
+  (void)x;
+  enqueue_start(P, s, 0);
+  SolverScalars h;
+  for (;;) {
+    cudaMemcpyAsync(&h, P.sc, sizeof(SolverScalars), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    if (h.done) break;
+    for (int j = 0; j < P.opt.restart; ++j) {
+      enqueue_iteration(P, j, s);
+      cudaMemcpyAsync(&h, P.sc, sizeof(SolverScalars), cudaMemcpyDeviceToHost, s);
+      cudaStreamSynchronize(s);
+      if (!h.active) break;
+    }
+    enqueue_restart(P, s);
+  }
+}
+
+static cudaGraphNode_t add_conditional(cudaGraph_t g, cudaStream_t s, cudaGraphConditionalHandle h,
+                                       cudaGraphConditionalNodeType type, cudaGraph_t* body) {
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaStreamCaptureStatus st;
+  cudaStreamGetCaptureInfo(s, &st, nullptr, nullptr, &deps, nullptr, &ndeps);
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = type;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp);
+  cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+  *body = cp.conditional.phGraph_out[0];
+  return node;
+}
+
+// Build the solve graph once per problem.  The solve reads and writes P.x.
+iim_status krylov_build_graph(Problem& P, double* x) {
+  (void)x;
+  cudaStream_t s;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return IIM_ERR_CUDA;
+  cudaGraph_t g;
+  cudaGraphCreate(&g, 0);
+  cudaGraphConditionalHandle hw;
+  cudaGraphConditionalHandleCreate(&hw, g, 0, 0);
+  const int m = P.opt.restart;
+  cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  enqueue_start(P, s, 1);
+  cudaGraph_t body;
+  add_conditional(g, s, hw, cudaGraphCondTypeWhile, &body);
+  cudaStreamEndCapture(s, &g);
+  std::vector<cudaGraphConditionalHandle> hif(m);
+  for (int j = 0; j < m; ++j) cudaGraphConditionalHandleCreate(&hif[j], body, 0, 0);
+  cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  std::vector<cudaGraph_t> ibody(m);
+  for (int j = 0; j < m; ++j) add_conditional(body, s, hif[j], cudaGraphCondTypeIf, &ibody[j]);
+  enqueue_restart(P, s);
+  cudaStreamEndCapture(s, &body);
+  for (int j = 0; j < m; ++j) {
+    cudaStreamBeginCaptureToGraph(s, ibody[j], nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    enqueue_iteration(P, j, s);
+    cudaStreamEndCapture(s, &ibody[j]);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("graph capture: ") + cudaGetErrorString(e));
+    cudaStreamDestroy(s);
+    return IIM_ERR_CUDA;
+  }
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(s);
+    return IIM_ERR_CUDA;
+  }
+  // the handles live in the solver scalars so that kernels can set them
+  cudaGraphConditionalHandle* dh = nullptr;
+  cudaMalloc(&dh, sizeof(cudaGraphConditionalHandle) * m);
+  cudaMemcpy(dh, hif.data(), sizeof(cudaGraphConditionalHandle) * m, cudaMemcpyHostToDevice);
+  k_set_handles<<<1, 1, 0, s>>>(P.sc, hw, dh, m);
+  note_launch();
+  cudaStreamSynchronize(s);
+  cudaFree(dh);
+  e = cudaGraphInstantiate(&P.graph_exec, g, 0);
+  cudaStreamDestroy(s);
+  P.graph = g;
+  if (e != cudaSuccess) {
+    set_error(std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return IIM_ERR_CUDA;
+  }
+  return IIM_OK;
+}
+
+void krylov_read_info(Problem& P, iim_solve_info* info) {
+  SolverScalars h;
+  cudaMemcpy(&h, P.sc, sizeof(SolverScalars), cudaMemcpyDeviceToHost);
+  if (!info) return;
+  info->iters = h.iters;
+  info->restarts = h.restarts;
+  info->converged = h.converged;
+  info->relres = h.relres;
+}
+
+}  // namespace iim

@@ -1,0 +1,301 @@
+// The (n, n+1) IIM operator w = L_Omega u (+ L_Gamma u_Gamma), paper Sec. 2.3, Eq. 12.
+//
+// Split into three kernels:
+//   k_ho_stencil  every unknown node: beta_sigma/h^2 sum_axes sum_j a_j u_{i+j e}, where
+//                 neighbours outside phase sigma (or outside the box) contribute 0;
+//   k_ho_ghost    one warp per control point: u_c (Dirichlet data, Neumann elimination
+//                 Eqs. 5-6, or the interface closure Eqs. 9-11) and the w ghost values
+//                 p_c(x_g) = s_c u_c + sum s_a u_a of Eq. 4;
+//   k_ho_correct  one thread per affected node: adds a_j p_c(x_{i+j e}) for every
+//                 out-of-phase offset past the first control point of each walk, and
+//                 the outer-box ghosts.
+// The stencil is FP64 and bound by the FP64 pipe on GB300 (2 FMA/clk/SM), so it
+// is written to use the fewest FP64 operations: neighbours at equal |j| are
+// summed first, then one FMA per |j| with beta/h^2 folded into the coefficients.
+#include "kernels.cuh"
+
+namespace iim {
+
+struct StencilCoef {
+  double c0[2];            // d * a_0 * beta_sigma / h^2 for sigma = minus, plus
+  double cj[2][kMaxW];     // a_j * beta_sigma / h^2
+};
+
+template <int D, int W>
+__global__ void __launch_bounds__(256) k_ho_stencil(GridView g, StencilCoef C, int interface_,
+                                                    const double* __restrict__ u,
+                                                    const uint8_t* __restrict__ phase, double* __restrict__ w) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.N) return;
+  const int n = g.n;
+  const uint8_t ph = phase[i];
+  if (!interface_ && !ph) { w[i] = 0.0; return; }
+  int m[3];
+  m[0] = (int)(i % n);
+  int64_t r = i / n;
+  m[1] = (int)(r % n);
+  m[2] = D > 2 ? (int)(r / n) : 0;
+  const int sig = ph ? 1 : 0;
+  double acc = C.c0[sig] * u[i];
+#pragma unroll
+  for (int j = 1; j <= W; ++j) {
+    double s = 0.0;
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax) {
+      const int64_t st = ax == 0 ? 1 : (ax == 1 ? (int64_t)n : (int64_t)n * n);
+      if (m[ax] - j >= 0) {
+        int64_t nb = i - j * st;
+        double v = u[nb];
+        s += phase[nb] == ph ? v : 0.0;
+      }
+      if (m[ax] + j < n) {
+        int64_t nb = i + j * st;
+        double v = u[nb];
+        s += phase[nb] == ph ? v : 0.0;
+      }
+    }
+    acc = fma(C.cj[sig][j - 1], s, acc);
+  }
+  w[i] = acc;
+}
+
+struct GhostParams {
+  int nfit, w, rcap, bc, interface_, with_data;
+  double beta_p, beta_m;
+  const int* K;
+  const int32_t* fit_R;
+  const int32_t* fit_nodes;
+  const double* fit_coef;
+  const double* fit_cdat;
+  const double* g;          // ubar / qbar per control point
+  const double* j0;
+  const double* j1;
+  double* G;                // [nfit][w]
+};
+
+// one warp per crossing (interface: both sides) or per fit (boundary problems)
+__global__ void __launch_bounds__(256) k_ho_ghost(GhostParams P, const double* __restrict__ u) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  const int K = *P.K;
+  const int rows = P.w + 1;
+  if (!P.interface_) {
+    if (warp >= K) return;
+    const int f = warp;
+    const int R = P.fit_R[f];
+    const int32_t* nodes = P.fit_nodes + (size_t)f * P.rcap;
+    const double* coef = P.fit_coef + (size_t)f * rows * P.rcap;
+    double acc[kMaxW];
+#pragma unroll
+    for (int k = 0; k < kMaxW; ++k) acc[k] = 0.0;
+    for (int a = lane; a < R; a += 32) {
+      double ua = u[nodes[a]];
+#pragma unroll
+      for (int k = 0; k < kMaxW; ++k)
+        if (k < P.w) acc[k] = fma(coef[(size_t)k * P.rcap + a], ua, acc[k]);
+    }
+    const double data = P.with_data ? P.g[f] : 0.0;
+#pragma unroll
+    for (int k = 0; k < kMaxW; ++k) {
+      if (k >= P.w) break;
+      double v = warp_sum(acc[k]);
+      if (lane == 0) P.G[(size_t)f * P.w + k] = v + P.fit_cdat[(size_t)f * rows + k] * data;
+    }
+    return;
+  }
+  if (warp >= K) return;
+  const int c = warp;
+  double accs[2][kMaxW + 1];
+#pragma unroll
+  for (int sd = 0; sd < 2; ++sd) {
+    const int f = 2 * c + sd;
+    const int R = P.fit_R[f];
+    const int32_t* nodes = P.fit_nodes + (size_t)f * P.rcap;
+    const double* coef = P.fit_coef + (size_t)f * rows * P.rcap;
+#pragma unroll
+    for (int k = 0; k <= kMaxW; ++k) accs[sd][k] = 0.0;
+    for (int a = lane; a < R; a += 32) {
+      double ua = u[nodes[a]];
+#pragma unroll
+      for (int k = 0; k <= kMaxW; ++k)
+        if (k <= P.w) accs[sd][k] = fma(coef[(size_t)k * P.rcap + a], ua, accs[sd][k]);
+    }
+#pragma unroll
+    for (int k = 0; k <= kMaxW; ++k) accs[sd][k] = warp_sum(accs[sd][k]);
+  }
+  // Eqs. 9-11: S = b+ s+_c - b- s-_c ; ubar = -(b+ D+ - b- D-)/S
+  const double *cp = P.fit_cdat + (size_t)(2 * c) * rows, *cm = P.fit_cdat + (size_t)(2 * c + 1) * rows;
+  const double bp = P.beta_p, bm = P.beta_m;
+  const double Sden = bp * cp[P.w] - bm * cm[P.w];
+  const double Dp = accs[0][P.w], Dm = accs[1][P.w];
+  const double ubar = -(bp * Dp - bm * Dm) / Sden;
+  double up = ubar, um = ubar;
+  if (P.with_data) {
+    up = ubar + (P.j1[c] - bm * cm[P.w] * P.j0[c]) / Sden;
+    um = ubar + (P.j1[c] - bp * cp[P.w] * P.j0[c]) / Sden;
+  }
+  if (lane < P.w) {
+    int k = lane;
+    double gp = 0, gm = 0;
+#pragma unroll
+    for (int kk = 0; kk < kMaxW; ++kk)
+      if (kk == k) { gp = accs[0][kk]; gm = accs[1][kk]; }
+    P.G[(size_t)(2 * c) * P.w + k] = gp + cp[k] * up;
+    P.G[(size_t)(2 * c + 1) * P.w + k] = gm + cm[k] * um;
+  }
+}
+
+struct CorrectParams {
+  GridView g;
+  int w, q, with_data, n_aff_cap, nfit_cap;
+  const int* n_aff;
+  const int32_t* aff_node;
+  const int32_t* aff_fit;
+  const int32_t* aff_j;
+  const double* G;
+  const uint8_t* phase;
+  const double* box;        // [B] face data
+  double a[2 * kMaxW + 1];
+  double scale[2];          // beta_sigma / h^2
+  double box_w[kMaxW][8];
+};
+
+__global__ void __launch_bounds__(256) k_ho_correct(CorrectParams P, const double* __restrict__ u,
+                                                    double* __restrict__ w) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= *P.n_aff || t >= P.n_aff_cap) return;
+  const GridView& g = P.g;
+  const int n = g.n, d = g.dim, W = P.w;
+  const int64_t i = P.aff_node[t];
+  int m[3];
+  m[0] = (int)(i % n);
+  int64_t r = i / n;
+  m[1] = (int)(r % n);
+  m[2] = d > 2 ? (int)(r / n) : 0;
+  const uint8_t ph = P.phase[i];
+  double acc = 0.0;
+  for (int ax = 0; ax < d; ++ax) {
+    const int64_t st = ax == 0 ? 1 : (ax == 1 ? (int64_t)n : (int64_t)n * n);
+    for (int sd = 0; sd < 2; ++sd) {
+      const int s = sd ? 1 : -1;
+      const int fit = P.aff_fit[t * 2 * d + 2 * ax + sd];
+      const int js = P.aff_j[t * 2 * d + 2 * ax + sd];
+      if (fit == -1 || fit >= P.nfit_cap) continue;
+      if (fit >= 0) {
+        for (int j = js; j <= W; ++j) {
+          int pos = m[ax] + j * s;
+          if (pos >= 0 && pos < n && P.phase[i + j * s * st] == ph) continue;   // back in phase: uses u
+          acc = fma(P.a[W + j * s], P.G[(size_t)fit * W + (j - js)], acc);
+        }
+      } else {
+        // outer box: ghosts from the degree-q line polynomial through the face value and
+        // the nodes 2..q+1 counted from the face
+        double face = 0.0;
+        if (P.with_data) {
+          int64_t off = 0, mul = 1;
+          for (int k = 0; k < d; ++k) {
+            if (k == ax) continue;
+            off += m[k] * mul;
+            mul *= n;
+          }
+          off += (int64_t)(2 * ax + sd) * mul;
+          face = P.box[off];
+        }
+        for (int j = js; j <= W; ++j) {
+          const int k = j - js;                  // ghost k+1 beyond the face
+          double v = P.box_w[k][0] * face;
+          for (int mm = 2; mm <= P.q + 1; ++mm) {
+            int pos = s > 0 ? n - mm : mm - 1;
+            v = fma(P.box_w[k][mm - 1], u[i + (int64_t)(pos - m[ax]) * st], v);
+          }
+          acc = fma(P.a[W + j * s], v, acc);
+        }
+      }
+    }
+  }
+  w[i] += P.scale[ph ? 1 : 0] * acc;
+}
+
+static StencilCoef stencil_coef(const Problem& P) {
+  StencilCoef C;
+  const double h2 = P.g.h * P.g.h;
+  const double beta[2] = {P.desc.beta_minus, P.desc.beta_plus};
+  for (int s = 0; s < 2; ++s) {
+    C.c0[s] = P.g.dim * P.a[P.w] * beta[s] / h2;
+    for (int j = 1; j <= kMaxW; ++j) C.cj[s][j - 1] = j <= P.w ? P.a[P.w + j] * beta[s] / h2 : 0.0;
+  }
+  return C;
+}
+
+void ho_apply(Problem& P, const double* u, double* w, bool with_data, cudaStream_t s) {
+  const GridView& g = P.g;
+  const int T = 256;
+  const int iface = P.desc.bc == IIM_BC_INTERFACE;
+  StencilCoef C = stencil_coef(P);
+  int grid = ceil_div(g.N, T);
+  if (g.dim == 2) {
+    if (P.w == 2) IIM_LAUNCH((k_ho_stencil<2, 2>), grid, T, 0, s, g, C, iface, u, P.phase, w);
+    else IIM_LAUNCH((k_ho_stencil<2, 3>), grid, T, 0, s, g, C, iface, u, P.phase, w);
+  } else {
+    if (P.w == 2) IIM_LAUNCH((k_ho_stencil<3, 2>), grid, T, 0, s, g, C, iface, u, P.phase, w);
+    else IIM_LAUNCH((k_ho_stencil<3, 3>), grid, T, 0, s, g, C, iface, u, P.phase, w);
+  }
+  GhostParams GP;
+  GP.nfit = P.nfit_cap;
+  GP.w = P.w;
+  GP.rcap = P.rcap;
+  GP.bc = P.desc.bc;
+  GP.interface_ = iface;
+  GP.with_data = with_data;
+  GP.beta_p = P.desc.beta_plus;
+  GP.beta_m = P.desc.beta_minus;
+  GP.K = P.d_counts + 0;
+  GP.fit_R = P.fit_R;
+  GP.fit_nodes = P.fit_nodes;
+  GP.fit_coef = P.fit_coef;
+  GP.fit_cdat = P.fit_cdat;
+  GP.g = P.d_g;
+  GP.j0 = P.d_j0;
+  GP.j1 = P.d_j1;
+  GP.G = P.G;
+  if (P.K_cap > 0) IIM_LAUNCH(k_ho_ghost, ceil_div((int64_t)P.K_cap * 32, T), T, 0, s, GP, u);
+  CorrectParams CP;
+  CP.g = g;
+  CP.w = P.w;
+  CP.q = P.q;
+  CP.with_data = with_data;
+  CP.n_aff_cap = P.aff_cap;
+  CP.nfit_cap = P.nfit_cap;
+  CP.n_aff = P.d_counts + 1;
+  CP.aff_node = P.aff_node;
+  CP.aff_fit = P.aff_fit;
+  CP.aff_j = P.aff_j;
+  CP.G = P.G;
+  CP.phase = P.phase;
+  CP.box = P.d_box;
+  for (int k = 0; k < 2 * kMaxW + 1; ++k) CP.a[k] = k < 2 * P.w + 1 ? P.a[k] : 0.0;
+  const double h2 = g.h * g.h;
+  CP.scale[0] = P.desc.beta_minus / h2;
+  CP.scale[1] = P.desc.beta_plus / h2;
+  for (int k = 0; k < kMaxW; ++k)
+    for (int mm = 0; mm < 8; ++mm) CP.box_w[k][mm] = P.box_w[k][mm];
+  if (P.aff_cap > 0) IIM_LAUNCH(k_ho_correct, ceil_div(P.aff_cap, T), T, 0, s, CP, u, w);
+}
+
+__global__ void k_rhs_finish(GridView g, int interface_, const uint8_t* __restrict__ phase,
+                             const double* __restrict__ f, const double* __restrict__ lg, double* __restrict__ b) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.N) return;
+  b[i] = (interface_ || phase[i]) ? f[i] - lg[i] : 0.0;
+}
+
+// b = f - L_Gamma u_Gamma: the operator applied to u = 0 with the data switched on
+void compute_rhs(Problem& P, const double* f, cudaStream_t s) {
+  double* zero = P.Z;                  // Z[0] is zeroed first: the apply reads it as u
+  double* lg = P.tmp;
+  cudaMemsetAsync(zero, 0, sizeof(double) * P.g.N, s);
+  ho_apply(P, zero, lg, true, s);
+  IIM_LAUNCH(k_rhs_finish, ceil_div(P.g.N, 256), 256, 0, s, P.g, P.desc.bc == IIM_BC_INTERFACE, P.phase, f, lg, P.b);
+}
+
+}  // namespace iim

@@ -6,8 +6,8 @@
   any polynomial P of degree <= q (piecewise for interfaces);
 * L 1 = 0 for a pure Neumann problem (Sec. 2.3);
 * truncation error of order k-2 at the affected points (Sec. 2.4, Fig. 2);
-* the closed form of the interface values (Eqs. 12-13) against a direct
-  solve of the discrete jump system (Eq. 11);
+* the closed form of the interface values (Eqs. 10-11) against a direct
+  solve of the discrete jump system (Eq. 9);
 * the spectrum bounds of Sec. 2.5.
 """
 import os
@@ -78,7 +78,7 @@ def test_pure_neumann_operator_annihilates_constants():
 
 
 def test_interface_closed_form_matches_jump_system():
-    """Eqs. 12-13 equal the solution of the discrete jump system of Eq. 11 with [u] = j0."""
+    """Eqs. 10-11 equal the solution of the discrete jump system of Eq. 9 with [u] = j0."""
     spec = W.star_interface_1024(128)
     spec.beta_plus, spec.beta_minus = 0.5, 1.7
     op = IIMOperator(spec)

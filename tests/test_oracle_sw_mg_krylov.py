@@ -1,7 +1,7 @@
 """Oracle pins for the preconditioner (Sec. 3) and the Krylov solver (Sec. 4.1).
 
-* every 1D Shortley-Weller formula (Eqs. 12-13) is exact on quadratics, the
-  defining property stated in Sec. 3.1; the interface wall values (Eq. 15)
+* every 1D Shortley-Weller formula (Eqs. 18-19) is exact on quadratics, the
+  defining property stated in Sec. 3.1; the interface wall values (Eq. 21)
   reproduce piecewise-linear flux-continuous functions exactly;
 * the V-cycle iterated as a solver converges to the sparse direct solution of
   the SW system (Sec. 3.3) and contracts fast for Dirichlet;
@@ -61,7 +61,7 @@ def test_sw_neumann_b_printed_form_is_not_exact():
 
 @pytest.mark.parametrize("trial", range(10))
 def test_sw_interface_walls_solve_the_discrete_jump_conditions(trial):
-    """Eq. 15 returns wall values with uw+ - uw- = [u] and the flux balance of Eq. 14."""
+    """Eq. 21 returns wall values with uw+ - uw- = [u] and the flux balance of Eq. 20."""
     bm, bp = RNG.uniform(0.1, 5, size=2)
     pm, pp = RNG.uniform(0.1, 0.9, size=2)
     dx = RNG.uniform(0.01, 0.2)

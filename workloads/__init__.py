@@ -5,7 +5,7 @@ solutions that generate their data (source term, boundary values, jumps).
 It contains none of the solver's arithmetic: no crossings, no fits, no
 stencils.  Both sides evaluate the data below at the points *they* computed.
 
-Problem statement (paper Sec. 2.1, Eq. 1 and Sec. 2.2, Eq. 5):
+Problem statement (paper Sec. 2.1, Eq. 1 and Sec. 2.2, Eq. 8):
   div(beta grad u) = f  in Omega,   u = ubar on Gamma_D,
   beta du/dn = qbar on Gamma_N,     [u] = j0, [beta du/dn] = j1 on Gamma_M,
 with n pointing out of Omega+ (towards Omega-), [.] = (+ side) - (- side).
