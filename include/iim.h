@@ -101,6 +101,7 @@ typedef struct {
   int converged;
   double relres;         /* final true relative residual */
   double solve_ms;       /* device time of the solve */
+  int64_t kernels;       /* kernels this solve executed on the device */
 } iim_solve_info;
 
 typedef struct iim_problem iim_problem;
@@ -168,6 +169,15 @@ iim_status iim_solve_host(iim_problem* p, const double* f_host, const double* g_
  * enqueues every solve graph on a pool of streams so that their kernels overlap
  * on the device, then waits.  infos may be NULL. */
 iim_status iim_batch_solve(iim_problem** probs, double** x_devs, int count, iim_solve_info* infos);
+
+/* Profiling: average device time (microseconds) of one launch of an internal
+ * kernel, timed with CUDA events on the problem's stream over ``reps`` back to
+ * back launches on the problem's own vectors (after 3 untimed launches).
+ * which: 0 high-order stencil, 1 ghost values, 2 corrections (Eq. 12 operator
+ * kernels); 3 one red half sweep on the finest level; 4 FGMRES multi-dot and
+ * 5 update over restart/2 + 1 vectors; 6 a whole V-cycle; 7 the whole operator.
+ * Overwrites the problem's work vectors: call it between solves.  Synchronises. */
+iim_status iim_kernel_time(iim_problem* p, int which, int reps, double* us);
 
 /* Kernel launches issued by this library in the calling process so far. */
 int64_t iim_launch_count(void);

@@ -42,7 +42,8 @@ class Options(ctypes.Structure):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("restarts", ctypes.c_int),
-                ("converged", ctypes.c_int), ("relres", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+                ("converged", ctypes.c_int), ("relres", ctypes.c_double), ("solve_ms", ctypes.c_double),
+                ("kernels", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -69,6 +70,7 @@ SIGNATURES = {
     "iim_solve_host": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 6 + [ctypes.POINTER(SolveInfo)]),
     "iim_batch_solve": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
                                        ctypes.POINTER(SolveInfo)]),
+    "iim_kernel_time": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "iim_launch_count": (ctypes.c_int64, []),
     "iim_last_error": (ctypes.c_char_p, []),
     "iim_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -256,6 +258,17 @@ def batch_solve(problems, xs, check=True):
     if check:
         _check(st, "iim_batch_solve")
     return [infos[i] for i in range(n)], st
+
+
+KERNELS = {"stencil": 0, "ghost": 1, "correct": 2, "smooth_fine": 3, "multidot": 4, "update": 5, "vcycle": 6,
+           "operator": 7}
+
+
+def kernel_time(problem, which, reps=50) -> float:
+    """Average device microseconds per launch of one internal kernel (see iim_kernel_time)."""
+    us = ctypes.c_double()
+    _check(load().iim_kernel_time(problem.h, KERNELS.get(which, which), int(reps), ctypes.byref(us)), "kernel_time")
+    return us.value
 
 
 def launch_count() -> int:

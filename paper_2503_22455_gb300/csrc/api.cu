@@ -243,9 +243,9 @@ iim_status iim_problem_create(const iim_problem_desc* desc, const iim_options* o
   IIM_ALLOC(P.d_monos, int, mono.size());
   cudaMemcpy(P.d_monos, mono.data(), sizeof(int) * mono.size(), cudaMemcpyHostToDevice);
   IIM_ALLOC(P.d_status, int, 4);
-  IIM_ALLOC(P.d_counts, int, 16 + 32);
+  IIM_ALLOC(P.d_counts, int, kCountSlots);
   cudaMemsetAsync(P.d_status, 0, sizeof(int) * 4, P.stream);
-  cudaMemsetAsync(P.d_counts, 0, sizeof(int) * 48, P.stream);
+  cudaMemsetAsync(P.d_counts, 0, sizeof(int) * kCountSlots, P.stream);
   IIM_ALLOC(P.phase, uint8_t, N);
   IIM_ALLOC(P.edge_flag, int32_t, N * d);
   IIM_ALLOC(P.edge_id, int32_t, N * d);
@@ -259,6 +259,7 @@ iim_status iim_problem_create(const iim_problem_desc* desc, const iim_options* o
   if (cuda_check("setup: crossing count") != IIM_OK) IIM_FAIL(IIM_ERR_CUDA);
   P.K = K;
   P.K_cap = K + K / 4 + 64;
+  IIM_ALLOC(P.cr_edge, int32_t, P.K_cap);
   IIM_ALLOC(P.cr_axis, int32_t, P.K_cap);
   IIM_ALLOC(P.cr_lo, int32_t, P.K_cap);
   IIM_ALLOC(P.cr_loplus, uint8_t, P.K_cap);
@@ -307,6 +308,7 @@ iim_status iim_problem_create(const iim_problem_desc* desc, const iim_options* o
   cudaMemsetAsync(P.b, 0, sizeof(double) * N, P.stream);
   // multigrid levels
   std::vector<int> sizes = level_sizes(n, d);
+  if ((int)sizes.size() > kMaxLevels) IIM_FAIL(IIM_ERR_INVALID_ARG);
   const size_t esz = opt->mg_precision == IIM_MG_FP64 ? 8 : 4;
   P.lv.resize(sizes.size());
   for (size_t l = 0; l < sizes.size(); ++l) {
@@ -321,9 +323,11 @@ iim_status iim_problem_create(const iim_problem_desc* desc, const iim_options* o
     IIM_ALLOC(L.flag, int32_t, L.g.N);
     IIM_ALLOC(L.idx, int32_t, L.g.N);
     L.u = dev_alloc(P, esz * L.g.N);
+    L.u2 = dev_alloc(P, esz * L.g.N);
     L.f = dev_alloc(P, esz * L.g.N);
-    if (!L.u || !L.f) IIM_FAIL(IIM_ERR_BUDGET);
+    if (!L.u || !L.u2 || !L.f) IIM_FAIL(IIM_ERR_BUDGET);
     cudaMemsetAsync(L.u, 0, esz * L.g.N, P.stream);
+    cudaMemsetAsync(L.u2, 0, esz * L.g.N, P.stream);
     cudaMemsetAsync(L.f, 0, esz * L.g.N, P.stream);
   }
   setup_levels(P, true);
@@ -334,6 +338,7 @@ iim_status iim_problem_create(const iim_problem_desc* desc, const iim_options* o
     L.n_irr = read_count(P, 2 + (int)l);
     L.irr_cap = L.n_irr + L.n_irr / 4 + 64;
     const int D = 2 * d + 1;
+    IIM_ALLOC(L.irr_node, int32_t, L.irr_cap);
     IIM_ALLOC(L.tab64, double, (size_t)L.irr_cap * D);
     IIM_ALLOC(L.tab32, float, (size_t)L.irr_cap * D);
   }
@@ -509,13 +514,19 @@ iim_status iim_solve(iim_problem* H, double* x, iim_solve_info* info) {
   Problem& P = H->P;
   cudaMemcpyAsync(P.x, x, sizeof(double) * P.g.N, cudaMemcpyDeviceToDevice, P.stream);
   cudaEventRecord(P.ev0, P.stream);
+  const int64_t l0 = iim_launch_count();
   iim_status st = solve_enqueue(P, P.stream);
   if (st != IIM_OK) return st;
+  const int64_t l1 = iim_launch_count();
   cudaEventRecord(P.ev1, P.stream);
   cudaMemcpyAsync(x, P.x, sizeof(double) * P.g.N, cudaMemcpyDeviceToDevice, P.stream);
   cudaStreamSynchronize(P.stream);
   if (cuda_check("solve") != IIM_OK) return IIM_ERR_CUDA;
-  return finish_info(P, info);
+  iim_solve_info tmp;
+  st = finish_info(P, &tmp);
+  if (!P.opt.use_graph) tmp.kernels = l1 - l0;
+  if (info) *info = tmp;
+  return st;
 }
 
 iim_status iim_solve_host(iim_problem* H, const double* f, const double* g, const double* j0, const double* j1,
@@ -529,13 +540,19 @@ iim_status iim_solve_host(iim_problem* H, const double* f, const double* g, cons
   compute_rhs(P, fst, P.stream);
   cudaMemsetAsync(P.x, 0, sizeof(double) * P.g.N, P.stream);
   cudaEventRecord(P.ev0, P.stream);
+  const int64_t l0 = iim_launch_count();
   iim_status st = solve_enqueue(P, P.stream);
   if (st != IIM_OK) return st;
+  const int64_t l1 = iim_launch_count();
   cudaEventRecord(P.ev1, P.stream);
   cudaMemcpyAsync(x, P.x, sizeof(double) * P.g.N, cudaMemcpyDeviceToHost, P.stream);
   cudaStreamSynchronize(P.stream);
   if (cuda_check("solve_host") != IIM_OK) return IIM_ERR_CUDA;
-  return finish_info(P, info);
+  iim_solve_info tmp;
+  st = finish_info(P, &tmp);
+  if (!P.opt.use_graph) tmp.kernels = l1 - l0;
+  if (info) *info = tmp;
+  return st;
 }
 
 iim_status iim_batch_solve(iim_problem** probs, double** xs, int count, iim_solve_info* infos) {
@@ -594,6 +611,36 @@ iim_status iim_batch_solve(iim_problem** probs, double** xs, int count, iim_solv
     if (st != IIM_OK && worst == IIM_OK) worst = st;
   }
   return worst;
+}
+
+iim_status iim_kernel_time(iim_problem* H, int which, int reps, double* us) {
+  if (!H || !us || reps < 1) return IIM_ERR_INVALID_ARG;
+  Problem& P = H->P;
+  cudaStream_t s = P.stream;
+  const int j = P.opt.restart / 2;
+  auto launch = [&]() {
+    switch (which) {
+      case 0: ho_stencil(P, P.x, P.tmp, s); break;
+      case 1: ho_ghost(P, P.x, false, s); break;
+      case 2: ho_correct(P, P.x, P.tmp, false, s); break;
+      case 3: mg_smooth_fine(P, 0, s); break;
+      case 4: krylov_orth_pass(P, j, 0, s); break;
+      case 5: krylov_orth_pass(P, j, 1, s); break;
+      case 6: mg_precondition(P, P.V, nullptr, P.tmp, s); break;
+      case 7: ho_apply(P, P.x, P.tmp, false, s); break;
+      default: break;
+    }
+  };
+  if (which < 0 || which > 7) return IIM_ERR_INVALID_ARG;
+  for (int r = 0; r < 3; ++r) launch();
+  cudaEventRecord(P.ev0, s);
+  for (int r = 0; r < reps; ++r) launch();
+  cudaEventRecord(P.ev1, s);
+  cudaEventSynchronize(P.ev1);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, P.ev0, P.ev1);
+  *us = 1e3 * ms / reps;
+  return cuda_check("kernel time");
 }
 
 }  // extern "C"

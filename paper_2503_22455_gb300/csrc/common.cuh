@@ -165,25 +165,28 @@ __device__ inline bool phase_plus_at(const Geom& G, const double* x) {
 }
 
 // Root of phi on the edge [x0, x0 + h e_ax]: safeguarded Newton with bisection.
-// Returns t in [0,1] (fraction of h from x0).
+// Returns t in [0,1] (fraction of h from x0).  Stops when the bracket or the
+// Newton step is below 2 ulps of 1, i.e. at double precision.
 __device__ inline double edge_root(const Geom& G, const double* x0, int ax, double h, int dim) {
   double x[3] = {x0[0], x0[1], dim > 2 ? x0[2] : 0.0};
   double lo = 0.0, hi = 1.0;
   bool s_lo = geom_phi(G, x) >= 0.0;
   double t = 0.5;
-  for (int it = 0; it < 200; ++it) {
+  for (int it = 0; it < 100; ++it) {
     x[ax] = x0[ax] + t * h;
     double f = geom_phi(G, x);
+    if (f == 0.0) break;
     bool s = f >= 0.0;
     if (s == s_lo) lo = t; else hi = t;
-    if (hi - lo <= 4e-16) break;
+    if (hi - lo <= 4.5e-16) break;
     double gr[3];
     geom_grad_g(G, x, gr);
     double df = G.sign * gr[ax] * h;
     double tn = (df != 0.0) ? t - f / df : 0.5 * (lo + hi);
     if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
-    if (fabs(tn - t) <= 1e-17) { t = tn; break; }
+    double step = fabs(tn - t);
     t = tn;
+    if (step <= 4.5e-16) break;
   }
   return t < 0 ? 0 : (t > 1 ? 1 : t);
 }

@@ -24,13 +24,19 @@ struct Level {
   int32_t* flag = nullptr;        // scratch for the irregular-node scan
   int32_t* idx = nullptr;
   int n_irr = 0, irr_cap = 0;
+  int32_t* irr_node = nullptr;    // [irr_cap] node of each irregular row
   float* tab32 = nullptr;
   double* tab64 = nullptr;
   void* u = nullptr;              // level vectors, float or double by mg precision
+  void* u2 = nullptr;             // second u buffer: fused kernels read one and write the other
   void* f = nullptr;
 };
 
 struct SolverScalars;             // device-side FGMRES state (krylov.cu)
+
+// slots of Problem::d_counts: control points, affected nodes, irregular rows of
+// level l at kCountLevel0 + l (at most kMaxLevels levels), unknowns of the coarsest level
+constexpr int kCountK = 0, kCountAff = 1, kCountLevel0 = 2, kMaxLevels = 24, kCountCoarse = 40, kCountSlots = 48;
 
 struct Problem {
   iim_problem_desc desc;
@@ -48,6 +54,7 @@ struct Problem {
   int32_t* edge_flag = nullptr;   // [dim * N]
   int32_t* edge_id = nullptr;     // [dim * N] exclusive scan -> crossing id of a cut edge
   int K = 0, K_cap = 0;
+  int32_t* cr_edge = nullptr;     // [K_cap] cut edge (axis * N + lower node) of each control point
   int32_t* cr_axis = nullptr;
   int32_t* cr_lo = nullptr;
   uint8_t* cr_loplus = nullptr;
@@ -97,11 +104,12 @@ struct Problem {
   int32_t* coarse_piv = nullptr;
   // status and scratch
   int* d_status = nullptr;
-  int* d_counts = nullptr;        // [8] device counters (K, n_aff, irregular counts, ...)
+  int* d_counts = nullptr;        // [kCountSlots] device counters (see kCount*)
   int* scan_scratch = nullptr;
   int64_t scan_scratch_len = 0;
   // CUDA graph of the solve
   cudaGraphExec_t graph_exec = nullptr;
+  int64_t kern_start = 0, kern_restart = 0, kern_iter[kMaxRestart] = {0};
   cudaGraph_t graph = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   size_t bytes = 0;               // device bytes held
@@ -119,17 +127,22 @@ iim_status setup_levels(Problem& P, bool size_only);
 
 // operator.cu
 void ho_apply(Problem& P, const double* u, double* w, bool with_data, cudaStream_t s);
+void ho_stencil(Problem& P, const double* u, double* w, cudaStream_t s);
+void ho_ghost(Problem& P, const double* u, bool with_data, cudaStream_t s);
+void ho_correct(Problem& P, const double* u, double* w, bool with_data, cudaStream_t s);
 void compute_rhs(Problem& P, const double* f, cudaStream_t s);
 
 // multigrid.cu
 void mg_precondition(Problem& P, const double* v, const double* vscale, double* z, cudaStream_t s);
 void mg_coarse_factor(Problem& P, cudaStream_t s);
+void mg_smooth_fine(Problem& P, int colour, cudaStream_t s);
 
 // krylov.cu
 iim_status krylov_alloc(Problem& P);
 void krylov_enqueue_solve(Problem& P, double* x, bool graph_mode);
 iim_status krylov_build_graph(Problem& P, double* x);
 void krylov_read_info(Problem& P, iim_solve_info* info);
+void krylov_orth_pass(Problem& P, int j, int which, cudaStream_t s);
 
 // api.cu
 void* dev_alloc(Problem& P, size_t bytes);

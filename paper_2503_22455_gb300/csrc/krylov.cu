@@ -67,11 +67,21 @@ __device__ inline bool last_block(unsigned int* counter) {
   return is_last;
 }
 
+// Sum the per-block partials in the last block: thread t adds blocks t, t+256, ... of
+// every component, then a fixed-order tree over the threads (deterministic).
 __device__ inline void sum_partials(const double* partial, int nblocks, int stride, int nv, double* out) {
-  // fixed order: threads k < nv sum column k over the blocks
+  __shared__ double red[kRedThreads / 32][kMaxRestart + 4];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int k = 0; k < nv; ++k) {
+    double s = 0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partial[(size_t)b * stride + k];
+    s = warp_sum(s);
+    if (lane == 0) red[wid][k] = s;
+  }
+  __syncthreads();
   if (threadIdx.x < nv) {
     double s = 0;
-    for (int b = 0; b < nblocks; ++b) s += partial[(size_t)b * stride + threadIdx.x];
+    for (int w = 0; w < kRedThreads / 32; ++w) s += red[w][threadIdx.x];
     out[threadIdx.x] = s;
   }
   __syncthreads();
@@ -329,6 +339,22 @@ static void orth(Problem& P, int j, cudaStream_t s, int second) {
   }
 }
 
+// one multidot (which = 0) or update (which = 1) pass over v_0..v_j (kernel timing)
+void krylov_orth_pass(Problem& P, int j, int which, cudaStream_t s) {
+  switch (j + 1) {
+#define IIM_CASE(k)                                                                                          \
+  case k:                                                                                                    \
+    if (which == 0)                                                                                          \
+      IIM_LAUNCH(k_multidot<k>, P.red_blocks, kRedThreads, 0, s, P.V, P.Npad, j, P.partial, P.counter, P.sc, 0); \
+    else                                                                                                     \
+      IIM_LAUNCH(k_update<k>, P.red_blocks, kRedThreads, 0, s, P.V, P.Npad, j, P.partial, P.counter, P.sc, 0);   \
+    break;
+    IIM_CASE(1) IIM_CASE(2) IIM_CASE(3) IIM_CASE(4) IIM_CASE(5) IIM_CASE(6) IIM_CASE(7) IIM_CASE(8)
+    IIM_CASE(9) IIM_CASE(10) IIM_CASE(11) IIM_CASE(12) IIM_CASE(13) IIM_CASE(14) IIM_CASE(15) IIM_CASE(16)
+#undef IIM_CASE
+  }
+}
+
 static void enqueue_iteration(Problem& P, int j, cudaStream_t s) {
   double* vj = P.V + (size_t)j * P.Npad;
   double* zj = P.Z + (size_t)j * P.Npad;
@@ -355,9 +381,7 @@ static void enqueue_start(Problem& P, cudaStream_t s, int graph_mode) {
              P.d_status);
 }
 
-struct HostFlags {
-  int active, done;
-};
+static int64_t launches_now() { return iim_launch_count(); }
 
 // host-driven loop (one synchronisation per iteration); used when graphs are off
 void krylov_enqueue_solve(Problem& P, double* x, bool graph_mode) {
@@ -408,7 +432,9 @@ iim_status krylov_build_graph(Problem& P, double* x) {
   cudaGraphConditionalHandleCreate(&hw, g, 0, 0);
   const int m = P.opt.restart;
   cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  int64_t c0 = launches_now();
   enqueue_start(P, s, 1);
+  P.kern_start = launches_now() - c0;
   cudaGraph_t body;
   add_conditional(g, s, hw, cudaGraphCondTypeWhile, &body);
   cudaStreamEndCapture(s, &g);
@@ -417,11 +443,15 @@ iim_status krylov_build_graph(Problem& P, double* x) {
   cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
   std::vector<cudaGraph_t> ibody(m);
   for (int j = 0; j < m; ++j) add_conditional(body, s, hif[j], cudaGraphCondTypeIf, &ibody[j]);
+  c0 = launches_now();
   enqueue_restart(P, s);
+  P.kern_restart = launches_now() - c0;
   cudaStreamEndCapture(s, &body);
   for (int j = 0; j < m; ++j) {
     cudaStreamBeginCaptureToGraph(s, ibody[j], nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    c0 = launches_now();
     enqueue_iteration(P, j, s);
+    P.kern_iter[j] = launches_now() - c0;
     cudaStreamEndCapture(s, &ibody[j]);
   }
   cudaError_t e = cudaGetLastError();
@@ -456,6 +486,18 @@ void krylov_read_info(Problem& P, iim_solve_info* info) {
   SolverScalars h;
   cudaMemcpy(&h, P.sc, sizeof(SolverScalars), cudaMemcpyDeviceToHost);
   if (!info) return;
+  // kernels executed by the graph: start + restarts x restart body + iterations
+  // (iterations of a cycle are consecutive from j = 0)
+  int64_t kern = P.kern_start + (int64_t)h.restarts * P.kern_restart;
+  {
+    int left = h.iters, m = P.opt.restart;
+    while (left > 0) {
+      int take = left < m ? left : m;
+      for (int j = 0; j < take; ++j) kern += P.kern_iter[j];
+      left -= take;
+    }
+  }
+  info->kernels = kern;
   info->iters = h.iters;
   info->restarts = h.restarts;
   info->converged = h.converged;

@@ -1,0 +1,445 @@
+// Fused Shortley-Weller multigrid kernels (paper Sec. 3.3), included by multigrid.cu.
+//
+// 2D fine levels: one CTA owns a TX x TY tile plus a halo of 3 in shared memory
+// and runs several red/black half sweeps back to back on shrinking margins
+// (temporal blocking), so each kernel reads and writes the level once:
+//   MODE 0  first pre-smoothing sweep from u = 0; on the finest level the FP64
+//           Krylov vector enters here: f = v * scale / beta_sigma
+//   MODE 1  last pre-smoothing sweep, residual, 2x2 restriction to the coarse f
+//   MODE 2  prolongation + correction, first post-smoothing sweep
+//   MODE 3  last post-smoothing sweep; on the finest level z = (double) u
+//   MODE 4  one plain sweep (only when nu > 2)
+// Coarse tail: every level with at most 4096 nodes and the dense coarse solve
+// run in a single CTA with the whole sub-hierarchy in shared memory.
+#pragma once
+
+namespace iim {
+
+template <typename T>
+struct LevelK {
+  int dim, n;
+  int64_t N;
+  T ih2;          // 1/h^2
+  T inv_dreg;     // 1/(-2d/h^2): inverse diagonal of a regular node
+  T dreg;         // -2d/h^2
+  const int32_t* aux;
+  const T* tab;
+  T* u;
+  T* f;
+};
+
+template <typename T>
+static LevelK<T> levk(const Level& L) {
+  LevelK<T> k;
+  k.dim = L.g.dim;
+  k.n = L.g.n;
+  k.N = L.g.N;
+  const double h2 = L.g.h * L.g.h;
+  k.ih2 = (T)(1.0 / h2);
+  k.dreg = (T)(-2.0 * L.g.dim / h2);
+  k.inv_dreg = (T)(-h2 / (2.0 * L.g.dim));
+  k.aux = L.aux;
+  k.tab = (const T*)(sizeof(T) == 8 ? (const void*)L.tab64 : (const void*)L.tab32);
+  k.u = (T*)L.u;
+  k.f = (T*)L.f;
+  return k;
+}
+
+constexpr int kH = 3;
+
+template <typename T>
+struct Fine2DParams {
+  LevelK<T> L;
+  LevelK<T> C;                 // coarse level (MODE 1, 2)
+  const T* u_in;               // u is read from u_in (tile + halo) and written to u_out:
+  T* u_out;                    // a kernel never reads what another CTA of it writes
+  const T* uc;                 // MODE 2: the coarse correction
+  int neumann;                 // Neumann prolongation: mean of the in-domain coarse neighbours
+  const double* v;             // MODE 0 on the finest level: the Krylov vector
+  const double* vscale;
+  const uint8_t* phase;
+  T inv_bp, inv_bm;
+  double* z;                   // MODE 3 on the finest level: output
+};
+
+template <typename T>
+__device__ inline T tab2(const LevelK<T>& L, int r, int k) { return L.tab[(size_t)r * 5 + k]; }
+
+template <typename T, int TX, int TY, int MODE>
+__global__ void __launch_bounds__(256) k_mg2d(Fine2DParams<T> P) {
+  constexpr int SX = TX + 2 * kH, SY = TY + 2 * kH, S = SX * SY;
+  __shared__ T us[S];
+  __shared__ T fs[S];
+  __shared__ int as[S];
+  const LevelK<T>& L = P.L;
+  const int n = L.n;
+  const int x0 = blockIdx.x * TX - kH, y0 = blockIdx.y * TY - kH;
+  const bool finest_in = MODE == 0 && P.v != nullptr;
+  const T vs = finest_in ? (T)(P.vscale ? *P.vscale : 1.0) : (T)1;
+  {
+    // all loads of a thread are issued before any is used (no aux -> f/u dependence)
+    constexpr int NL = (S + 255) / 256;
+    int ra[NL];
+    T rf[NL], ru[NL];
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      const int e = threadIdx.x + q * 256;
+      const int sx = e % SX, sy = e / SX;
+      const int gx = x0 + sx, gy = y0 + sy;
+      ra[q] = -2;
+      rf[q] = 0;
+      ru[q] = 0;
+      if (e < S && gx >= 0 && gx < n && gy >= 0 && gy < n) {
+        const int64_t g = (int64_t)gy * n + gx;
+        ra[q] = __ldg(L.aux + g);
+        if (finest_in) rf[q] = (T)__ldg(P.v + g) * (vs * (__ldg(P.phase + g) ? P.inv_bp : P.inv_bm));
+        else rf[q] = L.f[g];
+        if (MODE != 0) ru[q] = P.u_in[g];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      const int e = threadIdx.x + q * 256;
+      if (e >= S) continue;
+      const bool unk = ra[q] != -2;
+      us[e] = unk ? ru[q] : (T)0;
+      fs[e] = unk ? rf[q] : (T)0;
+      as[e] = ra[q];
+    }
+  }
+  __syncthreads();
+  if (MODE == 2) {
+    // u += P e_coarse on margin 2
+    const LevelK<T>& C = P.C;
+    for (int e = threadIdx.x; e < S; e += blockDim.x) {
+      const int sx = e % SX, sy = e / SX;
+      if (sx < kH - 2 || sx >= SX - (kH - 2) || sy < kH - 2 || sy >= SY - (kH - 2)) continue;
+      if (as[e] == -2) continue;
+      const int gx = x0 + sx, gy = y0 + sy;
+      const int I0 = gx >> 1, I1 = gy >> 1;
+      const int s0 = (gx & 1) ? 1 : -1, s1 = (gy & 1) ? 1 : -1;
+      T acc = 0;
+      int cnt = 0;
+#pragma unroll
+      for (int sel = 0; sel < 4; ++sel) {
+        const int b0 = sel & 1, b1 = sel >> 1;
+        const int c0 = I0 + b0 * s0, c1 = I1 + b1 * s1;
+        if (c0 < 0 || c0 >= C.n || c1 < 0 || c1 >= C.n) continue;
+        const int64_t ci = (int64_t)c1 * C.n + c0;
+        if (C.aux[ci] == -2) continue;
+        const T ev = P.uc[ci];
+        if (P.neumann) { acc += ev; ++cnt; }
+        else acc += (b0 ? (T)0.25 : (T)0.75) * (b1 ? (T)0.25 : (T)0.75) * ev;
+      }
+      if (P.neumann) acc = cnt > 0 ? acc / (T)cnt : (T)0;
+      us[e] += acc;
+    }
+    __syncthreads();
+  }
+  auto half_sweep = [&](int colour, int margin, bool from_zero) {
+    const int lo = kH - margin;
+    const int rw = SX - 2 * lo, rh = SY - 2 * lo, hw = (rw + 1) / 2;
+    for (int t = threadIdx.x; t < rh * hw; t += blockDim.x) {
+      const int ry = t / hw, k2 = t - ry * hw;
+      const int sy = lo + ry;
+      // first x of this colour in the row: parity of (gx + gy) must equal colour
+      const int par = ((x0 + lo + y0 + sy) & 1) != colour;
+      const int sx = lo + 2 * k2 + par;
+      if (sx >= SX - lo) continue;
+      const int e = sy * SX + sx;
+      const int a = as[e];
+      if (a == -2) continue;
+      T nv;
+      if (a == -1) {
+        const T s = from_zero ? (T)0 : (us[e - 1] + us[e + 1]) + (us[e - SX] + us[e + SX]);
+        nv = (fs[e] - L.ih2 * s) * L.inv_dreg;
+      } else {
+        T s = 0;
+        if (!from_zero)
+          s = tab2(L, a, 1) * us[e - 1] + tab2(L, a, 2) * us[e + 1] + tab2(L, a, 3) * us[e - SX] +
+              tab2(L, a, 4) * us[e + SX];
+        const T dg = tab2(L, a, 0);
+        nv = dg != (T)0 ? (fs[e] - s) / dg : (T)0;
+      }
+      us[e] = nv;
+    }
+    __syncthreads();
+  };
+  if (MODE == 0) { half_sweep(0, 1, true); half_sweep(1, 0, false); }
+  if (MODE == 1) { half_sweep(0, 2, false); half_sweep(1, 1, false); }
+  if (MODE == 2 || MODE == 3 || MODE == 4) { half_sweep(0, 1, false); half_sweep(1, 0, false); }
+  if (MODE == 1) {
+    // residual on the tile, kept in registers until every thread has read its neighbours
+    constexpr int TPT = (TX * TY + 255) / 256;
+    T rr[TPT];
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+      const int e0 = threadIdx.x + q * 256;
+      rr[q] = 0;
+      if (e0 >= TX * TY) continue;
+      const int tx = e0 % TX, ty = e0 / TX;
+      const int e = (ty + kH) * SX + tx + kH;
+      const int a = as[e];
+      if (a == -1) {
+        const T s = (us[e - 1] + us[e + 1]) + (us[e - SX] + us[e + SX]);
+        rr[q] = fs[e] - (L.dreg * us[e] + L.ih2 * s);
+      } else if (a >= 0) {
+        const T s = tab2(L, a, 1) * us[e - 1] + tab2(L, a, 2) * us[e + 1] + tab2(L, a, 3) * us[e - SX] +
+                    tab2(L, a, 4) * us[e + SX];
+        rr[q] = fs[e] - (tab2(L, a, 0) * us[e] + s);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+      const int e0 = threadIdx.x + q * 256;
+      if (e0 >= TX * TY) continue;
+      const int tx = e0 % TX, ty = e0 / TX;
+      fs[(ty + kH) * SX + tx + kH] = rr[q];
+    }
+    __syncthreads();
+    const LevelK<T>& C = P.C;
+    for (int e = threadIdx.x; e < (TX / 2) * (TY / 2); e += blockDim.x) {
+      const int cx = e % (TX / 2), cy = e / (TX / 2);
+      const int gcx = blockIdx.x * (TX / 2) + cx, gcy = blockIdx.y * (TY / 2) + cy;
+      if (gcx >= C.n || gcy >= C.n) continue;
+      const int64_t ci = (int64_t)gcy * C.n + gcx;
+      const int b = (kH + 2 * cy) * SX + kH + 2 * cx;
+      const T acc = (fs[b] + fs[b + 1]) + (fs[b + SX] + fs[b + SX + 1]);
+      C.f[ci] = C.aux[ci] == -2 ? (T)0 : acc * (T)0.25;
+    }
+  }
+  for (int e = threadIdx.x; e < TX * TY; e += blockDim.x) {
+    const int tx = e % TX, ty = e / TX;
+    const int gx = blockIdx.x * TX + tx, gy = blockIdx.y * TY + ty;
+    if (gx >= n || gy >= n) continue;
+    const int64_t g = (int64_t)gy * n + gx;
+    const int se = (ty + kH) * SX + tx + kH;
+    if (MODE == 3 && P.z != nullptr) P.z[g] = (double)us[se];
+    else P.u_out[g] = us[se];
+    if (finest_in) L.f[g] = fs[se];
+  }
+}
+
+// ---------------------------------------------------------------------------- coarse tail (one CTA)
+constexpr int kTailMaxLevels = 8;
+constexpr int kTailThreads = 1024;
+
+template <typename T>
+struct TailParams {
+  int nlev;                          // levels l0 .. l0+nlev-1; the last is the coarsest
+  LevelK<T> L[kTailMaxLevels];
+  int off[kTailMaxLevels + 1];       // offsets of the levels in the shared u / f / aux arrays
+  int toff[kTailMaxLevels + 1];      // offsets (in T) of the levels' tables in shared memory
+  const int* tcount[kTailMaxLevels]; // device counts of irregular rows per level
+  int tcap[kTailMaxLevels];
+  int stage_tables;                  // 1: tables copied to shared memory
+  int nu1, nu2, neumann;
+  T* u_out;                          // where the first level's u goes (when z is not set)
+  int nu;                            // coarse unknowns
+  const int32_t* map;
+  const T* inv;                      // dense inverse of the coarsest SW matrix (row major)
+  const double* v;                   // set when the tail starts at the finest level
+  const double* vscale;
+  const uint8_t* phase;
+  T inv_bp, inv_bm;
+  double* z;
+};
+
+template <typename T>
+__device__ inline T tabd(const T* tb, int dim, int r, int k) { return tb[r * (2 * dim + 1) + k]; }
+
+// offdiagonal part of (L u)_i from shared-memory u; m = (i0, i1, i2)
+template <typename T>
+__device__ inline T tail_offdiag(const LevelK<T>& L, const T* tb, const T* u, int i, const int* m, int a) {
+  const int n = L.n;
+  if (a == -1) {
+    T s = (u[i - 1] + u[i + 1]) + (u[i - n] + u[i + n]);
+    if (L.dim > 2) s += u[i - n * n] + u[i + n * n];
+    return s * L.ih2;
+  }
+  T s = 0;
+  int st = 1;
+  for (int ax = 0; ax < L.dim; ++ax) {
+    const T cl = tabd(tb, L.dim, a, 1 + 2 * ax), cr = tabd(tb, L.dim, a, 2 + 2 * ax);
+    if (cl != (T)0 && m[ax] > 0) s += cl * u[i - st];
+    if (cr != (T)0 && m[ax] < n - 1) s += cr * u[i + st];
+    st *= n;
+  }
+  return s;
+}
+
+// node -> (i0, i1, i2) for the nodes i = t, t + stride, ...: one division per level, then
+// a carry per step (stride is the block size)
+struct NodeWalk {
+  int n, dim, i0, i1, i2, d0, drow;
+  __device__ NodeWalk(int n_, int dim_, int start, int stride) : n(n_), dim(dim_) {
+    i0 = start % n;
+    const int r = start / n;
+    i1 = dim > 2 ? r % n : r;
+    i2 = dim > 2 ? r / n : 0;
+    d0 = stride % n;
+    drow = stride / n;
+  }
+  __device__ void advance() {
+    i0 += d0;
+    int rows = drow;
+    if (i0 >= n) { i0 -= n; ++rows; }
+    i1 += rows;
+    if (dim > 2 && i1 >= n) { i2 += i1 / n; i1 %= n; }
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kTailThreads) k_vcycle_tail(TailParams<T> P) {
+  extern __shared__ unsigned char smraw[];
+  const int tot = P.off[P.nlev];
+  T* su = (T*)smraw;
+  T* sf = su + tot;
+  T* st = sf + tot;                                   // staged tables
+  int* sa = (int*)(st + P.toff[P.nlev]);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int k = 0; k < P.nlev; ++k)
+    for (int i = tid; i < P.L[k].N; i += nt) sa[P.off[k] + i] = P.L[k].aux[i];
+  if (P.stage_tables) {
+    for (int k = 0; k < P.nlev; ++k) {
+      const int rows = min(*P.tcount[k], P.tcap[k]);
+      const int len = rows * (2 * P.L[k].dim + 1);
+      for (int e = tid; e < len; e += nt) st[P.toff[k] + e] = P.L[k].tab[e];
+    }
+  }
+  auto table = [&](int k) -> const T* { return P.stage_tables ? st + P.toff[k] : P.L[k].tab; };
+  {
+    const LevelK<T>& L = P.L[0];
+    const T vs = P.v ? (T)(P.vscale ? *P.vscale : 1.0) : (T)1;
+    for (int i = tid; i < L.N; i += nt) {
+      T f = 0;
+      if (L.aux[i] != -2) f = P.v ? (T)P.v[i] * (vs * (P.phase[i] ? P.inv_bp : P.inv_bm)) : L.f[i];
+      sf[i] = f;
+    }
+  }
+  __syncthreads();
+  auto sweep = [&](int k, int colour, bool from_zero) {
+    const LevelK<T>& L = P.L[k];
+    T* u = su + P.off[k];
+    const T* f = sf + P.off[k];
+    const int* aux = sa + P.off[k];
+    const T* tb = table(k);
+    NodeWalk w(L.n, L.dim, tid, nt);
+    for (int i = tid; i < L.N; i += nt, w.advance()) {
+      const int m[3] = {w.i0, w.i1, w.i2};
+      const int a = aux[i];
+      if (((m[0] + m[1] + m[2]) & 1) != colour) {
+        if (from_zero) u[i] = 0;
+        continue;
+      }
+      if (a == -2) { u[i] = 0; continue; }
+      const T s = from_zero ? (T)0 : tail_offdiag(L, tb, u, i, m, a);
+      if (a == -1) {
+        u[i] = (f[i] - s) * L.inv_dreg;
+      } else {
+        const T dg = tabd(tb, L.dim, a, 0);
+        u[i] = dg != (T)0 ? (f[i] - s) / dg : (T)0;
+      }
+    }
+    __syncthreads();
+  };
+  for (int k = 0; k < P.nlev - 1; ++k) {
+    for (int it = 0; it < P.nu1; ++it) {
+      sweep(k, 0, it == 0);
+      sweep(k, 1, false);
+    }
+    const LevelK<T>& L = P.L[k];
+    const LevelK<T>& C = P.L[k + 1];
+    const T* u = su + P.off[k];
+    const T* f = sf + P.off[k];
+    const int* aux = sa + P.off[k];
+    const int* auxc = sa + P.off[k + 1];
+    const T* tb = table(k);
+    const T wch = L.dim > 2 ? (T)0.125 : (T)0.25;
+    NodeWalk w(C.n, C.dim, tid, nt);
+    for (int I = tid; I < C.N; I += nt, w.advance()) {
+      T acc = 0;
+      if (auxc[I] != -2) {
+        const int nch = 1 << L.dim;
+        for (int c = 0; c < nch; ++c) {
+          const int m[3] = {2 * w.i0 + (c & 1), 2 * w.i1 + ((c >> 1) & 1), L.dim > 2 ? 2 * w.i2 + ((c >> 2) & 1) : 0};
+          const int i = m[0] + L.n * (m[1] + L.n * m[2]);
+          const int a = aux[i];
+          if (a == -2) continue;
+          const T dg = a == -1 ? L.dreg : tabd(tb, L.dim, a, 0);
+          acc += f[i] - (dg * u[i] + tail_offdiag(L, tb, u, i, m, a));
+        }
+        acc *= wch;
+      }
+      sf[P.off[k + 1] + I] = acc;
+    }
+    __syncthreads();
+  }
+  {
+    const int k = P.nlev - 1;
+    const LevelK<T>& L = P.L[k];
+    T* u = su + P.off[k];
+    const T* f = sf + P.off[k];
+    for (int i = tid; i < L.N; i += nt) u[i] = 0;
+    __syncthreads();
+    const int lane = tid & 31, wid = tid >> 5, nw = nt / 32;
+    for (int r = wid; r < P.nu; r += nw) {
+      T s = 0;
+      for (int c = lane; c < P.nu; c += 32) s += P.inv[(size_t)r * P.nu + c] * f[P.map[c]];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) u[P.map[r]] = s;
+    }
+    __syncthreads();
+  }
+  for (int k = P.nlev - 2; k >= 0; --k) {
+    const LevelK<T>& L = P.L[k];
+    const LevelK<T>& C = P.L[k + 1];
+    T* u = su + P.off[k];
+    const T* ec = su + P.off[k + 1];
+    const int* aux = sa + P.off[k];
+    const int* auxc = sa + P.off[k + 1];
+    NodeWalk w(L.n, L.dim, tid, nt);
+    for (int i = tid; i < L.N; i += nt, w.advance()) {
+      if (aux[i] == -2) continue;
+      const int I[3] = {w.i0 >> 1, w.i1 >> 1, w.i2 >> 1};
+      const int sg[3] = {(w.i0 & 1) ? 1 : -1, (w.i1 & 1) ? 1 : -1, (w.i2 & 1) ? 1 : -1};
+      T acc = 0;
+      int cnt = 0;
+      const int nsel = 1 << L.dim;
+      for (int sel = 0; sel < nsel; ++sel) {
+        int c[3];
+        T wgt = 1;
+        bool inb = true;
+        for (int q = 0; q < 3; ++q) {
+          const int b = (sel >> q) & 1;
+          c[q] = q < L.dim ? I[q] + b * sg[q] : 0;
+          if (q < L.dim) {
+            if (c[q] < 0 || c[q] >= C.n) inb = false;
+            wgt *= b ? (T)0.25 : (T)0.75;
+          }
+        }
+        if (!inb) continue;
+        const int ci = c[0] + C.n * (c[1] + C.n * c[2]);
+        if (auxc[ci] == -2) continue;
+        if (P.neumann) { acc += ec[ci]; ++cnt; }
+        else acc += wgt * ec[ci];
+      }
+      if (P.neumann) acc = cnt > 0 ? acc / (T)cnt : (T)0;
+      u[i] += acc;
+    }
+    __syncthreads();
+    for (int it = 0; it < P.nu2; ++it) {
+      sweep(k, 0, false);
+      sweep(k, 1, false);
+    }
+  }
+  const LevelK<T>& L = P.L[0];
+  for (int i = tid; i < L.N; i += nt) {
+    const T u = su[i];
+    if (P.z) P.z[i] = (double)u;
+    else P.u_out[i] = u;
+  }
+}
+
+}  // namespace iim

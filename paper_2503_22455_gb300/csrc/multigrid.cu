@@ -7,7 +7,10 @@
 // (Neumann, Sec. 3.3); a dense direct solve on the coarsest level.  Interface
 // problems run on lap(u) = f/beta per phase (Sec. 3.3): the FP64 Krylov vector
 // is divided by beta_sigma when it enters the FP32 hierarchy.
+#include <utility>
+
 #include "kernels.cuh"
+#include "mg_fused.cuh"
 
 namespace iim {
 
@@ -32,11 +35,10 @@ __device__ inline void idx3(const GridView& g, int64_t i, int* m) {
 
 // (L u)_i without the diagonal term: sum of off-diagonal coefficients times neighbours
 template <typename T>
-__device__ inline T offdiag_sum(const LevelView<T>& L, int64_t i, const int* m, int a, const T* __restrict__ u) {
+__device__ inline T offdiag_sum(const LevelView<T>& L, T ih2, int64_t i, const int* m, int a, const T* __restrict__ u) {
   const GridView& g = L.g;
   T s = 0;
   if (a == -1) {
-    const T ih2 = (T)(1.0 / (g.h * g.h));
     for (int ax = 0; ax < g.dim; ++ax) {
       int64_t st = ax == 0 ? 1 : (ax == 1 ? (int64_t)g.n : (int64_t)g.n * g.n);
       s += u[i - st] + u[i + st];
@@ -53,14 +55,14 @@ __device__ inline T offdiag_sum(const LevelView<T>& L, int64_t i, const int* m, 
 }
 
 template <typename T>
-__device__ inline T diag_of(const LevelView<T>& L, int a) {
-  if (a == -1) return (T)(-2.0 * L.g.dim / (L.g.h * L.g.h));
+__device__ inline T diag_of(const LevelView<T>& L, T dreg, int a) {
+  if (a == -1) return dreg;
   return tabv(L, a, 0);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_smooth(LevelView<T> L, T* __restrict__ u, const T* __restrict__ f,
-                                                int colour) {
+__global__ void __launch_bounds__(256) k_smooth(LevelView<T> L, T ih2, T dreg, T* __restrict__ u,
+                                                const T* __restrict__ f, int colour) {
   // one thread per node of the colour: node = 2 * t + parity fix-up along x
   const GridView& g = L.g;
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -76,14 +78,14 @@ __global__ void __launch_bounds__(256) k_smooth(LevelView<T> L, T* __restrict__ 
   int a = L.aux[i];
   if (a == -2) return;
   int m[3] = {xi, ry, rz};
-  T dg = diag_of(L, a);
-  T s = offdiag_sum(L, i, m, a, u);
+  T dg = diag_of(L, dreg, a);
+  T s = offdiag_sum(L, ih2, i, m, a, u);
   u[i] = dg != (T)0 ? (f[i] - s) / dg : (T)0;
 }
 
 // coarse f = mean over the 2^d children of r = f - L u (zero at non-unknowns)
 template <typename T>
-__global__ void __launch_bounds__(256) k_resid_restrict(LevelView<T> F, const T* __restrict__ u,
+__global__ void __launch_bounds__(256) k_resid_restrict(LevelView<T> F, T ih2, T dreg, const T* __restrict__ u,
                                                         const T* __restrict__ f, GridView gc,
                                                         const int32_t* __restrict__ aux_c, T* __restrict__ fc) {
   int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -99,7 +101,7 @@ __global__ void __launch_bounds__(256) k_resid_restrict(LevelView<T> F, const T*
     int64_t i = m[0] + (int64_t)g.n * m[1] + (int64_t)g.n * g.n * m[2];
     int a = F.aux[i];
     if (a == -2) continue;
-    T r = f[i] - (diag_of(F, a) * u[i] + offdiag_sum(F, i, m, a, u));
+    T r = f[i] - (diag_of(F, dreg, a) * u[i] + offdiag_sum(F, ih2, i, m, a, u));
     acc += r;
   }
   fc[I] = acc / (T)nch;
@@ -179,7 +181,7 @@ __global__ void k_coarse_assemble(LevelView<double> L, const int32_t* __restrict
   int a = L.aux[i];
   int m[3];
   idx3(L.g, i, m);
-  A[(size_t)r * nu + r] = (T)diag_of(L, a);
+  A[(size_t)r * nu + r] = (T)diag_of(L, -2.0 * L.g.dim / (L.g.h * L.g.h), a);
   const GridView& g = L.g;
   for (int ax = 0; ax < g.dim; ++ax) {
     int64_t st = ax == 0 ? 1 : (ax == 1 ? (int64_t)g.n : (int64_t)g.n * g.n);
@@ -209,16 +211,21 @@ __global__ void k_unknown_flag(GridView g, const int32_t* __restrict__ aux, int3
   if (i < g.N) flag[i] = aux[i] != -2;
 }
 
-// LU with partial pivoting (one CTA), then the explicit inverse (column by column)
+// LU with partial pivoting (one CTA; the matrix is staged in shared memory when it
+// fits), then the explicit inverse, one warp per column.
 template <typename T>
-__global__ void k_coarse_lu(T* __restrict__ A, int nu, int32_t* __restrict__ piv, T* __restrict__ inv,
-                            int* status) {
+__global__ void k_coarse_lu(T* __restrict__ Ag, int nu, int32_t* __restrict__ piv, T* __restrict__ inv, int* status,
+                            int in_smem) {
+  extern __shared__ unsigned char smraw[];
   __shared__ int s_p;
   __shared__ T s_best[32];
   __shared__ int s_bi[32];
   const int tid = threadIdx.x, nt = blockDim.x;
+  T* A = in_smem ? (T*)smraw : Ag;
+  if (in_smem)
+    for (int e = tid; e < nu * nu; e += nt) A[e] = Ag[e];
+  __syncthreads();
   for (int k = 0; k < nu; ++k) {
-    // pivot search
     T best = -1;
     int bi = k;
     for (int r = k + tid; r < nu; r += nt) {
@@ -242,7 +249,7 @@ __global__ void k_coarse_lu(T* __restrict__ A, int nu, int32_t* __restrict__ piv
       if (!(b0 > 0)) set_status(status, IIM_ERR_SINGULAR);
     }
     __syncthreads();
-    int p = s_p;
+    const int p = s_p;
     if (p != k)
       for (int c = tid; c < nu; c += nt) {
         T t = A[(size_t)k * nu + c];
@@ -250,21 +257,59 @@ __global__ void k_coarse_lu(T* __restrict__ A, int nu, int32_t* __restrict__ piv
         A[(size_t)p * nu + c] = t;
       }
     __syncthreads();
-    T d = A[(size_t)k * nu + k];
+    const T d = A[(size_t)k * nu + k];
+    const int rem = nu - k - 1;
     for (int r = k + 1 + tid; r < nu; r += nt) A[(size_t)r * nu + k] /= d;
     __syncthreads();
-    int rem = nu - k - 1;
     for (int e = tid; e < rem * rem; e += nt) {
       int r = k + 1 + e / rem, c = k + 1 + e % rem;
       A[(size_t)r * nu + c] -= A[(size_t)r * nu + k] * A[(size_t)k * nu + c];
     }
     __syncthreads();
   }
-  // inverse: solve L U x = P e_j, one warp per column
+  if (in_smem)
+    for (int e = tid; e < nu * nu; e += nt) Ag[e] = A[e];
+  __syncthreads();
+  if (in_smem == 2) {
+    // inverse in shared memory: X = U^-1 L^-1 P, all columns at once, one row per step
+    T* X = A + (size_t)nu * nu;
+    for (int e = tid; e < nu * nu; e += nt) X[e] = 0;
+    __syncthreads();
+    if (tid == 0) {
+      // P applied to the identity: row swaps in factorisation order
+      for (int j = 0; j < nu; ++j) {
+        int r = j;
+        for (int k = 0; k < nu; ++k) {
+          if (piv[k] == r) r = k;
+          else if (k == r) r = piv[k];
+        }
+        X[(size_t)r * nu + j] = 1;
+      }
+    }
+    __syncthreads();
+    for (int r = 1; r < nu; ++r) {                  // forward, unit lower
+      for (int j = tid; j < nu; j += nt) {
+        T s = X[(size_t)r * nu + j];
+        for (int c = 0; c < r; ++c) s -= A[(size_t)r * nu + c] * X[(size_t)c * nu + j];
+        X[(size_t)r * nu + j] = s;
+      }
+      __syncthreads();
+    }
+    for (int r = nu - 1; r >= 0; --r) {             // backward
+      for (int j = tid; j < nu; j += nt) {
+        T s = X[(size_t)r * nu + j];
+        for (int c = r + 1; c < nu; ++c) s -= A[(size_t)r * nu + c] * X[(size_t)c * nu + j];
+        X[(size_t)r * nu + j] = s / A[(size_t)r * nu + r];
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < nu * nu; e += nt) inv[e] = X[e];
+    return;
+  }
+  // inverse from global memory: solve L U x = P e_j, one warp per column
   const int lane = tid & 31, wid = tid >> 5, nw = nt / 32;
   for (int j = wid; j < nu; j += nw) {
-    T* x = inv + (size_t)j;      // column j of the inverse, stride nu (row major inverse)
-    // b = P e_j : apply the row swaps to e_j
+    T* x = inv + (size_t)j;      // column j of the (row major) inverse, stride nu
     for (int r = lane; r < nu; r += 32) x[(size_t)r * nu] = (r == j) ? (T)1 : (T)0;
     __syncwarp();
     if (lane == 0)
@@ -318,40 +363,180 @@ static LevelView<T> view(const Level& L) {
   return v;
 }
 
+// first level handled by the single-CTA tail: the first with at most 4096 nodes
+static size_t tail_start(const Problem& P) {
+  size_t l = 0;
+  while (l + 1 < P.lv.size() && P.lv[l].g.N > 4096) ++l;
+  return l;
+}
+
 template <typename T>
-static void vcycle(Problem& P, size_t l, cudaStream_t s) {
+static void launch_tail(Problem& P, size_t l0, const double* v, const double* vscale, double* z, cudaStream_t s,
+                        T* u_out = nullptr) {
+  TailParams<T> tp;
+  tp.u_out = u_out ? u_out : (T*)P.lv[l0].u;
+  tp.nlev = (int)(P.lv.size() - l0);
+  int off = 0;
+  for (int k = 0; k < tp.nlev; ++k) {
+    tp.L[k] = levk<T>(P.lv[l0 + k]);
+    tp.off[k] = off;
+    off += (int)P.lv[l0 + k].g.N;
+  }
+  tp.off[tp.nlev] = off;
+  int toff = 0;
+  for (int k = 0; k < tp.nlev; ++k) {
+    const Level& L = P.lv[l0 + k];
+    tp.toff[k] = toff;
+    tp.tcount[k] = P.d_counts + 2 + (int)(l0 + k);
+    tp.tcap[k] = L.irr_cap;
+    toff += L.irr_cap * (2 * L.g.dim + 1);
+  }
+  tp.toff[tp.nlev] = toff;
+  const size_t base = (sizeof(T) * 2 + sizeof(int)) * (size_t)off;
+  tp.stage_tables = base + sizeof(T) * (size_t)toff <= 200 * 1024;
+  if (!tp.stage_tables) {
+    toff = 0;
+    for (int k = 0; k <= tp.nlev; ++k) tp.toff[k] = 0;
+  }
+  tp.nu1 = P.opt.nu1;
+  tp.nu2 = P.opt.nu2;
+  tp.neumann = P.desc.bc == IIM_BC_NEUMANN;
+  tp.nu = P.coarse_nu;
+  tp.map = P.coarse_map;
+  const T* inv = (const T*)(sizeof(T) == 8 ? (void*)P.coarse_lu64 : (void*)P.coarse_lu32);
+  tp.inv = inv + (size_t)P.coarse_nu * P.coarse_nu;
+  tp.v = v;
+  tp.vscale = vscale;
+  tp.phase = P.phase;
+  tp.inv_bp = (T)(1.0 / P.desc.beta_plus);
+  tp.inv_bm = (T)(1.0 / P.desc.beta_minus);
+  tp.z = z;
+  const size_t smem = base + sizeof(T) * (size_t)toff;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_vcycle_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  IIM_LAUNCH(k_vcycle_tail<T>, 1, kTailThreads, smem, s, tp);
+}
+
+template <typename T, int TX, int TY>
+static void launch_fine2d(Problem& P, size_t l, int mode, const double* v, const double* vscale, double* z,
+                          const T* u_in, T* u_out, const T* uc, cudaStream_t s) {
+  Fine2DParams<T> fp;
+  fp.L = levk<T>(P.lv[l]);
+  fp.u_in = u_in;
+  fp.u_out = u_out;
+  fp.uc = uc;
+  if (l + 1 < P.lv.size()) fp.C = levk<T>(P.lv[l + 1]);
+  fp.neumann = P.desc.bc == IIM_BC_NEUMANN;
+  fp.v = v;
+  fp.vscale = vscale;
+  fp.phase = P.phase;
+  fp.inv_bp = (T)(1.0 / P.desc.beta_plus);
+  fp.inv_bm = (T)(1.0 / P.desc.beta_minus);
+  fp.z = z;
+  const int n = P.lv[l].g.n;
+  dim3 grid(ceil_div(n, TX), ceil_div(n, TY));
+  switch (mode) {
+    case 0: IIM_LAUNCH((k_mg2d<T, TX, TY, 0>), grid, 256, 0, s, fp); break;
+    case 1: IIM_LAUNCH((k_mg2d<T, TX, TY, 1>), grid, 256, 0, s, fp); break;
+    case 2: IIM_LAUNCH((k_mg2d<T, TX, TY, 2>), grid, 256, 0, s, fp); break;
+    case 3: IIM_LAUNCH((k_mg2d<T, TX, TY, 3>), grid, 256, 0, s, fp); break;
+    default: IIM_LAUNCH((k_mg2d<T, TX, TY, 4>), grid, 256, 0, s, fp); break;
+  }
+}
+
+template <typename T>
+static void fine2d(Problem& P, size_t l, int mode, const double* v, const double* vscale, double* z, const T* u_in,
+                   T* u_out, const T* uc, cudaStream_t s) {
+  if (P.lv[l].g.n >= 512) launch_fine2d<T, 64, 16>(P, l, mode, v, vscale, z, u_in, u_out, uc, s);
+  else launch_fine2d<T, 32, 8>(P, l, mode, v, vscale, z, u_in, u_out, uc, s);
+}
+
+// 2D: fused kernels per fine level (MODE 0, [4...], 1 down; 2, [4...], 3 up), ping-ponging
+// between the level's two u buffers.  Returns the buffer that holds the level's result.
+template <typename T>
+static T* vcycle2d(Problem& P, size_t l, size_t lt, const double* v, const double* vscale, double* z,
+                   cudaStream_t s) {
+  T* A = (T*)P.lv[l].u;
+  T* B = (T*)P.lv[l].u2;
+  if (l == lt) {
+    launch_tail<T>(P, l, l == 0 ? v : nullptr, l == 0 ? vscale : nullptr, l == 0 ? z : nullptr, s, A);
+    return A;
+  }
+  fine2d<T>(P, l, 0, l == 0 ? v : nullptr, vscale, nullptr, nullptr, A, nullptr, s);
+  for (int it = 1; it < P.opt.nu1 - 1; ++it) {
+    fine2d<T>(P, l, 4, nullptr, nullptr, nullptr, A, B, nullptr, s);
+    std::swap(A, B);
+  }
+  fine2d<T>(P, l, 1, nullptr, nullptr, nullptr, A, B, nullptr, s);
+  std::swap(A, B);
+  const T* uc = vcycle2d<T>(P, l + 1, lt, nullptr, nullptr, nullptr, s);
+  fine2d<T>(P, l, 2, nullptr, nullptr, nullptr, A, B, uc, s);
+  std::swap(A, B);
+  for (int it = 1; it < P.opt.nu2 - 1; ++it) {
+    fine2d<T>(P, l, 4, nullptr, nullptr, nullptr, A, B, nullptr, s);
+    std::swap(A, B);
+  }
+  fine2d<T>(P, l, 3, nullptr, nullptr, l == 0 ? z : nullptr, A, B, nullptr, s);
+  return B;
+}
+
+// generic path (3D fine levels): one kernel per half sweep, transfers separate
+template <typename T>
+static void vcycle(Problem& P, size_t l, size_t lt, cudaStream_t s) {
   const int Tn = 256;
   Level& L = P.lv[l];
   T* u = (T*)L.u;
   T* f = (T*)L.f;
-  if (l + 1 == P.lv.size()) {
-    const T* inv = (const T*)(sizeof(T) == 8 ? (void*)P.coarse_lu64 : (void*)P.coarse_lu32);
-    IIM_LAUNCH(k_coarse_solve<T>, 1, 1024, sizeof(T) * (P.coarse_nu + 1), s, P.coarse_nu, P.coarse_map,
-               inv + (size_t)P.coarse_nu * P.coarse_nu, f, u, L.g.N);
+  if (l == lt) {
+    launch_tail<T>(P, l, nullptr, nullptr, nullptr, s);
     return;
   }
   LevelView<T> V = view<T>(L);
+  LevelK<T> K = levk<T>(L);
   const int64_t ncol = (L.g.N / L.g.n) * ((L.g.n + 1) / 2);
   IIM_LAUNCH(k_zero<T>, ceil_div(L.g.N, Tn), Tn, 0, s, u, L.g.N);
   for (int it = 0; it < P.opt.nu1; ++it)
-    for (int c = 0; c < 2; ++c) IIM_LAUNCH(k_smooth<T>, ceil_div(ncol, Tn), Tn, 0, s, V, u, f, c);
+    for (int c = 0; c < 2; ++c) IIM_LAUNCH(k_smooth<T>, ceil_div(ncol, Tn), Tn, 0, s, V, K.ih2, K.dreg, u, f, c);
   Level& C = P.lv[l + 1];
-  IIM_LAUNCH(k_resid_restrict<T>, ceil_div(C.g.N, Tn), Tn, 0, s, V, u, f, C.g, C.aux, (T*)C.f);
-  vcycle<T>(P, l + 1, s);
+  IIM_LAUNCH(k_resid_restrict<T>, ceil_div(C.g.N, Tn), Tn, 0, s, V, K.ih2, K.dreg, u, f, C.g, C.aux, (T*)C.f);
+  vcycle<T>(P, l + 1, lt, s);
   IIM_LAUNCH(k_prolong<T>, ceil_div(L.g.N, Tn), Tn, 0, s, L.g, L.aux, u, C.g, C.aux, (const T*)C.u,
              P.desc.bc == IIM_BC_NEUMANN);
   for (int it = 0; it < P.opt.nu2; ++it)
-    for (int c = 0; c < 2; ++c) IIM_LAUNCH(k_smooth<T>, ceil_div(ncol, Tn), Tn, 0, s, V, u, f, c);
+    for (int c = 0; c < 2; ++c) IIM_LAUNCH(k_smooth<T>, ceil_div(ncol, Tn), Tn, 0, s, V, K.ih2, K.dreg, u, f, c);
 }
 
 template <typename T>
 static void precondition_t(Problem& P, const double* v, const double* vscale, double* z, cudaStream_t s) {
   Level& L = P.lv[0];
   const int Tn = 256;
+  const size_t lt = tail_start(P);
+  if (lt == 0) {
+    launch_tail<T>(P, 0, v, vscale, z, s);
+    return;
+  }
+  if (P.g.dim == 2 && P.opt.nu1 >= 2 && P.opt.nu2 >= 2) {
+    vcycle2d<T>(P, 0, lt, v, vscale, z, s);
+    return;
+  }
   IIM_LAUNCH(k_bridge_in<T>, ceil_div(L.g.N, Tn), Tn, 0, s, L.g, v, vscale, P.phase, L.aux,
              1.0 / P.desc.beta_plus, 1.0 / P.desc.beta_minus, (T*)L.f);
-  vcycle<T>(P, 0, s);
+  vcycle<T>(P, 0, lt, s);
   IIM_LAUNCH(k_bridge_out<T>, ceil_div(L.g.N, Tn), Tn, 0, s, L.g, (const T*)L.u, z);
+}
+
+template <typename T>
+static void smooth_fine_t(Problem& P, int colour, cudaStream_t s) {
+  Level& L = P.lv[0];
+  LevelView<T> V = view<T>(L);
+  LevelK<T> K = levk<T>(L);
+  const int64_t ncol = (L.g.N / L.g.n) * ((L.g.n + 1) / 2);
+  IIM_LAUNCH(k_smooth<T>, ceil_div(ncol, 256), 256, 0, s, V, K.ih2, K.dreg, (T*)L.u, (const T*)L.f, colour);
+}
+
+// one red or black half sweep on the finest level (kernel timing)
+void mg_smooth_fine(Problem& P, int colour, cudaStream_t s) {
+  if (P.opt.mg_precision == IIM_MG_FP64) smooth_fine_t<double>(P, colour, s);
+  else smooth_fine_t<float>(P, colour, s);
 }
 
 void mg_precondition(Problem& P, const double* v, const double* vscale, double* z, cudaStream_t s) {
@@ -366,18 +551,26 @@ void mg_coarse_factor(Problem& P, cudaStream_t s) {
   if (nu <= 0) return;
   const int Tn = 256;
   IIM_LAUNCH(k_unknown_flag, ceil_div(C.g.N, Tn), Tn, 0, s, C.g, C.aux, C.flag);
-  scan_exclusive(C.flag, C.idx, C.g.N, P.d_counts + 7, P.scan_scratch, s);
+  scan_exclusive(C.flag, C.idx, C.g.N, P.d_counts + kCountCoarse, P.scan_scratch, s);
   int32_t* inv = C.flag;            // reuse: node -> unknown index
   IIM_LAUNCH(k_coarse_map, ceil_div(C.g.N, Tn), Tn, 0, s, C.g, C.aux, C.idx, P.coarse_map, inv);
   LevelView<double> V = view<double>(C);
   if (P.opt.mg_precision == IIM_MG_FP64) {
     IIM_LAUNCH(k_coarse_assemble<double>, ceil_div(nu, 128), 128, 0, s, V, P.coarse_map, nu, inv, P.coarse_lu64);
-    IIM_LAUNCH(k_coarse_lu<double>, 1, 1024, 0, s, P.coarse_lu64, nu, P.coarse_piv,
-               P.coarse_lu64 + (size_t)nu * nu, P.d_status);
+    size_t sm = sizeof(double) * (size_t)nu * nu;
+    int in_smem = sm <= 200 * 1024;
+    if (2 * sm <= 200 * 1024) { in_smem = 2; sm *= 2; }
+    if (in_smem) cudaFuncSetAttribute(k_coarse_lu<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    IIM_LAUNCH(k_coarse_lu<double>, 1, 1024, in_smem ? sm : 0, s, P.coarse_lu64, nu, P.coarse_piv,
+               P.coarse_lu64 + (size_t)nu * nu, P.d_status, in_smem);
   } else {
     IIM_LAUNCH(k_coarse_assemble<float>, ceil_div(nu, 128), 128, 0, s, V, P.coarse_map, nu, inv, P.coarse_lu32);
-    IIM_LAUNCH(k_coarse_lu<float>, 1, 1024, 0, s, P.coarse_lu32, nu, P.coarse_piv, P.coarse_lu32 + (size_t)nu * nu,
-               P.d_status);
+    size_t sm = sizeof(float) * (size_t)nu * nu;
+    int in_smem = sm <= 200 * 1024;
+    if (2 * sm <= 200 * 1024) { in_smem = 2; sm *= 2; }
+    if (in_smem) cudaFuncSetAttribute(k_coarse_lu<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    IIM_LAUNCH(k_coarse_lu<float>, 1, 1024, in_smem ? sm : 0, s, P.coarse_lu32, nu, P.coarse_piv,
+               P.coarse_lu32 + (size_t)nu * nu, P.d_status, in_smem);
   }
 }
 

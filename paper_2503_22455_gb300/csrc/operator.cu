@@ -39,21 +39,26 @@ __global__ void __launch_bounds__(256) k_ho_stencil(GridView g, StencilCoef C, i
   double acc = C.c0[sig] * u[i];
 #pragma unroll
   for (int j = 1; j <= W; ++j) {
-    double s = 0.0;
+    double v[2 * D];
 #pragma unroll
     for (int ax = 0; ax < D; ++ax) {
       const int64_t st = ax == 0 ? 1 : (ax == 1 ? (int64_t)n : (int64_t)n * n);
+      v[2 * ax] = 0.0;
+      v[2 * ax + 1] = 0.0;
       if (m[ax] - j >= 0) {
         int64_t nb = i - j * st;
-        double v = u[nb];
-        s += phase[nb] == ph ? v : 0.0;
+        double t = u[nb];
+        v[2 * ax] = phase[nb] == ph ? t : 0.0;
       }
       if (m[ax] + j < n) {
         int64_t nb = i + j * st;
-        double v = u[nb];
-        s += phase[nb] == ph ? v : 0.0;
+        double t = u[nb];
+        v[2 * ax + 1] = phase[nb] == ph ? t : 0.0;
       }
     }
+    double s = v[0];
+#pragma unroll
+    for (int k = 1; k < 2 * D; ++k) s += v[k];
     acc = fma(C.cj[sig][j - 1], s, acc);
   }
   w[i] = acc;
@@ -227,7 +232,7 @@ static StencilCoef stencil_coef(const Problem& P) {
   return C;
 }
 
-void ho_apply(Problem& P, const double* u, double* w, bool with_data, cudaStream_t s) {
+void ho_stencil(Problem& P, const double* u, double* w, cudaStream_t s) {
   const GridView& g = P.g;
   const int T = 256;
   const int iface = P.desc.bc == IIM_BC_INTERFACE;
@@ -240,6 +245,11 @@ void ho_apply(Problem& P, const double* u, double* w, bool with_data, cudaStream
     if (P.w == 2) IIM_LAUNCH((k_ho_stencil<3, 2>), grid, T, 0, s, g, C, iface, u, P.phase, w);
     else IIM_LAUNCH((k_ho_stencil<3, 3>), grid, T, 0, s, g, C, iface, u, P.phase, w);
   }
+}
+
+void ho_ghost(Problem& P, const double* u, bool with_data, cudaStream_t s) {
+  const int T = 256;
+  const int iface = P.desc.bc == IIM_BC_INTERFACE;
   GhostParams GP;
   GP.nfit = P.nfit_cap;
   GP.w = P.w;
@@ -259,6 +269,11 @@ void ho_apply(Problem& P, const double* u, double* w, bool with_data, cudaStream
   GP.j1 = P.d_j1;
   GP.G = P.G;
   if (P.K_cap > 0) IIM_LAUNCH(k_ho_ghost, ceil_div((int64_t)P.K_cap * 32, T), T, 0, s, GP, u);
+}
+
+void ho_correct(Problem& P, const double* u, double* w, bool with_data, cudaStream_t s) {
+  const GridView& g = P.g;
+  const int T = 256;
   CorrectParams CP;
   CP.g = g;
   CP.w = P.w;
@@ -280,6 +295,12 @@ void ho_apply(Problem& P, const double* u, double* w, bool with_data, cudaStream
   for (int k = 0; k < kMaxW; ++k)
     for (int mm = 0; mm < 8; ++mm) CP.box_w[k][mm] = P.box_w[k][mm];
   if (P.aff_cap > 0) IIM_LAUNCH(k_ho_correct, ceil_div(P.aff_cap, T), T, 0, s, CP, u, w);
+}
+
+void ho_apply(Problem& P, const double* u, double* w, bool with_data, cudaStream_t s) {
+  ho_stencil(P, u, w, s);
+  ho_ghost(P, u, with_data, s);
+  ho_correct(P, u, w, with_data, s);
 }
 
 __global__ void k_rhs_finish(GridView g, int interface_, const uint8_t* __restrict__ phase,

@@ -39,17 +39,27 @@ __global__ void k_edge_flags(GridView g, const uint8_t* __restrict__ phase, int3
   flag[e] = f;
 }
 
-__global__ void k_crossings(Geom G, GridView g, const int32_t* __restrict__ flag, const int32_t* __restrict__ id,
-                            const uint8_t* __restrict__ phase, int cap, int32_t* cr_axis, int32_t* cr_lo,
-                            uint8_t* cr_loplus, double* cr_t, double* cr_x, double* cr_n, double* cr_kappa,
-                            int* status) {
+// cut edges -> compact list in canonical order (axis, lower node)
+__global__ void k_compact(const int32_t* __restrict__ flag, const int32_t* __restrict__ id, int64_t len, int cap,
+                          int32_t* __restrict__ list, int* status) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= g.N * g.dim || !flag[e]) return;
+  if (e >= len || !flag[e]) return;
   int c = id[e];
   if (c >= cap) {
     set_status(status, IIM_ERR_CAPACITY);
     return;
   }
+  list[c] = (int32_t)e;
+}
+
+// one thread per control point, so that the FP64 root solves run on full warps
+__global__ void k_crossings(Geom G, GridView g, const int32_t* __restrict__ edges, const int* __restrict__ K, int cap,
+                            const uint8_t* __restrict__ phase, int32_t* cr_axis, int32_t* cr_lo,
+                            uint8_t* cr_loplus, double* cr_t, double* cr_x, double* cr_n, double* cr_kappa,
+                            int* status) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= *K || c >= cap) return;
+  const int64_t e = edges[c];
   int ax = (int)(e / g.N);
   int64_t i = e - (int64_t)ax * g.N;
   int m[3];
@@ -502,14 +512,14 @@ __global__ void k_sw_classify(SWParams P, const uint8_t* __restrict__ phase, int
   flag[i] = f;
 }
 
-__global__ void k_sw_fill(SWParams P, const uint8_t* __restrict__ phase, const int32_t* __restrict__ flag,
-                          const int32_t* __restrict__ idx, int cap, int32_t* __restrict__ aux, double* tab64,
+// one thread per irregular node (compacted), so that the FP64 root solves run on full warps
+__global__ void k_sw_fill(SWParams P, const uint8_t* __restrict__ phase, const int32_t* __restrict__ list,
+                          const int* __restrict__ count, int cap, int32_t* __restrict__ aux, double* tab64,
                           float* tab32, int* status) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const GridView& g = P.g;
-  if (i >= g.N || !flag[i]) return;
-  int r = idx[i];
-  if (r >= cap) { set_status(status, IIM_ERR_CAPACITY); return; }
+  if (r >= *count || r >= cap) return;
+  const int64_t i = list[r];
   int m[3];
   node_index(g, i, m);
   const int D = 2 * g.dim + 1;
@@ -575,7 +585,9 @@ iim_status setup_geometry(Problem& P, bool size_only) {
   IIM_LAUNCH(k_edge_flags, ceil_div(g.N * g.dim, T), T, 0, s, g, P.phase, P.edge_flag);
   scan_exclusive(P.edge_flag, P.edge_id, g.N * g.dim, P.d_counts + 0, P.scan_scratch, s);
   if (size_only) return IIM_OK;
-  IIM_LAUNCH(k_crossings, ceil_div(g.N * g.dim, T), T, 0, s, P.geom, g, P.edge_flag, P.edge_id, P.phase, P.K_cap,
+  IIM_LAUNCH(k_compact, ceil_div(g.N * g.dim, T), T, 0, s, P.edge_flag, P.edge_id, g.N * g.dim, P.K_cap, P.cr_edge,
+             P.d_status);
+  IIM_LAUNCH(k_crossings, ceil_div(P.K_cap, 128), 128, 0, s, P.geom, g, P.cr_edge, P.d_counts + 0, P.K_cap, P.phase,
              P.cr_axis, P.cr_lo, P.cr_loplus, P.cr_t, P.cr_x, P.cr_n, P.cr_kappa, P.d_status);
   IIM_LAUNCH(k_curvature_check, ceil_div(P.K_cap, T), T, 0, s, P.cr_kappa, P.d_counts + 0, g.h, P.d_status);
   WalkParams W{g, P.w, P.q, P.desc.bc == IIM_BC_INTERFACE, P.desc.box_bc};
@@ -644,8 +656,10 @@ iim_status setup_levels(Problem& P, bool size_only) {
     IIM_LAUNCH(k_sw_classify, ceil_div(L.g.N, T), T, 0, P.stream, S, L.phase, L.aux, L.flag, P.d_status);
     scan_exclusive(L.flag, L.idx, L.g.N, P.d_counts + 2 + (int)l, P.scan_scratch, P.stream);
     if (size_only) continue;
-    IIM_LAUNCH(k_sw_fill, ceil_div(L.g.N, T), T, 0, P.stream, S, L.phase, L.flag, L.idx, L.irr_cap, L.aux, L.tab64,
-               L.tab32, P.d_status);
+    IIM_LAUNCH(k_compact, ceil_div(L.g.N, T), T, 0, P.stream, L.flag, L.idx, L.g.N, L.irr_cap, L.irr_node,
+               P.d_status);
+    IIM_LAUNCH(k_sw_fill, ceil_div(L.irr_cap, 128), 128, 0, P.stream, S, L.phase, L.irr_node, P.d_counts + 2 + (int)l,
+               L.irr_cap, L.aux, L.tab64, L.tab32, P.d_status);
   }
   return IIM_OK;
 }

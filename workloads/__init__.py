@@ -403,3 +403,26 @@ def serving_trace(count: int = 2000, rate: float = 200.0, seed: int = 22455,
                                solution=sol, name=f"req{i}")
         out.append((float(t[i]), spec))
     return out
+
+
+def star_interface_variant(n: int, step: int, seed: int = 2503) -> ProblemSpec:
+    """The 1024^2 star interface problem with a seeded variant of its manufactured solution.
+
+    Same geometry and coefficients as ``star_interface_1024``; u- = sin(pi x + a) cos(pi y + b),
+    u+ = exp(x + y)/4 + c (a, b, c drawn per step), so every step solves a new system.
+    """
+    rng = np.random.default_rng([seed, step])
+    a, b = rng.uniform(0, 2 * np.pi, size=2)
+    c = rng.uniform(-0.5, 0.5)
+    pi = math.pi
+    um = lambda X: np.sin(pi * X[..., 0] + a) * np.cos(pi * X[..., 1] + b)
+    gm = lambda X: np.stack([pi * np.cos(pi * X[..., 0] + a) * np.cos(pi * X[..., 1] + b),
+                             -pi * np.sin(pi * X[..., 0] + a) * np.sin(pi * X[..., 1] + b)], axis=-1)
+    lm = lambda X: -2 * pi * pi * um(X)
+    up = lambda X: np.exp(X[..., 0] + X[..., 1]) / 4 + c
+    gp = lambda X: np.stack([np.exp(X[..., 0] + X[..., 1]) / 4] * 2, axis=-1)
+    lp = lambda X: np.exp(X[..., 0] + X[..., 1]) / 2
+    spec = star_interface_1024(n)
+    spec.solution = Manufactured(up, gp, lp, um, gm, lm)
+    spec.name = f"star_interface_{n}_step{step}"
+    return spec
