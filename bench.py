@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-roofline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="host-driven FGMRES loop (for kernel-level profiling)")
+    ap.add_argument("--batch", type=int, default=8, help="independent problems solved concurrently per step")
     return ap.parse_args()
 
 
@@ -112,8 +113,8 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_inputs(P, steps, n, rank):
-    """Per-step data at the problem's own control points (fixed geometry)."""
+def make_inputs(P, steps, n, rank, index=0, batch=1):
+    """Per-step data at the problem's own control points (fixed geometry per problem)."""
     import numpy as np
     import torch
 
@@ -125,7 +126,7 @@ def make_inputs(P, steps, n, rank):
     plus = W.from_flat(phase, n, 2)
     dev_in, host_in, specs = [], [], []
     for s in range(steps):
-        spec = W.star_interface_variant(n, s + 1000 * rank)
+        spec = W.star_interface_variant(n, s + 1000 * (rank * batch + index), angle=star_angle(index, batch))
         f = W.to_flat(W.source_term(spec, X, plus))
         g, j0, j1 = W.boundary_data(spec, xc, nc)
         box = W.box_data(spec)
@@ -134,6 +135,12 @@ def make_inputs(P, steps, n, rank):
         host_in.append(host)
         specs.append(spec)
     return dev_in, host_in, specs
+
+
+def star_angle(index, batch):
+    """Problem i of a batch solves the star rotated by 2 pi i / (5 batch)."""
+    import math
+    return 2 * math.pi * index / (5 * max(batch, 1))
 
 
 def run_ours(args):
@@ -154,27 +161,43 @@ def run_ours(args):
         iim.load()
     import workloads as W
 
-    n = args.n
+    n, B = args.n, max(1, args.batch)
     K, Wm = args.steps, args.warmup
-    stream = torch.cuda.current_stream()
-    base = W.star_interface_1024(n)
-    P = iim.Problem(iim.desc_from_spec(base), iim.default_options(tol=1e-10, mg_precision=iim.MG_FP32,
-                                                                  use_graph=0 if args.no_graph else 1), stream)
-    dev_in, host_in, specs = make_inputs(P, Wm + K, n, rank)
-    x = torch.zeros(P.N, dtype=torch.float64, device="cuda")
+    main = torch.cuda.current_stream()
+    streams = [torch.cuda.Stream() for _ in range(B)]
+    specs0 = [W.star_interface_1024(n, phase=star_angle(i, B)) for i in range(B)]
+    opts = iim.default_options(tol=1e-10, mg_precision=iim.MG_FP32, use_graph=0 if args.no_graph else 1)
+    probs = [iim.Problem(iim.desc_from_spec(sp), opts, st) for sp, st in zip(specs0, streams)]
+    inputs = [make_inputs(P, Wm + K, n, rank, i, B) for i, P in enumerate(probs)]
+    xs = [torch.zeros(P.N, dtype=torch.float64, device="cuda") for P in probs]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2 (129 MB)
+    torch.cuda.synchronize()
 
-    def step(s, prob):
+    def step(s, problems, xvec):
+        """Set-up + data + solve of every problem of the batch, concurrently on their streams."""
         l0 = iim.launch_count()
-        prob.setup()
-        f, j0, j1, box = dev_in[s]
-        prob.set_data(f, None, j0, j1, box)
-        x.zero_()
-        _, info = prob.solve(x)
-        return info, iim.launch_count() - l0 - 1 + info.kernels   # graph launch counted once by the host
+        start = torch.cuda.Event()
+        start.record(main)
+        for i, P in enumerate(problems):
+            st = streams[i]
+            st.wait_event(start)
+            with torch.cuda.stream(st):
+                P.setup()
+                f, j0, j1, box = inputs[i][0][s]
+                P.set_data(f, None, j0, j1, box)
+                xvec[i].zero_()
+        if len(problems) == 1 and args.no_graph:
+            _, info = problems[0].solve(xvec[0])
+            infos = [info]
+        else:
+            infos, _ = iim.batch_solve(problems, xvec)
+        for st in streams[:len(problems)]:
+            main.wait_stream(st)
+        kern = iim.launch_count() - l0 - sum(1 for _ in infos) + sum(inf.kernels for inf in infos)
+        return infos, kern
 
     for s in range(Wm):
-        step(s, P)
+        step(s, probs, xs)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -185,13 +208,14 @@ def run_ours(args):
     torch.cuda.nvtx.range_push("timed")
     for k in range(K):
         flush.zero_()
-        ev[k][0].record(stream)
-        info, nl = step(Wm + k, P)
-        ev[k][1].record(stream)
-        iters.append(info.iters)
+        ev[k][0].record(main)
+        infos, nl = step(Wm + k, probs, xs)
+        ev[k][1].record(main)
         launches += nl
-        if not info.converged:
-            raise RuntimeError(f"step {k} did not converge: {info.as_dict()}")
+        for inf in infos:
+            iters.append(inf.iters)
+            if not inf.converged:
+                raise RuntimeError(f"step {k} did not converge: {inf.as_dict()}")
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     clk = clocks.stop()
@@ -200,23 +224,33 @@ def run_ours(args):
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
-    value = world * K / (total_ms / 1e3)
+    value = world * B * K / (total_ms / 1e3)
 
-    # accuracy of the last step against its manufactured solution
-    spec = specs[Wm + K - 1]
-    ph = P.phase().cpu().numpy().astype(bool)
+    # accuracy of the last step of problem 0 against its manufactured solution
+    spec = inputs[0][2][Wm + K - 1]
+    ph = probs[0].phase().cpu().numpy().astype(bool)
     Xn = W.node_coords(n, 2)
     ex = W.to_flat(np.where(W.from_flat(ph, n, 2), spec.solution.u_plus(Xn), spec.solution.u_minus(Xn)))
-    err_exact = float(np.max(np.abs(x.cpu().numpy() - ex)))
+    err_exact = float(np.max(np.abs(xs[0].cpu().numpy() - ex)))
 
-    # the all-FP64 form (FP64 multigrid) for the FP32-MG vs FP64 comparison
+    # latency of one solve (batch of one, the same problem)
+    lat = []
+    for k in range(min(K, 5)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(main)
+        step(Wm + k, probs[:1], xs[:1])
+        b.record(main)
+        torch.cuda.synchronize()
+        lat.append(a.elapsed_time(b))
+
     fp64_form = None
     if args.fp64_steps > 0:
-        fp64_form = fp64_run(args, iim, torch, base, stream, step, flush, Wm, x, ph, Xn, specs, W, np)
+        fp64_form = fp64_run(args, iim, torch, specs0, streams, inputs, step, flush, Wm, main)
     e2e = None
     if not args.no_e2e:
-        e2e = e2e_run(P, torch, host_in, Wm, K, world)
-    roof = None if args.no_roofline else roofline(P, iim, torch, stream)
+        e2e = e2e_run(probs, torch, inputs, Wm, K, world, main)
+    roof = None if args.no_roofline else roofline(probs[0], iim, torch, main)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(n, statistics.mean(iters))
@@ -226,9 +260,10 @@ def run_ours(args):
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "mg_dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "order": 6, "bc": "interface", "box": "dirichlet",
-                   "geometry": "star r=0.5+0.1 sin(5 theta)", "tol": 1e-10, "krylov": "FGMRES(10), right",
-                   "preconditioner": "SW multigrid V(2,2), fp32", "l2": "flushed between steps",
-                   "step": "setup+data+solve"},
+                   "geometry": "star r=0.5+0.1 sin(5 theta), rotated per problem", "tol": 1e-10,
+                   "krylov": "FGMRES(10), right", "preconditioner": "SW multigrid V(2,2), fp32",
+                   "batch": B, "l2": "flushed between steps", "step": "per problem: setup+data+solve"},
+        "latency_ms_single_solve": statistics.median(lat),
         "iters_mean": statistics.mean(iters), "err_vs_exact": err_exact,
         "fp64_form": fp64_form,
         "e2e": e2e,
@@ -247,41 +282,50 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def fp64_run(args, iim, torch, base, stream, step, flush, Wm, x, ph, Xn, specs, W, np):
-    P64 = iim.Problem(iim.desc_from_spec(base), iim.default_options(tol=1e-10, mg_precision=iim.MG_FP64), stream)
-    step(0, P64)
-    t64, it64 = [], []
+def fp64_run(args, iim, torch, specs0, streams, inputs, step, flush, Wm, main):
+    """The all-FP64 form (FP64 multigrid), same batch and inputs."""
+    import statistics as st
+    opts = iim.default_options(tol=1e-10, mg_precision=iim.MG_FP64)
+    probs = [iim.Problem(iim.desc_from_spec(sp), opts, s) for sp, s in zip(specs0, streams)]
+    xs = [torch.zeros(P.N, dtype=torch.float64, device="cuda") for P in probs]
+    step(0, probs, xs)
+    t, it = [], []
     for k in range(args.fp64_steps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        info, _ = step(Wm + k, P64)
-        b.record(stream)
+        a.record(main)
+        infos, _ = step(Wm + k, probs, xs)
+        b.record(main)
         torch.cuda.synchronize()
-        t64.append(a.elapsed_time(b))
-        it64.append(info.iters)
-    n = base.n
-    last = specs[Wm + args.fp64_steps - 1]
-    ex = W.to_flat(np.where(W.from_flat(ph, n, 2), last.solution.u_plus(Xn), last.solution.u_minus(Xn)))
-    out = {"value": 1e3 / statistics.mean(t64), "unit": "solves/s", "iters": statistics.mean(it64),
-           "err_vs_exact": float(np.max(np.abs(x.cpu().numpy() - ex)))}
-    P64.close()
-    return out
+        t.append(a.elapsed_time(b))
+        it += [inf.iters for inf in infos]
+    for P in probs:
+        P.close()
+    return {"value": len(probs) * 1e3 / st.mean(t), "unit": "solves/s", "iters": st.mean(it)}
 
 
-def e2e_run(P, torch, host_in, Wm, K, world):
-    """End to end through the host-buffer entry point: H2D of the step's inputs, D2H of x."""
-    xh = torch.empty(P.N, dtype=torch.float64).pin_memory()
+def e2e_run(probs, torch, inputs, Wm, K, world, main):
+    """End to end through the host-buffer entry point (one host thread per problem):
+    H2D of every step's inputs and D2H of x inside the timed region."""
+    import concurrent.futures as cf
+    xh = [torch.empty(P.N, dtype=torch.float64).pin_memory() for P in probs]
+
+    def one(i, k):
+        P = probs[i]
+        f, j0, j1, box = inputs[i][1][Wm + k]
+        P.setup()
+        P.solve_host(f, None, j0, j1, box, x=xh[i])
+
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for k in range(K):
-        f, j0, j1, box = host_in[Wm + k]
-        P.setup()
-        P.solve_host(f, None, j0, j1, box, x=xh)
+    with cf.ThreadPoolExecutor(max_workers=len(probs)) as ex:
+        for k in range(K):
+            list(ex.map(lambda i: one(i, k), range(len(probs))))
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    h2d = sum(t.numel() * 8 for t in host_in[Wm])
-    return {"value": world * K / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": P.N * 8}
+    h2d = sum(t.numel() * 8 for t in inputs[0][1][Wm])
+    return {"value": world * len(probs) * K / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": h2d * len(probs),
+            "d2h_bytes_per_step": probs[0].N * 8 * len(probs)}
 
 
 def roofline(P, iim, torch, stream):

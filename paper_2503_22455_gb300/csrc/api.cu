@@ -285,6 +285,7 @@ iim_status iim_problem_create(const iim_problem_desc* desc, const iim_options* o
   const bool iface = desc->bc == IIM_BC_INTERFACE;
   P.nfit_cap = iface ? 2 * P.K_cap : P.K_cap;
   IIM_ALLOC(P.fit_R, int32_t, P.nfit_cap);
+  IIM_ALLOC(P.fit_overflow, int, P.nfit_cap);
   IIM_ALLOC(P.fit_nodes, int32_t, (size_t)P.nfit_cap * P.rcap);
   IIM_ALLOC(P.fit_coef, double, (size_t)P.nfit_cap * (P.w + 1) * P.rcap);
   IIM_ALLOC(P.fit_cdat, double, (size_t)P.nfit_cap * (P.w + 1));
@@ -354,6 +355,10 @@ iim_status iim_problem_create(const iim_problem_desc* desc, const iim_options* o
     cudaMemcpy(aux.data(), C.aux, sizeof(int32_t) * C.g.N, cudaMemcpyDeviceToHost);
     int nu = 0;
     for (auto a : aux) nu += a != -2;
+    if (nu > 4096) {
+      set_error("the coarsest multigrid level has more than 4096 unknowns: choose n with more factors of 2");
+      IIM_FAIL(IIM_ERR_INVALID_ARG);
+    }
     P.coarse_nu = nu;
     IIM_ALLOC(P.coarse_map, int32_t, nu > 0 ? nu : 1);
     IIM_ALLOC(P.coarse_piv, int32_t, nu > 0 ? nu : 1);

@@ -65,6 +65,7 @@ struct Problem {
   // fits: boundary problems one per crossing (Omega+ side); interface two (2c: +, 2c+1: -)
   int nfit = 0, nfit_cap = 0;
   int32_t* fit_R = nullptr;       // [nfit]
+  int* fit_overflow = nullptr;    // [nfit] fits the warp kernel hands to the CTA kernel
   int32_t* fit_nodes = nullptr;   // [nfit][rcap]
   double* fit_coef = nullptr;     // [nfit][w+1][rcap]
   double* fit_cdat = nullptr;     // [nfit][w+1]

@@ -9,8 +9,8 @@
 //   MODE 2  prolongation + correction, first post-smoothing sweep
 //   MODE 3  last post-smoothing sweep; on the finest level z = (double) u
 //   MODE 4  one plain sweep (only when nu > 2)
-// Coarse tail: every level with at most 4096 nodes and the dense coarse solve
-// run in a single CTA with the whole sub-hierarchy in shared memory.
+// Coarse tail: every level with at most 1024 nodes (one per thread) and the dense
+// coarse solve run in a single CTA with the whole sub-hierarchy in shared memory.
 #pragma once
 
 namespace iim {
@@ -109,7 +109,8 @@ __global__ void __launch_bounds__(256) k_mg2d(Fine2DParams<T> P) {
   }
   __syncthreads();
   if (MODE == 2) {
-    // u += P e_coarse on margin 2
+    // u += P e_coarse on margin 2.  The coarse u is 0 at coarse non-unknowns, so the
+    // bilinear form needs no aux; the Neumann mean counts in-domain neighbours.
     const LevelK<T>& C = P.C;
     for (int e = threadIdx.x; e < S; e += blockDim.x) {
       const int sx = e % SX, sy = e / SX;
@@ -118,20 +119,24 @@ __global__ void __launch_bounds__(256) k_mg2d(Fine2DParams<T> P) {
       const int gx = x0 + sx, gy = y0 + sy;
       const int I0 = gx >> 1, I1 = gy >> 1;
       const int s0 = (gx & 1) ? 1 : -1, s1 = (gy & 1) ? 1 : -1;
-      T acc = 0;
-      int cnt = 0;
+      T ev[4];
+      int ok[4];
 #pragma unroll
       for (int sel = 0; sel < 4; ++sel) {
-        const int b0 = sel & 1, b1 = sel >> 1;
-        const int c0 = I0 + b0 * s0, c1 = I1 + b1 * s1;
-        if (c0 < 0 || c0 >= C.n || c1 < 0 || c1 >= C.n) continue;
+        const int c0 = I0 + (sel & 1) * s0, c1 = I1 + (sel >> 1) * s1;
+        ok[sel] = c0 >= 0 && c0 < C.n && c1 >= 0 && c1 < C.n;
         const int64_t ci = (int64_t)c1 * C.n + c0;
-        if (C.aux[ci] == -2) continue;
-        const T ev = P.uc[ci];
-        if (P.neumann) { acc += ev; ++cnt; }
-        else acc += (b0 ? (T)0.25 : (T)0.75) * (b1 ? (T)0.25 : (T)0.75) * ev;
+        ev[sel] = ok[sel] ? P.uc[ci] : (T)0;
+        if (P.neumann) ok[sel] = ok[sel] && C.aux[ci] != -2;
       }
-      if (P.neumann) acc = cnt > 0 ? acc / (T)cnt : (T)0;
+      T acc;
+      if (P.neumann) {
+        int cnt = ok[0] + ok[1] + ok[2] + ok[3];
+        acc = cnt > 0 ? ((ok[0] ? ev[0] : 0) + (ok[1] ? ev[1] : 0) + (ok[2] ? ev[2] : 0) + (ok[3] ? ev[3] : 0)) / (T)cnt
+                      : (T)0;
+      } else {
+        acc = (T)0.5625 * ev[0] + (T)0.1875 * ev[1] + (T)0.1875 * ev[2] + (T)0.0625 * ev[3];
+      }
       us[e] += acc;
     }
     __syncthreads();
@@ -319,27 +324,27 @@ __global__ void __launch_bounds__(kTailThreads) k_vcycle_tail(TailParams<T> P) {
     }
   }
   __syncthreads();
+  // thread tid owns nodes tid, tid + blockDim.x, ... of every level (one node when N <= blockDim.x)
   auto sweep = [&](int k, int colour, bool from_zero) {
     const LevelK<T>& L = P.L[k];
     T* u = su + P.off[k];
     const T* f = sf + P.off[k];
-    const int* aux = sa + P.off[k];
     const T* tb = table(k);
-    NodeWalk w(L.n, L.dim, tid, nt);
-    for (int i = tid; i < L.N; i += nt, w.advance()) {
-      const int m[3] = {w.i0, w.i1, w.i2};
-      const int a = aux[i];
+    const int n = L.n;
+    for (int i = tid; i < L.N; i += blockDim.x) {
+      const int a = sa[P.off[k] + i];
+      const int m[3] = {i % n, L.dim > 2 ? (i / n) % n : i / n, L.dim > 2 ? i / (n * n) : 0};
       if (((m[0] + m[1] + m[2]) & 1) != colour) {
         if (from_zero) u[i] = 0;
-        continue;
-      }
-      if (a == -2) { u[i] = 0; continue; }
-      const T s = from_zero ? (T)0 : tail_offdiag(L, tb, u, i, m, a);
-      if (a == -1) {
-        u[i] = (f[i] - s) * L.inv_dreg;
+      } else if (a == -2) {
+        u[i] = 0;
       } else {
-        const T dg = tabd(tb, L.dim, a, 0);
-        u[i] = dg != (T)0 ? (f[i] - s) / dg : (T)0;
+        const T s = from_zero ? (T)0 : tail_offdiag(L, tb, u, i, m, a);
+        if (a == -1) u[i] = (f[i] - s) * L.inv_dreg;
+        else {
+          const T dg = tabd(tb, L.dim, a, 0);
+          u[i] = dg != (T)0 ? (f[i] - s) / dg : (T)0;
+        }
       }
     }
     __syncthreads();

@@ -363,10 +363,11 @@ static LevelView<T> view(const Level& L) {
   return v;
 }
 
-// first level handled by the single-CTA tail: the first with at most 4096 nodes
+// first level handled by the single-CTA tail: the first with at most kTailThreads
+// nodes, so that each thread of the tail owns at most one node per level
 static size_t tail_start(const Problem& P) {
   size_t l = 0;
-  while (l + 1 < P.lv.size() && P.lv[l].g.N > 4096) ++l;
+  while (l + 1 < P.lv.size() && P.lv[l].g.N > kTailThreads) ++l;
   return l;
 }
 

@@ -78,75 +78,73 @@ struct GhostParams {
   double* G;                // [nfit][w]
 };
 
-// one warp per crossing (interface: both sides) or per fit (boundary problems)
+// Eight lanes per control point: each lane accumulates an eighth of the X_c terms
+// of every row (sequential FMAs, no per-term reduction), then two shuffle steps
+// combine the quarters.  Boundary problems: rows 0..w-1 of fit c.  Interface
+// problems: rows 0..w of fits 2c (+) and 2c+1 (-), then the closure of Eqs. 9-11.
+constexpr int kGhostLanes = 8;
+
+__device__ inline double quad_sum(double v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 4, kGhostLanes);
+  v += __shfl_xor_sync(0xffffffffu, v, 2, kGhostLanes);
+  v += __shfl_xor_sync(0xffffffffu, v, 1, kGhostLanes);
+  return v;
+}
+
+template <int W>
 __global__ void __launch_bounds__(256) k_ho_ghost(GhostParams P, const double* __restrict__ u) {
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = gid / kGhostLanes, q = gid % kGhostLanes;
   const int K = *P.K;
-  const int rows = P.w + 1;
-  if (!P.interface_) {
-    if (warp >= K) return;
-    const int f = warp;
-    const int R = P.fit_R[f];
-    const int32_t* nodes = P.fit_nodes + (size_t)f * P.rcap;
-    const double* coef = P.fit_coef + (size_t)f * rows * P.rcap;
-    double acc[kMaxW];
+  const bool live = c < K;                       // every lane takes part in the shuffles
+  const int rows = W + 1;
+  const int nsides = P.interface_ ? 2 : 1;
+  double acc[2][W + 1];
 #pragma unroll
-    for (int k = 0; k < kMaxW; ++k) acc[k] = 0.0;
-    for (int a = lane; a < R; a += 32) {
-      double ua = u[nodes[a]];
+  for (int sd = 0; sd < 2; ++sd)
 #pragma unroll
-      for (int k = 0; k < kMaxW; ++k)
-        if (k < P.w) acc[k] = fma(coef[(size_t)k * P.rcap + a], ua, acc[k]);
-    }
-    const double data = P.with_data ? P.g[f] : 0.0;
-#pragma unroll
-    for (int k = 0; k < kMaxW; ++k) {
-      if (k >= P.w) break;
-      double v = warp_sum(acc[k]);
-      if (lane == 0) P.G[(size_t)f * P.w + k] = v + P.fit_cdat[(size_t)f * rows + k] * data;
-    }
-    return;
-  }
-  if (warp >= K) return;
-  const int c = warp;
-  double accs[2][kMaxW + 1];
+    for (int k = 0; k <= W; ++k) acc[sd][k] = 0.0;
 #pragma unroll
   for (int sd = 0; sd < 2; ++sd) {
-    const int f = 2 * c + sd;
+    if (sd >= nsides || !live) continue;
+    const int f = P.interface_ ? 2 * c + sd : c;
     const int R = P.fit_R[f];
     const int32_t* nodes = P.fit_nodes + (size_t)f * P.rcap;
     const double* coef = P.fit_coef + (size_t)f * rows * P.rcap;
+    const int nr = P.interface_ ? W + 1 : W;
+    for (int a = q; a < R; a += kGhostLanes) {
+      const double ua = u[nodes[a]];
 #pragma unroll
-    for (int k = 0; k <= kMaxW; ++k) accs[sd][k] = 0.0;
-    for (int a = lane; a < R; a += 32) {
-      double ua = u[nodes[a]];
-#pragma unroll
-      for (int k = 0; k <= kMaxW; ++k)
-        if (k <= P.w) accs[sd][k] = fma(coef[(size_t)k * P.rcap + a], ua, accs[sd][k]);
+      for (int k = 0; k <= W; ++k)
+        if (k < nr) acc[sd][k] = fma(coef[(size_t)k * P.rcap + a], ua, acc[sd][k]);
     }
+  }
 #pragma unroll
-    for (int k = 0; k <= kMaxW; ++k) accs[sd][k] = warp_sum(accs[sd][k]);
+  for (int sd = 0; sd < 2; ++sd)
+#pragma unroll
+    for (int k = 0; k <= W; ++k)
+      if (sd < nsides) acc[sd][k] = quad_sum(acc[sd][k]);
+  if (!live || q != 0) return;
+  if (!P.interface_) {
+    const double data = P.with_data ? P.g[c] : 0.0;
+#pragma unroll
+    for (int k = 0; k < W; ++k) P.G[(size_t)c * W + k] = acc[0][k] + P.fit_cdat[(size_t)c * rows + k] * data;
+    return;
   }
   // Eqs. 9-11: S = b+ s+_c - b- s-_c ; ubar = -(b+ D+ - b- D-)/S
   const double *cp = P.fit_cdat + (size_t)(2 * c) * rows, *cm = P.fit_cdat + (size_t)(2 * c + 1) * rows;
   const double bp = P.beta_p, bm = P.beta_m;
-  const double Sden = bp * cp[P.w] - bm * cm[P.w];
-  const double Dp = accs[0][P.w], Dm = accs[1][P.w];
-  const double ubar = -(bp * Dp - bm * Dm) / Sden;
+  const double Sden = bp * cp[W] - bm * cm[W];
+  const double ubar = -(bp * acc[0][W] - bm * acc[1][W]) / Sden;
   double up = ubar, um = ubar;
   if (P.with_data) {
-    up = ubar + (P.j1[c] - bm * cm[P.w] * P.j0[c]) / Sden;
-    um = ubar + (P.j1[c] - bp * cp[P.w] * P.j0[c]) / Sden;
+    up = ubar + (P.j1[c] - bm * cm[W] * P.j0[c]) / Sden;
+    um = ubar + (P.j1[c] - bp * cp[W] * P.j0[c]) / Sden;
   }
-  if (lane < P.w) {
-    int k = lane;
-    double gp = 0, gm = 0;
 #pragma unroll
-    for (int kk = 0; kk < kMaxW; ++kk)
-      if (kk == k) { gp = accs[0][kk]; gm = accs[1][kk]; }
-    P.G[(size_t)(2 * c) * P.w + k] = gp + cp[k] * up;
-    P.G[(size_t)(2 * c + 1) * P.w + k] = gm + cm[k] * um;
+  for (int k = 0; k < W; ++k) {
+    P.G[(size_t)(2 * c) * W + k] = acc[0][k] + cp[k] * up;
+    P.G[(size_t)(2 * c + 1) * W + k] = acc[1][k] + cm[k] * um;
   }
 }
 
@@ -268,7 +266,12 @@ void ho_ghost(Problem& P, const double* u, bool with_data, cudaStream_t s) {
   GP.j0 = P.d_j0;
   GP.j1 = P.d_j1;
   GP.G = P.G;
-  if (P.K_cap > 0) IIM_LAUNCH(k_ho_ghost, ceil_div((int64_t)P.K_cap * 32, T), T, 0, s, GP, u);
+  if (P.K_cap > 0) {
+    // small blocks: a few thousand control points must still spread over all 152 SMs
+    const int grid = ceil_div((int64_t)P.K_cap * kGhostLanes, 64);
+    if (P.w == 2) IIM_LAUNCH(k_ho_ghost<2>, grid, 64, 0, s, GP, u);
+    else IIM_LAUNCH(k_ho_ghost<3>, grid, 64, 0, s, GP, u);
+  }
 }
 
 void ho_correct(Problem& P, const double* u, double* w, bool with_data, cudaStream_t s) {
@@ -294,7 +297,7 @@ void ho_correct(Problem& P, const double* u, double* w, bool with_data, cudaStre
   CP.scale[1] = P.desc.beta_plus / h2;
   for (int k = 0; k < kMaxW; ++k)
     for (int mm = 0; mm < 8; ++mm) CP.box_w[k][mm] = P.box_w[k][mm];
-  if (P.aff_cap > 0) IIM_LAUNCH(k_ho_correct, ceil_div(P.aff_cap, T), T, 0, s, CP, u, w);
+  if (P.aff_cap > 0) IIM_LAUNCH(k_ho_correct, ceil_div(P.aff_cap, 64), 64, 0, s, CP, u, w);
 }
 
 void ho_apply(Problem& P, const double* u, double* w, bool with_data, cudaStream_t s) {

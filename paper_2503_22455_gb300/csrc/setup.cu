@@ -178,6 +178,7 @@ struct FitParams {
   const int32_t* cr_axis;
   const int32_t* cr_lo;
   const uint8_t* cr_loplus;
+  const double* cr_t;
   const double* cr_x;
   const double* cr_n;
   const int* monos;                       // [M][3]
@@ -206,12 +207,13 @@ __device__ inline void better(double& d2, int& fl, double od2, int ofl) {
 // One CTA per fit: gather X_c, scaled-monomial Vandermonde, Householder QR,
 // ghost / derivative rows v^T R^-1 Q^T (Sec. 2.1: one QR per control point,
 // one triangular solve and one product per stencil).
-__global__ void __launch_bounds__(kFitThreads) k_fit(FitParams P) {
+__global__ void __launch_bounds__(kFitThreads) k_fit(FitParams P, const int* __restrict__ only) {
   extern __shared__ double sm[];
   const int f = blockIdx.x;
   const GridView& g = P.g;
   const int c = P.interface_ ? (f >> 1) : f;
   if (c >= *P.K) return;
+  if (only && !only[f]) return;
   const bool sig_plus = P.interface_ ? ((f & 1) == 0) : true;
   const int d = g.dim, n = g.n, M = P.M, LD = P.rcap + 1;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -457,6 +459,516 @@ __global__ void __launch_bounds__(kFitThreads) k_fit(FitParams P) {
   if (tid == 0) set_status(P.status, IIM_ERR_RANK);
 }
 
+// One warp per fit (the common case): rows of X_c up to RW; fits with more rows are
+// flagged in `overflow` and redone by k_fit (one CTA each).  Householder QR with
+// lanes over columns (the Householder vector is broadcast from shared memory),
+// then the w (+1) stencil rows by quarter-warps, one row each.
+struct WarpFitSmem {
+  int RW, LDW, M;
+  __host__ __device__ size_t bytes() const {
+    return sizeof(double) * ((size_t)M * LDW + 4 * LDW + 4 * M + 2 * M + 3 * RW) + sizeof(int) * RW;
+  }
+};
+
+__device__ inline void qw_sum(double& v) {          // sum over the 8 lanes of a quarter-warp
+  v += __shfl_xor_sync(0xffffffffu, v, 4, 8);
+  v += __shfl_xor_sync(0xffffffffu, v, 2, 8);
+  v += __shfl_xor_sync(0xffffffffu, v, 1, 8);
+}
+
+__global__ void __launch_bounds__(128) k_fit_warp(FitParams P, WarpFitSmem L, int* __restrict__ overflow) {
+  extern __shared__ double smw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int f = blockIdx.x * (blockDim.x >> 5) + wib;
+  const GridView& g = P.g;
+  const int nfit_here = P.interface_ ? 2 * (*P.K) : *P.K;
+  if (f >= nfit_here) return;
+  const int c = P.interface_ ? (f >> 1) : f;
+  const bool sig_plus = P.interface_ ? ((f & 1) == 0) : true;
+  const int d = g.dim, n = g.n, M = P.M, LDW = L.LDW, RW = L.RW;
+  double* V = smw + (size_t)wib * (L.bytes() / sizeof(double) + 1);
+  double* S = V + (size_t)M * LDW;         // [4][LDW]
+  double* Y = S + 4 * LDW;                 // [4][M]
+  double* alpha = Y + 4 * M;               // [M] (stores 1/R_kk after the rank test)
+  double* beta = alpha + M;                // [M]
+  double* rel = beta + M;                  // [RW][3]
+  int* nodes = (int*)(rel + 3 * RW);       // [RW]
+  double xc[3] = {0, 0, 0}, nrm[3] = {0, 0, 0};
+  for (int k = 0; k < d; ++k) {
+    xc[k] = P.cr_x[c * d + k];
+    nrm[k] = P.cr_n[c * d + k];
+  }
+  double ns[3];
+  for (int k = 0; k < 3; ++k) ns[k] = sig_plus ? -nrm[k] : nrm[k];
+  const int ax = P.cr_axis[c];
+  const int64_t lo = P.cr_lo[c];
+  const bool lo_sig = (P.cr_loplus[c] != 0) == sig_plus;
+  int cidx[3];
+  for (int k = 0; k < 3; ++k) cidx[k] = k < d ? (int)floor((xc[k] + 1.0) / g.h - 0.5) : 0;
+  for (int grow = 0; grow <= 3; ++grow) {
+    const double an = P.q + 1.0 + 0.5 * grow, at = P.q / 2 + 1.0 + 0.5 * grow;
+    const int rad = (int)ceil(an) + 1;
+    int wlo[3] = {0, 0, 0}, wext[3] = {1, 1, 1};
+    for (int k = 0; k < d; ++k) {
+      wlo[k] = max(0, cidx[k] - rad);
+      wext[k] = min(n, cidx[k] + rad + 2) - wlo[k];
+    }
+    const int total = wext[0] * wext[1] * wext[2];
+    auto position = [&](int p, int* mm) {
+      const int i0 = p % wext[0], r = p / wext[0];
+      mm[0] = wlo[0] + i0;
+      mm[1] = wlo[1] + r % wext[1];
+      mm[2] = wlo[2] + r / wext[1];
+    };
+    // nearest phase-sigma node
+    double bd = 1e300;
+    int bf = 0x7fffffff;
+    for (int p = lane; p < total; p += 32) {
+      int mm[3];
+      position(p, mm);
+      const int64_t fl = mm[0] + (int64_t)n * mm[1] + (int64_t)n * n * mm[2];
+      if ((P.phase[fl] != 0) != sig_plus) continue;
+      double d2 = 0;
+      for (int k = 0; k < d; ++k) {
+        const double rr = (node_x(g, mm[k]) - xc[k]) / g.h;
+        d2 += rr * rr;
+      }
+      better(bd, bf, d2, (int)fl);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double od = __shfl_xor_sync(0xffffffffu, bd, o);
+      const int of = __shfl_xor_sync(0xffffffffu, bf, o);
+      better(bd, bf, od, of);
+    }
+    const int nearest = bf;
+    auto selected = [&](int p, int64_t& fl, double* rr) -> bool {
+      int mm[3];
+      position(p, mm);
+      fl = mm[0] + (int64_t)n * mm[1] + (int64_t)n * n * mm[2];
+      if ((P.phase[fl] != 0) != sig_plus || fl == nearest) return false;
+      double d2 = 0, t = 0;
+      for (int k = 0; k < d; ++k) {
+        rr[k] = (node_x(g, mm[k]) - xc[k]) / g.h;
+        d2 += rr[k] * rr[k];
+        t += rr[k] * ns[k];
+      }
+      const double tau2 = fmax(d2 - t * t, 0.0);
+      return t >= 0.0 && tau2 / (at * at) + t * t / (an * an) <= 1.0;
+    };
+    // ordered compaction: contiguous chunks per lane, warp prefix sum of the counts
+    const int chunk = (total + 31) / 32;
+    const int p0 = lane * chunk, p1 = min(total, p0 + chunk);
+    int my = 0;
+    for (int p = p0; p < p1; ++p) {
+      int64_t fl;
+      double rr[3];
+      my += selected(p, fl, rr);
+    }
+    int incl = my;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int R = __shfl_sync(0xffffffffu, incl, 31);
+    if (R > RW) {
+      if (lane == 0) overflow[f] = 1;
+      return;
+    }
+    {
+      int o = incl - my;
+      for (int p = p0; p < p1; ++p) {
+        int64_t fl;
+        double rr[3] = {0, 0, 0};
+        if (selected(p, fl, rr)) {
+          nodes[o] = (int)fl;
+          for (int k = 0; k < 3; ++k) rel[o * 3 + k] = rr[k];
+          ++o;
+        }
+      }
+    }
+    __syncwarp();
+    const int m = R + 1;
+    if (m < M) continue;
+    for (int e = lane; e < m * M; e += 32) {
+      const int col = e / m, row = e - col * m;
+      V[(size_t)col * LDW + row] = row == 0 ? (col == 0 ? 1.0 : 0.0) : monomial(P.monos + 3 * col, rel + 3 * (row - 1), d);
+    }
+    __syncwarp();
+    // Householder QR, lane j owns columns j and j + 32
+    for (int k = 0; k < M; ++k) {
+      const double* vk = V + (size_t)k * LDW;
+      if (lane == (k & 31)) {
+        double s0 = 0, s1 = 0;
+        int r = k;
+        for (; r + 1 < m; r += 2) { s0 = fma(vk[r], vk[r], s0); s1 = fma(vk[r + 1], vk[r + 1], s1); }
+        if (r < m) s0 = fma(vk[r], vk[r], s0);
+        const double s = s0 + s1;
+        const double x0 = vk[k];
+        const double nr = sqrt(s);
+        const double a = x0 >= 0 ? -nr : nr;
+        const double vtv = 2.0 * (s - x0 * a);
+        V[(size_t)k * LDW + k] = x0 - a;
+        alpha[k] = a;
+        beta[k] = vtv > 0 ? 2.0 / vtv : 0.0;
+      }
+      __syncwarp();
+      const double bk = beta[k];
+      for (int j = lane; j < M; j += 32) {
+        if (j <= k) continue;
+        double* vj = V + (size_t)j * LDW;
+        double s0 = 0, s1 = 0;
+        int r = k;
+        for (; r + 1 < m; r += 2) { s0 = fma(vk[r], vj[r], s0); s1 = fma(vk[r + 1], vj[r + 1], s1); }
+        if (r < m) s0 = fma(vk[r], vj[r], s0);
+        const double sc = (s0 + s1) * bk;
+        for (r = k; r < m; ++r) vj[r] = fma(-sc, vk[r], vj[r]);
+      }
+      __syncwarp();
+    }
+    bool ok;
+    {
+      double mx = 0, mn = 1e300;
+      for (int k = lane; k < M; k += 32) { mx = fmax(mx, fabs(alpha[k])); mn = fmin(mn, fabs(alpha[k])); }
+      for (int o = 16; o > 0; o >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      }
+      ok = (mn >= 1e-8 * mx) && mx > 0;
+    }
+    if (!ok) continue;
+    // stencil rows: quarter-warp t < nt solves for target t (ghost t < w, derivative t = w)
+    const int nt = (P.bc == IIM_BC_DIRICHLET) ? P.w : P.w + 1;
+    const int t = lane >> 3, ql = lane & 7;
+    double* y = Y + t * M;
+    double* srow = S + t * LDW;
+    if (t < nt) {
+      if (t < P.w) {
+        const int step = lo_sig ? 1 : -1;
+        int mlo[3];
+        {
+          int64_t r = lo;
+          mlo[0] = (int)(r % n); r /= n; mlo[1] = (int)(r % n); mlo[2] = d > 2 ? (int)(r / n) : 0;
+        }
+        int gm[3] = {mlo[0], mlo[1], mlo[2]};
+        gm[ax] += (lo_sig ? 1 : 0) + t * step;
+        double xi[3] = {0, 0, 0};
+        for (int k = 0; k < d; ++k) xi[k] = (node_x(g, gm[k]) - xc[k]) / g.h;
+        for (int col = ql; col < M; col += 8) y[col] = monomial(P.monos + 3 * col, xi, d);
+      } else {
+        for (int col = ql; col < M; col += 8) {
+          const int* e = P.monos + 3 * col;
+          double v = 0;
+          if (e[0] + e[1] + e[2] == 1)
+            for (int k = 0; k < d; ++k)
+              if (e[k] == 1) v = nrm[k] / g.h;
+          y[col] = v;
+        }
+      }
+    }
+    __syncwarp();
+    for (int i = 0; i < M; ++i) {                       // y = R^-T c
+      double part = 0;
+      if (t < nt)
+        for (int l = ql; l < i; l += 8) part = fma(V[(size_t)i * LDW + l], y[l], part);
+      qw_sum(part);
+      if (t < nt && ql == 0) y[i] = (y[i] - part) / alpha[i];
+      __syncwarp();
+    }
+    if (t < nt)
+      for (int r = ql; r < m; r += 8) srow[r] = r < M ? y[r] : 0.0;
+    __syncwarp();
+    for (int k = M - 1; k >= 0; --k) {                   // s = H_0 ... H_{M-1} [y; 0]
+      const double* vk = V + (size_t)k * LDW;
+      double dot = 0;
+      if (t < nt)
+        for (int r = k + ql; r < m; r += 8) dot = fma(vk[r], srow[r], dot);
+      qw_sum(dot);
+      dot *= beta[k];
+      if (t < nt)
+        for (int r = k + ql; r < m; r += 8) srow[r] = fma(-dot, vk[r], srow[r]);
+      __syncwarp();
+    }
+    // outputs (same folding as the CTA kernel)
+    const int rows = P.w + 1;
+    double* coef = P.fit_coef + (size_t)f * rows * P.rcap;
+    double* cdat = P.fit_cdat + (size_t)f * rows;
+    if (P.bc == IIM_BC_NEUMANN) {
+      double s2 = 0;
+      for (int r = lane; r < m; r += 32) { const double v = P.beta_p * S[P.w * LDW + r]; s2 += v * v; }
+      s2 = warp_sum(s2);
+      const double Dc = P.beta_p * S[P.w * LDW];
+      if (!(fabs(Dc) >= 1e-12 * sqrt(s2))) {
+        if (lane == 0) set_status(P.status, IIM_ERR_SINGULAR);
+        return;
+      }
+      for (int e = lane; e < P.w * R; e += 32) {
+        const int k = e / R, al = e - k * R;
+        coef[(size_t)k * P.rcap + al] = S[k * LDW + 1 + al] - S[k * LDW] * (P.beta_p * S[P.w * LDW + 1 + al]) / Dc;
+      }
+      if (lane < P.w) cdat[lane] = S[lane * LDW] / Dc;
+    } else {
+      for (int e = lane; e < nt * R; e += 32) {
+        const int k = e / R, al = e - k * R;
+        coef[(size_t)k * P.rcap + al] = S[k * LDW + 1 + al];
+      }
+      if (lane < nt) cdat[lane] = S[lane * LDW];
+    }
+    for (int e = lane; e < R; e += 32) P.fit_nodes[(size_t)f * P.rcap + e] = nodes[e];
+    if (lane == 0) P.fit_R[f] = R;
+    return;
+  }
+  if (lane == 0) overflow[f] = 2;       // the CTA kernel reports IIM_ERR_RANK if it fails as well
+}
+
+// 2D: a quarter-warp (8 lanes, rows over lanes) per fit and four fits per warp in
+// lockstep, so that every FP64 instruction runs on all 32 lanes.  Only the first
+// region size is tried here; fits that need a larger region, have too few or too
+// many rows, or fail the rank test are flagged and redone by k_fit (one CTA each),
+// which applies the same rules.
+constexpr int kQuadRows = 56;          // rows of X_c a quarter-warp holds (typical: 23 for q = 4, 44 for q = 6)
+
+struct QuadFitSmem {
+  int M;
+  __host__ __device__ int LDQ() const { return kQuadRows + 1; }
+  __host__ __device__ size_t doubles() const {
+    return (size_t)M * LDQ() + 4 * LDQ() + 4 * M + 3 * M + 2 * kQuadRows + kQuadRows / 2 + 1;
+  }
+};
+
+__device__ inline void q8_sum(double& v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 4, 8);
+  v += __shfl_xor_sync(0xffffffffu, v, 2, 8);
+  v += __shfl_xor_sync(0xffffffffu, v, 1, 8);
+}
+
+__global__ void __launch_bounds__(32) k_fit_quad(FitParams P, QuadFitSmem Lq, int* __restrict__ overflow) {
+  extern __shared__ double smq[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int qf = lane >> 3, ql = lane & 7;                   // fit slot in the warp, lane in the quarter
+  const int f = (blockIdx.x * (blockDim.x >> 5) + wib) * 4 + qf;
+  const GridView& g = P.g;
+  const int nfit_here = P.interface_ ? 2 * (*P.K) : *P.K;
+  const int M = P.M, LDQ = Lq.LDQ(), n = g.n;
+  double* base = smq + (size_t)(wib * 4 + qf) * Lq.doubles();
+  double* V = base;                      // [M][LDQ]
+  double* S = V + (size_t)M * LDQ;       // [4][LDQ]
+  double* Y = S + 4 * LDQ;               // [4][M]
+  double* alpha = Y + 4 * M;             // [M]
+  double* ialpha = alpha + M;            // [M]
+  double* beta = ialpha + M;             // [M]
+  double* rel = beta + M;                // [kQuadRows][2]
+  int* nodes = (int*)(rel + 2 * kQuadRows);
+  bool active = f < nfit_here;
+  const int c = P.interface_ ? (f >> 1) : f;
+  const bool sig_plus = P.interface_ ? ((f & 1) == 0) : true;
+  double xc[2] = {0, 0}, nrm[2] = {0, 0};
+  int ax = 0;
+  int64_t lo = 0;
+  bool lo_sig = true;
+  if (active) {
+    xc[0] = P.cr_x[2 * c]; xc[1] = P.cr_x[2 * c + 1];
+    nrm[0] = P.cr_n[2 * c]; nrm[1] = P.cr_n[2 * c + 1];
+    ax = P.cr_axis[c];
+    lo = P.cr_lo[c];
+    lo_sig = (P.cr_loplus[c] != 0) == sig_plus;
+  }
+  const double ns0 = sig_plus ? -nrm[0] : nrm[0], ns1 = sig_plus ? -nrm[1] : nrm[1];
+  const double an = P.q + 1.0, at = P.q / 2 + 1.0;
+  const int rad = (int)ceil(an) + 1;
+  int wlo0 = 0, wlo1 = 0, we0 = 1, we1 = 1;
+  if (active) {
+    const int c0 = (int)floor((xc[0] + 1.0) / g.h - 0.5), c1 = (int)floor((xc[1] + 1.0) / g.h - 0.5);
+    wlo0 = max(0, c0 - rad); we0 = min(n, c0 + rad + 2) - wlo0;
+    wlo1 = max(0, c1 - rad); we1 = min(n, c1 + rad + 2) - wlo1;
+  }
+  const int total = active ? we0 * we1 : 0;
+  const double ih = 0.5 * n;                          // 1/h, exact
+  // The phase-sigma node nearest to x_c is the sigma end of the cut edge: every other
+  // node is at least h away while that end is t h <= h away (equality only when x_c
+  // sits on the far node); that degenerate case takes the full search.
+  int nearest;
+  {
+    const double tq = active ? P.cr_t[c] : 0.0;
+    const double dnear = lo_sig ? tq : 1.0 - tq;      // distance to the sigma end, in h
+    int anear = (int)lo;
+    if (!lo_sig) anear += ax == 0 ? 1 : n;
+    if (dnear < 1.0 - 1e-9) {
+      nearest = anear;
+    } else {
+      double bd = 1e300;
+      int bf = 0x7fffffff;
+      for (int p = ql; p < total; p += 8) {
+        const int i0 = wlo0 + p % we0, i1 = wlo1 + p / we0;
+        const int fl = i0 + n * i1;
+        if ((P.phase[fl] != 0) != sig_plus) continue;
+        const double r0 = (node_x(g, i0) - xc[0]) * ih, r1 = (node_x(g, i1) - xc[1]) * ih;
+        better(bd, bf, r0 * r0 + r1 * r1, fl);
+      }
+      for (int o = 4; o > 0; o >>= 1) {
+        const double od = __shfl_xor_sync(0xffffffffu, bd, o, 8);
+        const int of = __shfl_xor_sync(0xffffffffu, bf, o, 8);
+        better(bd, bf, od, of);
+      }
+      nearest = bf;
+    }
+  }
+  auto selected = [&](int p, int& fl, double& r0, double& r1) -> bool {
+    const int i0 = wlo0 + p % we0, i1 = wlo1 + p / we0;
+    fl = i0 + n * i1;
+    if ((P.phase[fl] != 0) != sig_plus || fl == nearest) return false;
+    r0 = (node_x(g, i0) - xc[0]) * ih;
+    r1 = (node_x(g, i1) - xc[1]) * ih;
+    const double d2 = r0 * r0 + r1 * r1, t = r0 * ns0 + r1 * ns1;
+    const double tau2 = fmax(d2 - t * t, 0.0);
+    return t >= 0.0 && tau2 / (at * at) + t * t / (an * an) <= 1.0;
+  };
+  // one pass over the window: selection bits per lane (chunks of at most 64 positions)
+  const int chunk = (total + 7) / 8;
+  const int p0 = ql * chunk, p1 = min(total, p0 + chunk);
+  unsigned long long bits = 0;
+  int my = 0;
+  for (int p = p0; p < p1 && p - p0 < 64; ++p) {
+    int fl;
+    double r0, r1;
+    if (selected(p, fl, r0, r1)) { bits |= 1ull << (p - p0); ++my; }
+  }
+  int incl = my;
+  for (int o = 1; o < 8; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o, 8);
+    if (ql >= o) incl += y;
+  }
+  const int R = __shfl_sync(0xffffffffu, incl, 7, 8);
+  if (active && (R > kQuadRows || R + 1 < M || chunk > 64)) {
+    if (ql == 0) overflow[f] = 1;
+    active = false;
+  }
+  if (active) {
+    int o = incl - my;
+    while (bits) {
+      const int b = __ffsll((long long)bits) - 1;
+      bits &= bits - 1;
+      const int p = p0 + b;
+      const int i0 = wlo0 + p % we0, i1 = wlo1 + p / we0;
+      nodes[o] = i0 + n * i1;
+      rel[2 * o] = (node_x(g, i0) - xc[0]) * ih;
+      rel[2 * o + 1] = (node_x(g, i1) - xc[1]) * ih;
+      ++o;
+    }
+  }
+  __syncwarp();
+  const int m = active ? R + 1 : 0;
+  for (int e = ql; e < m * M; e += 8) {
+    const int col = e / m, row = e - col * m;
+    V[(size_t)col * LDQ + row] = row == 0 ? (col == 0 ? 1.0 : 0.0) : monomial(P.monos + 3 * col, rel + 2 * (row - 1), 2);
+  }
+  __syncwarp();
+  // Householder QR, rows over the 8 lanes
+  for (int k = 0; k < M; ++k) {
+    double* vk = V + (size_t)k * LDQ;
+    double s = 0;
+    for (int r = k + ql; r < m; r += 8) s = fma(vk[r], vk[r], s);
+    q8_sum(s);
+    if (ql == 0 && m > 0) {
+      const double x0 = vk[k];
+      const double nr = sqrt(s);
+      const double a = x0 >= 0 ? -nr : nr;
+      const double vtv = 2.0 * (s - x0 * a);
+      vk[k] = x0 - a;
+      alpha[k] = a;
+      beta[k] = vtv > 0 ? 2.0 / vtv : 0.0;
+    }
+    __syncwarp();
+    const double bk = m > 0 ? beta[k] : 0.0;
+    for (int j = k + 1; j < M; ++j) {
+      double* vj = V + (size_t)j * LDQ;
+      double d = 0;
+      for (int r = k + ql; r < m; r += 8) d = fma(vk[r], vj[r], d);
+      q8_sum(d);
+      d *= bk;
+      for (int r = k + ql; r < m; r += 8) vj[r] = fma(-d, vk[r], vj[r]);
+    }
+    __syncwarp();
+  }
+  if (active) {
+    double mx = 0, mn = 1e300;
+    for (int k = 0; k < M; ++k) { mx = fmax(mx, fabs(alpha[k])); mn = fmin(mn, fabs(alpha[k])); }
+    if (!(mn >= 1e-8 * mx && mx > 0)) {
+      if (ql == 0) overflow[f] = 2;
+      active = false;
+    }
+  }
+  for (int k = ql; k < M; k += 8) ialpha[k] = active ? 1.0 / alpha[k] : 0.0;
+  __syncwarp();
+  // stencil rows, one target after the other (rows over the 8 lanes)
+  const int nt = (P.bc == IIM_BC_DIRICHLET) ? P.w : P.w + 1;
+  for (int t = 0; t < nt; ++t) {
+    double* y = Y + t * M;
+    double* srow = S + t * LDQ;
+    if (t < P.w) {
+      int mlo0 = (int)(lo % n), mlo1 = (int)(lo / n);
+      int gm0 = mlo0, gm1 = mlo1;
+      const int off = (lo_sig ? 1 : 0) + t * (lo_sig ? 1 : -1);
+      if (ax == 0) gm0 += off; else gm1 += off;
+      const double xi[2] = {(node_x(g, gm0) - xc[0]) * ih, (node_x(g, gm1) - xc[1]) * ih};
+      for (int col = ql; col < M; col += 8) y[col] = monomial(P.monos + 3 * col, xi, 2);
+    } else {
+      for (int col = ql; col < M; col += 8) {
+        const int* e = P.monos + 3 * col;
+        y[col] = (e[0] + e[1] == 1) ? (e[0] ? nrm[0] : nrm[1]) * ih : 0.0;
+      }
+    }
+    __syncwarp();
+    for (int i = 0; i < M; ++i) {                  // y = R^-T c
+      double part = 0;
+      for (int l = ql; l < i; l += 8) part = fma(V[(size_t)i * LDQ + l], y[l], part);
+      q8_sum(part);
+      if (ql == 0) y[i] = (y[i] - part) * ialpha[i];
+      __syncwarp();
+    }
+    for (int r = ql; r < m; r += 8) srow[r] = r < M ? y[r] : 0.0;
+    __syncwarp();
+    for (int k = M - 1; k >= 0; --k) {              // s = Q [y; 0]
+      const double* vk = V + (size_t)k * LDQ;
+      double d = 0;
+      for (int r = k + ql; r < m; r += 8) d = fma(vk[r], srow[r], d);
+      q8_sum(d);
+      d *= (m > 0 ? beta[k] : 0.0);
+      for (int r = k + ql; r < m; r += 8) srow[r] = fma(-d, vk[r], srow[r]);
+      __syncwarp();
+    }
+  }
+  if (!active) return;
+  const int rows = P.w + 1;
+  double* coef = P.fit_coef + (size_t)f * rows * P.rcap;
+  double* cdat = P.fit_cdat + (size_t)f * rows;
+  if (P.bc == IIM_BC_NEUMANN) {
+    double s2 = 0;
+    for (int r = ql; r < m; r += 8) { const double v = P.beta_p * S[P.w * LDQ + r]; s2 += v * v; }
+    // all lanes of this quarter are active here (the whole quarter shares `active`)
+    s2 += __shfl_xor_sync(__activemask(), s2, 4, 8);
+    s2 += __shfl_xor_sync(__activemask(), s2, 2, 8);
+    s2 += __shfl_xor_sync(__activemask(), s2, 1, 8);
+    const double Dc = P.beta_p * S[P.w * LDQ];
+    if (!(fabs(Dc) >= 1e-12 * sqrt(s2))) {
+      if (ql == 0) set_status(P.status, IIM_ERR_SINGULAR);
+      return;
+    }
+    for (int e = ql; e < P.w * R; e += 8) {
+      const int k = e / R, al = e - k * R;
+      coef[(size_t)k * P.rcap + al] = S[k * LDQ + 1 + al] - S[k * LDQ] * (P.beta_p * S[P.w * LDQ + 1 + al]) / Dc;
+    }
+    if (ql < P.w) cdat[ql] = S[ql * LDQ] / Dc;
+  } else {
+    for (int e = ql; e < nt * R; e += 8) {
+      const int k = e / R, al = e - k * R;
+      coef[(size_t)k * P.rcap + al] = S[k * LDQ + 1 + al];
+    }
+    if (ql < nt) cdat[ql] = S[ql * LDQ];
+  }
+  for (int e = ql; e < R; e += 8) P.fit_nodes[(size_t)f * P.rcap + e] = nodes[e];
+  if (ql == 0) P.fit_R[f] = R;
+}
+
 // ------------------------------------------------------------------------------ Shortley-Weller levels
 struct SWParams {
   GridView g;
@@ -625,6 +1137,7 @@ iim_status setup_fits(Problem& P) {
   F.cr_axis = P.cr_axis;
   F.cr_lo = P.cr_lo;
   F.cr_loplus = P.cr_loplus;
+  F.cr_t = P.cr_t;
   F.cr_x = P.cr_x;
   F.cr_n = P.cr_n;
   F.monos = P.d_monos;
@@ -634,15 +1147,45 @@ iim_status setup_fits(Problem& P) {
   F.fit_coef = P.fit_coef;
   F.fit_cdat = P.fit_cdat;
   F.status = P.d_status;
+  if (P.nfit_cap <= 0) return IIM_OK;
+  // warp per fit
+  WarpFitSmem W;
+  W.M = P.M;
+  W.RW = P.g.dim == 2 ? 64 : 128;
+  W.LDW = W.RW + 1;
+  const size_t per_warp = (W.bytes() / sizeof(double) + 1) * sizeof(double);
+  int wpb = (int)((200 * 1024) / per_warp);
+  wpb = wpb > 4 ? 4 : (wpb < 1 ? 1 : wpb);
+  const size_t smw = per_warp * wpb;
+  cudaError_t e = cudaFuncSetAttribute(k_fit_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw);
+  if (e != cudaSuccess) {
+    set_error(std::string("least-squares kernel shared memory: ") + cudaGetErrorString(e));
+    return IIM_ERR_CUDA;
+  }
+  cudaMemsetAsync(P.fit_overflow, 0, sizeof(int) * P.nfit_cap, P.stream);
+  if (P.g.dim == 2 && P.M <= 28) {
+    QuadFitSmem Q;
+    Q.M = P.M;
+    const size_t smq = sizeof(double) * Q.doubles() * 4;       // one warp, four fits
+    e = cudaFuncSetAttribute(k_fit_quad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
+    if (e != cudaSuccess) {
+      set_error(std::string("least-squares kernel shared memory: ") + cudaGetErrorString(e));
+      return IIM_ERR_CUDA;
+    }
+    IIM_LAUNCH(k_fit_quad, ceil_div(P.nfit_cap, 4), 32, smq, P.stream, F, Q, P.fit_overflow);
+  } else {
+    IIM_LAUNCH(k_fit_warp, ceil_div(P.nfit_cap, wpb), 32 * wpb, smw, P.stream, F, W, P.fit_overflow);
+  }
+  // CTA per fit for the flagged ones (more rows than a warp holds, or a grown region)
   size_t smem = fit_smem_bytes(P);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) {
       set_error(std::string("least-squares kernel shared memory: ") + cudaGetErrorString(e));
       return IIM_ERR_CUDA;
     }
   }
-  if (P.nfit_cap > 0) IIM_LAUNCH(k_fit, P.nfit_cap, kFitThreads, smem, P.stream, F);
+  IIM_LAUNCH(k_fit, P.nfit_cap, kFitThreads, smem, P.stream, F, P.fit_overflow);
   return IIM_OK;
 }
 

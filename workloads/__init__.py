@@ -405,10 +405,11 @@ def serving_trace(count: int = 2000, rate: float = 200.0, seed: int = 22455,
     return out
 
 
-def star_interface_variant(n: int, step: int, seed: int = 2503) -> ProblemSpec:
+def star_interface_variant(n: int, step: int, seed: int = 2503, angle: float = 0.0) -> ProblemSpec:
     """The 1024^2 star interface problem with a seeded variant of its manufactured solution.
 
-    Same geometry and coefficients as ``star_interface_1024``; u- = sin(pi x + a) cos(pi y + b),
+    Same geometry (rotated by ``angle``) and coefficients as ``star_interface_1024``;
+    u- = sin(pi x + a) cos(pi y + b),
     u+ = exp(x + y)/4 + c (a, b, c drawn per step), so every step solves a new system.
     """
     rng = np.random.default_rng([seed, step])
@@ -422,7 +423,7 @@ def star_interface_variant(n: int, step: int, seed: int = 2503) -> ProblemSpec:
     up = lambda X: np.exp(X[..., 0] + X[..., 1]) / 4 + c
     gp = lambda X: np.stack([np.exp(X[..., 0] + X[..., 1]) / 4] * 2, axis=-1)
     lp = lambda X: np.exp(X[..., 0] + X[..., 1]) / 2
-    spec = star_interface_1024(n)
+    spec = star_interface_1024(n, phase=angle)
     spec.solution = Manufactured(up, gp, lp, um, gm, lm)
     spec.name = f"star_interface_{n}_step{step}"
     return spec
