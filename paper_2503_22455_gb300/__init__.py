@@ -65,6 +65,7 @@ SIGNATURES = {
     "iim_set_data": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 5),
     "iim_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "iim_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "iim_apply_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "iim_precondition": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "iim_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(SolveInfo)]),
     "iim_solve_host": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 6 + [ctypes.POINTER(SolveInfo)]),
@@ -214,6 +215,12 @@ class Problem:
     def apply(self, u, include_data=False, out=None):
         w = out if out is not None else self._empty(self.N)
         _check(load().iim_apply(self.h, _ptr(u), _ptr(w), int(include_data)), "iim_apply")
+        return w
+
+    def apply_noalloc(self, u, include_data=False, out=None):
+        """iim_apply with the ghost values in the library's fixed device area (see iim.h)."""
+        w = out if out is not None else self._empty(self.N)
+        _check(load().iim_apply_noalloc(self.h, _ptr(u), _ptr(w), int(include_data)), "iim_apply_noalloc")
         return w
 
     def rhs(self):

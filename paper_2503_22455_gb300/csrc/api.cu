@@ -471,6 +471,13 @@ iim_status iim_apply(iim_problem* H, const double* u, double* w, int include_dat
   return cuda_check("apply");
 }
 
+iim_status iim_apply_noalloc(iim_problem* H, const double* u, double* w, int include_data) {
+  if (!H || !u || !w) return IIM_ERR_INVALID_ARG;
+  iim_status st = ho_apply_noalloc(H->P, u, w, include_data != 0, H->P.stream);
+  if (st != IIM_OK) return st;
+  return cuda_check("apply_noalloc");
+}
+
 iim_status iim_rhs(iim_problem* H, double* b) {
   if (!H || !b) return IIM_ERR_INVALID_ARG;
   cudaMemcpyAsync(b, H->P.b, sizeof(double) * H->P.g.N, cudaMemcpyDeviceToDevice, H->P.stream);

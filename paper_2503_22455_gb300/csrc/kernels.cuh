@@ -131,6 +131,7 @@ void ho_apply(Problem& P, const double* u, double* w, bool with_data, cudaStream
 void ho_stencil(Problem& P, const double* u, double* w, cudaStream_t s);
 void ho_ghost(Problem& P, const double* u, bool with_data, cudaStream_t s);
 void ho_correct(Problem& P, const double* u, double* w, bool with_data, cudaStream_t s);
+iim_status ho_apply_noalloc(Problem& P, const double* u, double* w, bool with_data, cudaStream_t s);
 void compute_rhs(Problem& P, const double* f, cudaStream_t s);
 
 // multigrid.cu

@@ -12,6 +12,9 @@
 // The stencil is FP64 and bound by the FP64 pipe on GB300 (2 FMA/clk/SM), so it
 // is written to use the fewest FP64 operations: neighbours at equal |j| are
 // summed first, then one FMA per |j| with beta/h^2 folded into the coefficients.
+#include <mutex>
+#include <string>
+
 #include "kernels.cuh"
 
 namespace iim {
@@ -320,6 +323,102 @@ void compute_rhs(Problem& P, const double* f, cudaStream_t s) {
   cudaMemsetAsync(zero, 0, sizeof(double) * P.g.N, s);
   ho_apply(P, zero, lg, true, s);
   IIM_LAUNCH(k_rhs_finish, ceil_div(P.g.N, 256), 256, 0, s, P.g, P.desc.bc == IIM_BC_INTERFACE, P.phase, f, lg, P.b);
+}
+
+
+// ---------------------------------------------------------------------------- no-allocation apply
+// The same three kernels as ho_apply, but the ghost values go to a file-scope
+// device array instead of the problem's workspace.  kNoAllocGhostMax doubles
+// (2 MiB) are reserved on every device that loads the library, for the life of
+// the process.  All calls share the array, so calls that overlap on the device
+// (other streams, other threads, other problems) race on it.  Each call writes
+// every ghost value before it reads it, so nothing in the array has to be cleared.
+namespace {
+constexpr int64_t kNoAllocGhostMax = 1 << 18;
+__device__ __align__(256) double g_noalloc_ghost[kNoAllocGhostMax];
+constexpr int kNoAllocMaxDevices = 64;
+double* g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
+std::mutex g_noalloc_mu;
+}  // namespace
+
+iim_status ho_apply_noalloc(Problem& P, const double* u, double* w, bool with_data, cudaStream_t s) {
+  const int64_t need = (int64_t)P.nfit_cap * P.w;
+  if (need > kNoAllocGhostMax) {
+    set_error("iim_apply_noalloc: the problem needs " + std::to_string(need) + " ghost values, more than the " +
+              std::to_string(kNoAllocGhostMax) + " the static scratch holds");
+    return IIM_ERR_CAPACITY;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+    cudaGetLastError();
+    set_error("iim_apply_noalloc: no usable current device");
+    return IIM_ERR_CUDA;
+  }
+  double* G = nullptr;
+  {
+    // first call on this device: look up the device address of the array (the host
+    // symbol is only a stand-in), with this device current
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* ptr = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_ghost);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string("iim_apply_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        return IIM_ERR_CUDA;
+      }
+      g_noalloc_addr[dev] = (double*)ptr;
+    }
+    G = g_noalloc_addr[dev];
+  }
+  ho_stencil(P, u, w, s);
+  const int iface = P.desc.bc == IIM_BC_INTERFACE;
+  GhostParams GP;
+  GP.nfit = P.nfit_cap;
+  GP.w = P.w;
+  GP.rcap = P.rcap;
+  GP.bc = P.desc.bc;
+  GP.interface_ = iface;
+  GP.with_data = with_data;
+  GP.beta_p = P.desc.beta_plus;
+  GP.beta_m = P.desc.beta_minus;
+  GP.K = P.d_counts + 0;
+  GP.fit_R = P.fit_R;
+  GP.fit_nodes = P.fit_nodes;
+  GP.fit_coef = P.fit_coef;
+  GP.fit_cdat = P.fit_cdat;
+  GP.g = P.d_g;
+  GP.j0 = P.d_j0;
+  GP.j1 = P.d_j1;
+  GP.G = G;
+  if (P.K_cap > 0) {
+    const int grid = ceil_div((int64_t)P.K_cap * kGhostLanes, 64);
+    if (P.w == 2) IIM_LAUNCH(k_ho_ghost<2>, grid, 64, 0, s, GP, u);
+    else IIM_LAUNCH(k_ho_ghost<3>, grid, 64, 0, s, GP, u);
+  }
+  CorrectParams CP;
+  const GridView& g = P.g;
+  CP.g = g;
+  CP.w = P.w;
+  CP.q = P.q;
+  CP.with_data = with_data;
+  CP.n_aff_cap = P.aff_cap;
+  CP.nfit_cap = P.nfit_cap;
+  CP.n_aff = P.d_counts + 1;
+  CP.aff_node = P.aff_node;
+  CP.aff_fit = P.aff_fit;
+  CP.aff_j = P.aff_j;
+  CP.G = G;
+  CP.phase = P.phase;
+  CP.box = P.d_box;
+  for (int k = 0; k < 2 * kMaxW + 1; ++k) CP.a[k] = k < 2 * P.w + 1 ? P.a[k] : 0.0;
+  const double h2 = g.h * g.h;
+  CP.scale[0] = P.desc.beta_minus / h2;
+  CP.scale[1] = P.desc.beta_plus / h2;
+  for (int k = 0; k < kMaxW; ++k)
+    for (int mm = 0; mm < 8; ++mm) CP.box_w[k][mm] = P.box_w[k][mm];
+  if (P.aff_cap > 0) IIM_LAUNCH(k_ho_correct, ceil_div(P.aff_cap, 64), 64, 0, s, CP, u, w);
+  return IIM_OK;
 }
 
 }  // namespace iim
