@@ -61,7 +61,7 @@ def box_ghost_weights(q: int, w: int) -> np.ndarray:
 
 
 class IIMOperator:
-    def __init__(self, spec, check_curvature=True):
+    def __init__(self, spec, check_curvature=True, lazy=False):
         self.spec = spec
         self.n = n = spec.n
         self.d = d = spec.dim
@@ -80,8 +80,10 @@ class IIMOperator:
         self.unknown = np.ones_like(self.plus) if spec.bc == INTERFACE else self.plus.copy()
         self.box_w = box_ghost_weights(q, w) if spec.box_bc == BOX_DIRICHLET else None
         self._check_box()
-        self._build_records()
-        self._build_fits()
+        self.fits = {}
+        if not lazy:
+            self._build_records()
+            self._build_fits()
 
     # ------------------------------------------------------------------ records
     def _check_box(self):
@@ -156,8 +158,14 @@ class IIMOperator:
             if self.bc == INTERFACE:
                 need.add((c, not side))
         self.fits = {}
-        cr = self.cross
         for (c, side) in sorted(need):
+            self._fit(c, side)
+
+    def _fit(self, c, side):
+        """The fit of crossing c on one side (built on first use)."""
+        key = (c, side)
+        if key not in self.fits:
+            cr = self.cross
             ax = int(cr.axis[c])
             lo = cr.lo_idx[c]
             hi = lo.copy()
@@ -167,8 +175,9 @@ class IIMOperator:
                 start, step = hi, 1
             else:
                 start, step = lo, -1
-            self.fits[(c, side)] = build_fit(cr.x[c], cr.normal[c], side, self.plus, self.n, self.h,
-                                             self.q, self.w, ax, start, step)
+            self.fits[key] = build_fit(cr.x[c], cr.normal[c], side, self.plus, self.n, self.h,
+                                       self.q, self.w, ax, start, step)
+        return self.fits[key]
 
     # ------------------------------------------------------------------ apply
     def control_values(self, u_flat, data, include_data):
@@ -261,6 +270,84 @@ class IIMOperator:
         out = beta * acc_flat / (self.h * self.h)
         out[~self.unknown.ravel(order="F")] = 0.0
         return out
+
+    def apply_at(self, u_flat, nodes, data=None, include_data=False):
+        """(L u)_i (+ data) at the given flat node indices only, with the same rules
+        as ``apply``; fits are built on first use, so this serves grids far too large
+        for the full oracle."""
+        n, d, w, a = self.n, self.d, self.w, self.a
+        data = data or {}
+        plus = self.plus
+        out = np.zeros(len(nodes))
+        for t, node in enumerate(nodes):
+            m = self._unflat(int(node))
+            side = bool(plus[tuple(m)])
+            if not self.unknown[tuple(m)]:
+                continue
+            acc = d * a[w] * u_flat[node]
+            for ax in range(d):
+                for s in (-1, 1):
+                    event = None
+                    for j in range(1, w + 1):
+                        p = m.copy()
+                        p[ax] += j * s
+                        inb = 0 <= p[ax] < n
+                        if event is None and (not inb or bool(plus[tuple(p)]) != side):
+                            event = (j, inb)
+                        if inb and bool(plus[tuple(p)]) == side:
+                            acc += a[w + j * s] * u_flat[self._flat(p)]
+                    if event is None:
+                        continue
+                    jstar, inb = event
+                    if inb:
+                        # crossing on the edge between offsets jstar-1 and jstar
+                        pa = m.copy()
+                        pa[ax] += (jstar - 1) * s
+                        pb = m.copy()
+                        pb[ax] += jstar * s
+                        lower = pa if s > 0 else pb
+                        c = self.cross.lookup[(ax, self._flat(lower))]
+                        G = self._ghosts_of(c, side, u_flat, data, include_data)
+                        for j in range(jstar, w + 1):
+                            p = m.copy()
+                            p[ax] += j * s
+                            if 0 <= p[ax] < n and bool(plus[tuple(p)]) == side:
+                                continue
+                            acc += a[w + j * s] * G[j - jstar]
+                    else:
+                        line = []
+                        for mm in range(2, self.q + 2):
+                            p = m.copy()
+                            p[ax] = n - mm if s > 0 else mm - 1
+                            line.append(self._flat(p))
+                        face = data["box"][self._box_index(m, ax, s)] if include_data else 0.0
+                        for j in range(jstar, w + 1):
+                            k = j - jstar + 1
+                            acc += a[w + j * s] * (self.box_w[k - 1, 0] * face + self.box_w[k - 1, 1:] @ u_flat[line])
+            beta = self.beta_p if side else self.beta_m
+            out[t] = beta * acc / (self.h * self.h)
+        return out
+
+    def _ghosts_of(self, c, side, u_flat, data, include_data):
+        """Ghost values of crossing c on one side (Eqs. 4-6, 9-11)."""
+        bp, bm = self.beta_p, self.beta_m
+        f = self._fit(c, side)
+        if self.bc == DIRICHLET:
+            uc = data["g"][c] if include_data else 0.0
+        elif self.bc == NEUMANN:
+            sv = bp * f.deriv
+            uc = ((data["g"][c] if include_data else 0.0) - sv[1:] @ u_flat[f.nodes]) / sv[0]
+        else:
+            fp, fm = self._fit(c, True), self._fit(c, False)
+            Sden = bp * fp.deriv[0] - bm * fm.deriv[0]
+            ubar = -(bp * (fp.deriv[1:] @ u_flat[fp.nodes]) - bm * (fm.deriv[1:] @ u_flat[fm.nodes])) / Sden
+            uc = ubar
+            if include_data:
+                if side:
+                    uc = ubar + (data["j1"][c] - bm * fm.deriv[0] * data["j0"][c]) / Sden
+                else:
+                    uc = ubar + (data["j1"][c] - bp * fp.deriv[0] * data["j0"][c]) / Sden
+        return f.ghost[:, 0] * uc + f.ghost[:, 1:] @ u_flat[f.nodes]
 
     def _box_index(self, m, ax, s):
         """Index into the box data array (faces -x0,+x0,-x1,+x1,...; others flat)."""

@@ -147,3 +147,23 @@ def test_spectrum_bounds(bc, order):
     assert np.max(lam.real) <= gold["re_upper"] + 1e-9
     lower = -2 * float(sigma_max(order)) * (1 + gold["neumann6_overshoot"] + 1e-3)
     assert np.min(lam.real) >= lower
+
+
+@pytest.mark.parametrize("case", ["iface2d_6", "neu3d_ellipsoid_4", "dir2d_circle_4"])
+def test_sampled_apply_equals_full_apply(case):
+    """The lazy per-node evaluation used for full-size parity equals the full operator."""
+    spec = CASES[case]()
+    rng = np.random.default_rng(4)
+    if spec.bc == W.INTERFACE:
+        spec.solution = W.two_phase_star_solution()
+    elif spec.solution is None:
+        spec.solution = W.sin_cos_2d(1.3, 0.2, 0.7, 0.4)
+    full = OracleProblem(spec)
+    f, data = full.data()
+    lazy = IIMOperator(spec, lazy=True)
+    u = rng.standard_normal(spec.n ** spec.dim)
+    nodes = np.concatenate([rng.choice(spec.n ** spec.dim, 200, replace=False),
+                            np.array(sorted({r[0] for r in full.op.iim_rec}))[:150]])
+    for incl in (False, True):
+        ref = full.op.apply(u, data, incl)[nodes]
+        assert np.max(np.abs(lazy.apply_at(u, nodes, data, incl) - ref)) < 1e-13 * np.max(np.abs(ref))
