@@ -51,6 +51,23 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(ms, world):
+    """The slowest rank's timed region (ms); a collective on the timing only."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, max_ms):
+    """Units per second over all ranks (weak scaling: every rank solves its own problems)."""
+    return world * units_per_rank / (max_ms / 1e3)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -219,12 +236,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     clk = clocks.stop()
-    total_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * B * K / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world)
+    value = whole_job_rate(B * K, world, total_ms)
 
     # accuracy of the last step of problem 0 against its manufactured solution
     spec = inputs[0][2][Wm + K - 1]
