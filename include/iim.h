@@ -32,7 +32,7 @@
  *   a message for the calling thread.  Device-side failures (rank-deficient
  *   fits, NaN in the Krylov recurrence, ...) are recorded in a status word on
  *   the device and reported by the next call that synchronises
- *   (iim_problem_create, iim_problem_setup_sync, iim_solve, iim_status_get).
+ *   (iim_problem_create, iim_solve, iim_status_get, iim_engine_release).
  */
 #ifndef IIM_H
 #define IIM_H
@@ -120,7 +120,10 @@ iim_status iim_problem_create(const iim_problem_desc* desc, const iim_options* o
 /* Re-run the set-up in place (same dim, n, bc, order, box), optionally with new
  * geometry parameters (params may be NULL).  Asynchronous: no allocation and no
  * host synchronisation; the workspace must be large enough (device-checked,
- * IIM_ERR_CAPACITY is reported by the next synchronising call). */
+ * IIM_ERR_CAPACITY is reported by the next synchronising call).  With
+ * opt.use_graph the set-up kernels are captured into a CUDA graph the first
+ * time and replayed by later calls with the same geometry (new parameters
+ * capture it again). */
 iim_status iim_problem_setup(iim_problem* p, const double* geom_params);
 
 /* Synchronise the problem's stream and return the device status word. */
@@ -131,6 +134,9 @@ void iim_problem_destroy(iim_problem* p);
 /* Sizes: number of control points K, box data points B (2 d n^(d-1) or 0),
  * grid nodes N = n^d, unknowns. */
 iim_status iim_problem_sizes(iim_problem* p, int* K, int* B, int64_t* N, int64_t* n_unknowns);
+
+/* Device bytes the problem holds (its whole workspace). */
+iim_status iim_problem_bytes(iim_problem* p, size_t* bytes);
 
 /* Control points in canonical order (axis, then flat index of the lower node
  * of the cut grid edge): xc_dev [K][dim], normal_dev [K][dim] (out of Omega+).
@@ -188,6 +194,126 @@ iim_status iim_solve_host(iim_problem* p, const double* f_host, const double* g_
  * enqueues every solve graph on a pool of streams so that their kernels overlap
  * on the device, then waits.  infos may be NULL. */
 iim_status iim_batch_solve(iim_problem** probs, double** x_devs, int count, iim_solve_info* infos);
+
+/* ------------------------------------------------------------------------
+ * Batched engine: many independent problems solved together.
+ *
+ * Each admitted problem ("slot") keeps its grids, multigrid hierarchy, Krylov
+ * basis and FGMRES scalars on the device.  iim_engine_run launches one CUDA
+ * graph that repeats a "tick" until every slot has finished or max_ticks ticks
+ * have run; a tick advances every slot by one step of its own solve (an FGMRES
+ * iteration of Sec. 4.1 with one V-cycle of Sec. 3.3, or a restart with the
+ * true-residual test) through persistent kernels that walk device-side lists
+ * of (slot, thread block) work items.  The work of a slot is split into the
+ * same thread blocks as in iim_solve, so a slot's iterates, iteration count
+ * and solution are bit for bit those of iim_solve on the same problem,
+ * whatever else is in the engine.  Slots may be admitted and released between
+ * runs; the lists are rewritten then, and the graph is captured again only
+ * when a new kind of work appears.  The paper solves one problem at a time;
+ * this batching is an addition of this library.
+ *
+ * All calls are on the engine's stream (stream argument of create; NULL = the
+ * legacy default stream).  The engine only borrows problems: a problem must
+ * stay alive until it is released, and must not be used by other calls while
+ * admitted.
+ * ---------------------------------------------------------------------- */
+typedef struct iim_engine iim_engine;
+
+/* Create an engine for up to max_slots problems solved with opt (tol, restart,
+ * max_iter and reorth are taken per problem from the problem's own options;
+ * nu1, nu2 and the FP32 multigrid are engine-wide: nu1, nu2 >= 2). */
+iim_status iim_engine_create(const iim_options* opt, int max_slots, void* stream, iim_engine** out);
+void iim_engine_destroy(iim_engine* e);
+
+/* Admit a set-up problem whose data have been set (iim_set_data): its solve
+ * starts at the next run from x0_dev (NULL: zero).  Work already enqueued on
+ * the problem's stream comes first.  *slot receives the slot index.
+ * IIM_ERR_CAPACITY when every slot is taken; IIM_ERR_INVALID_ARG when the
+ * problem's multigrid options differ from the engine's. */
+iim_status iim_engine_admit(iim_engine* e, iim_problem* p, const double* x0_dev, int* slot);
+
+/* Enqueue one graph launch running up to max_ticks ticks (it stops earlier when
+ * every slot has finished).  Asynchronous. */
+iim_status iim_engine_run(iim_engine* e, int max_ticks);
+
+/* Outcome of the last run: *live = slots still running, done[0 .. *ndone) =
+ * slots that finished since the previous poll (done: int[max_slots]), and the
+ * ticks run so far.  wait = 0 returns IIM_ERR_TIMEOUT at once while the run is
+ * still on the device; wait = 1 blocks until it is done.  Any pointer may be NULL. */
+iim_status iim_engine_poll(iim_engine* e, int wait, int* live, int* done, int* ndone, int64_t* ticks);
+
+/* Remove a slot: copy its solution to x_dev (NULL: skip) and fill info (the
+ * kernels field is 0: the engine's launches are shared, see iim_engine_stats).
+ * Releasing a running slot cancels its solve (status IIM_ERR_TIMEOUT).
+ * Synchronises the engine's stream. */
+iim_status iim_engine_release(iim_engine* e, int slot, double* x_dev, iim_solve_info* info);
+
+/* Kernel launches per tick of the captured graph, and ticks run so far. */
+iim_status iim_engine_stats(iim_engine* e, int64_t* kernels_per_tick, int64_t* ticks);
+
+/* Tile shapes of the fused 2D multigrid kernels per level size class (n <= 32,
+ * 64, 128, 256, 512, larger; int[6]): 0 = 32x8, 1 = 64x8, 2 = 32x16, 3 = 64x16.
+ * The shape changes the speed, not the result.  NULL restores the defaults. */
+iim_status iim_engine_set_shapes(iim_engine* e, const int* shape_of_class);
+iim_status iim_engine_get_shapes(iim_engine* e, int* shape_of_class);
+
+/* Autotuner: for every size class in use, time the grouped V-cycle of all
+ * admitted slots (reps repetitions) with each tile shape and keep the fastest;
+ * *best_ms = the tuned V-cycle time.  It uses each slot's first Krylov vectors
+ * as scratch, so it is only allowed before the first run after admission
+ * (IIM_ERR_INVALID_ARG once a slot has started).  Synchronises. */
+iim_status iim_engine_autotune(iim_engine* e, int reps, double* best_ms);
+
+/* ------------------------------------------------------------------------
+ * Request loop ("server") over an engine.
+ *
+ * Requests are queued by iim_server_submit and admitted, in submission order,
+ * while the device memory they will hold fits hbm_budget bytes.  An admitted
+ * request's problem is created and set up on its own stream, beside the
+ * engine's work; the caller then sets its data and marks it ready.  Ready
+ * requests join the engine between runs of ticks_per_run ticks, and leave it
+ * when their solve ends: their solution is copied to the host and their device
+ * memory returned to the budget, so that queued requests can enter while
+ * others are still running.  Nothing here blocks on the device except the
+ * copy of a finished solution and iim_server_data_ready.  Latency of a
+ * request: from iim_server_submit to its solution being on the host.
+ * ---------------------------------------------------------------------- */
+typedef struct iim_server iim_server;
+
+/* opt as for iim_engine_create; max_slots problems on the device at once. */
+iim_status iim_server_create(const iim_options* opt, size_t hbm_budget, int max_slots, int ticks_per_run,
+                             iim_server** out);
+/* Frees every request still held (running solves are cancelled). */
+void iim_server_destroy(iim_server* s);
+
+/* Queue a request; *id identifies it.  IIM_ERR_BUDGET if it alone exceeds the budget. */
+iim_status iim_server_submit(iim_server* s, const iim_problem_desc* desc, int64_t* id);
+
+/* One turn of the loop: (1) when the last run has finished, release the slots
+ * that finished; (2) put ready requests into free slots and launch the next run;
+ * (3) copy the finished solutions to the host; (4) create queued requests that
+ * fit the budget.  need_data[0 .. *n_need) = ids created in this turn, waiting
+ * for data; finished[0 .. *n_fin) = ids finished (or failed) in this turn.
+ * Arrays may be NULL with capacity 0 (ids beyond a capacity are not reported). */
+iim_status iim_server_step(iim_server* s, int64_t* need_data, int cap_need, int* n_need, int64_t* finished,
+                           int cap_fin, int* n_fin);
+
+/* The problem of a request waiting for data (NULL otherwise): set its data with
+ * iim_set_data (after iim_control_points / iim_phase as needed). */
+iim_problem* iim_server_problem(iim_server* s, int64_t id);
+
+/* The request's data are set: it joins the engine at the next run.  Waits for
+ * the request's stream, so the caller's data buffers are free when it returns. */
+iim_status iim_server_data_ready(iim_server* s, int64_t id);
+
+/* Result of a finished request (x_host: n^d doubles, may be NULL), then forget
+ * it.  Returns the request's final status; IIM_ERR_TIMEOUT while it is not finished. */
+iim_status iim_server_take(iim_server* s, int64_t id, double* x_host, iim_solve_info* info, double* latency_s);
+
+/* Device bytes held by requests now and at most so far, queued requests,
+ * requests in the engine, engine runs launched. */
+iim_status iim_server_stats(iim_server* s, size_t* bytes_in_use, size_t* peak_bytes, int* queued, int* resident,
+                            int64_t* runs);
 
 /* Profiling: average device time (microseconds) of one launch of an internal
  * kernel, timed with CUDA events on the problem's stream over ``reps`` back to

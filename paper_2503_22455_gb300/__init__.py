@@ -14,6 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libiim.so")
 
 IIM_OK = 0
+IIM_ERR_TIMEOUT = 8
 STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "curvature", 3: "rank", 4: "singular", 5: "not converged",
                 6: "breakdown", 7: "budget", 8: "timeout", 9: "cuda", 10: "geometry", 11: "capacity"}
 GEOM = {"circle": 0, "ellipse": 1, "star": 2, "sphere": 3, "ellipsoid": 4}
@@ -61,6 +62,7 @@ SIGNATURES = {
     "iim_problem_sizes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "iim_control_points": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "iim_problem_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     "iim_phase": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "iim_set_data": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 5),
     "iim_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
@@ -73,6 +75,33 @@ SIGNATURES = {
                                        ctypes.POINTER(SolveInfo)]),
     "iim_kernel_time": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "iim_launch_count": (ctypes.c_int64, []),
+    "iim_engine_create": (ctypes.c_int, [ctypes.POINTER(Options), ctypes.c_int, ctypes.c_void_p,
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    "iim_engine_destroy": (None, [ctypes.c_void_p]),
+    "iim_engine_admit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "iim_engine_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "iim_engine_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int64)]),
+    "iim_engine_release": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(SolveInfo)]),
+    "iim_engine_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "iim_engine_set_shapes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "iim_engine_get_shapes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "iim_engine_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "iim_server_create": (ctypes.c_int, [ctypes.POINTER(Options), ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    "iim_server_destroy": (None, [ctypes.c_void_p]),
+    "iim_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Desc), ctypes.POINTER(ctypes.c_int64)]),
+    "iim_server_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int)]),
+    "iim_server_problem": (ctypes.c_void_p, [ctypes.c_void_p, ctypes.c_int64]),
+    "iim_server_data_ready": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "iim_server_take": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(SolveInfo),
+                                       ctypes.POINTER(ctypes.c_double)]),
+    "iim_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t),
+                                        ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)]),
     "iim_last_error": (ctypes.c_char_p, []),
     "iim_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -167,10 +196,24 @@ class Problem:
         self.K, self.B, self.N, self.n_unknowns = K.value, B.value, N.value, U.value
         self.dim, self.n = desc.dim, desc.n
 
+    @classmethod
+    def view(cls, handle, desc: Desc):
+        """A non-owning view of a problem the library holds (e.g. a server request)."""
+        self = cls.__new__(cls)
+        lib = load()
+        self.desc, self.options, self.stream, self._owned = desc, None, None, False
+        self.h = ctypes.c_void_p(handle)
+        K, B = ctypes.c_int(), ctypes.c_int()
+        N, U = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib.iim_problem_sizes(self.h, ctypes.byref(K), ctypes.byref(B), ctypes.byref(N), ctypes.byref(U)))
+        self.K, self.B, self.N, self.n_unknowns = K.value, B.value, N.value, U.value
+        self.dim, self.n = desc.dim, desc.n
+        return self
+
     def close(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and getattr(self, "_owned", True):
             load().iim_problem_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -197,19 +240,41 @@ class Problem:
     def status(self):
         return load().iim_status_get(self.h)
 
+    def device_bytes(self) -> int:
+        b = ctypes.c_size_t()
+        _check(load().iim_problem_bytes(self.h, ctypes.byref(b)))
+        return b.value
+
+    def _foreign_stream_sync(self, before):
+        """A view's problem runs on a library stream that torch's stream does not order:
+        wait for torch's work before the library reads our tensors, and for the
+        library's copies before torch reads them."""
+        if getattr(self, "_owned", True):
+            return
+        import torch
+        if before:
+            torch.cuda.current_stream().synchronize()
+        else:
+            _check(self.status(), "problem status")
+
     def control_points(self):
         xc = self._empty(max(self.K, 1), self.dim)
         nc = self._empty(max(self.K, 1), self.dim)
+        self._foreign_stream_sync(True)
         _check(load().iim_control_points(self.h, _ptr(xc), _ptr(nc)))
+        self._foreign_stream_sync(False)
         return xc[:self.K], nc[:self.K]
 
     def phase(self):
         import torch
         ph = torch.empty(self.N, dtype=torch.uint8, device="cuda")
+        self._foreign_stream_sync(True)
         _check(load().iim_phase(self.h, ctypes.c_void_p(ph.data_ptr())))
+        self._foreign_stream_sync(False)
         return ph
 
     def set_data(self, f, g=None, j0=None, j1=None, box=None):
+        self._foreign_stream_sync(True)
         _check(load().iim_set_data(self.h, _ptr(f), _ptr(g), _ptr(j0), _ptr(j1), _ptr(box)), "iim_set_data")
 
     def apply(self, u, include_data=False, out=None):
@@ -280,3 +345,182 @@ def kernel_time(problem, which, reps=50) -> float:
 
 def launch_count() -> int:
     return int(load().iim_launch_count())
+
+
+class Engine:
+    """Batched engine (see iim.h): admit set-up problems, run ticks, poll, release."""
+
+    def __init__(self, options: Options | None = None, max_slots: int = 64, stream=None):
+        import torch
+        lib = load()
+        self.options = options or default_options()
+        self.stream = stream or torch.cuda.current_stream()
+        self.max_slots = int(max_slots)
+        h = ctypes.c_void_p()
+        _check(lib.iim_engine_create(ctypes.byref(self.options), self.max_slots,
+                                     ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)), "iim_engine_create")
+        self.h = h
+        self._done = (ctypes.c_int * self.max_slots)()
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().iim_engine_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def admit(self, problem: Problem, x0=None) -> int:
+        slot = ctypes.c_int()
+        _check(load().iim_engine_admit(self.h, problem.h, _ptr(x0), ctypes.byref(slot)), "iim_engine_admit")
+        return slot.value
+
+    def run(self, max_ticks: int = 1 << 30):
+        _check(load().iim_engine_run(self.h, int(max_ticks)), "iim_engine_run")
+
+    def poll(self, wait=True):
+        """(finished, live, ticks): finished is None while the last run is still on the device."""
+        live, nd, ticks = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+        st = load().iim_engine_poll(self.h, int(bool(wait)), ctypes.byref(live), self._done, ctypes.byref(nd),
+                                    ctypes.byref(ticks))
+        if st == IIM_ERR_TIMEOUT and not wait:
+            return None, None, None
+        _check(st, "iim_engine_poll")
+        return [self._done[i] for i in range(nd.value)], live.value, ticks.value
+
+    def release(self, slot: int, x=None, check=True):
+        info = SolveInfo()
+        _check(load().iim_engine_release(self.h, int(slot), _ptr(x), ctypes.byref(info)), "iim_engine_release")
+        if check and info.status != IIM_OK:
+            raise IIMError(info.status, f"slot {slot}: " + load().iim_status_string(info.status).decode())
+        return info
+
+    def stats(self):
+        k, t = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().iim_engine_stats(self.h, ctypes.byref(k), ctypes.byref(t)))
+        return k.value, t.value
+
+    def set_shapes(self, shapes=None):
+        arr = None if shapes is None else (ctypes.c_int * 6)(*shapes)
+        _check(load().iim_engine_set_shapes(self.h, arr), "iim_engine_set_shapes")
+
+    def shapes(self):
+        arr = (ctypes.c_int * 6)()
+        _check(load().iim_engine_get_shapes(self.h, arr))
+        return list(arr)
+
+    def autotune(self, reps=3) -> float:
+        ms = ctypes.c_double()
+        _check(load().iim_engine_autotune(self.h, int(reps), ctypes.byref(ms)), "iim_engine_autotune")
+        return ms.value
+
+    def solve_all(self, max_ticks: int = 1 << 30):
+        """Run until every admitted slot has finished; returns the tick count of the run."""
+        t0 = self.stats()[1]
+        self.run(max_ticks)
+        self.poll(wait=True)
+        return self.stats()[1] - t0
+
+
+class Server:
+    """Request loop over an engine (see iim.h): submit, step, set data, take."""
+
+    def __init__(self, options: Options | None = None, budget_bytes: int = 1 << 34, max_slots: int = 64,
+                 ticks_per_run: int = 4, cap: int = 4096):
+        lib = load()
+        self.options = options or default_options()
+        h = ctypes.c_void_p()
+        _check(lib.iim_server_create(ctypes.byref(self.options), ctypes.c_size_t(int(budget_bytes)), int(max_slots),
+                                     int(ticks_per_run), ctypes.byref(h)), "iim_server_create")
+        self.h = h
+        self.cap = cap
+        self._need = (ctypes.c_int64 * cap)()
+        self._fin = (ctypes.c_int64 * cap)()
+        self.descs = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().iim_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, desc: Desc) -> int:
+        rid = ctypes.c_int64()
+        _check(load().iim_server_submit(self.h, ctypes.byref(desc), ctypes.byref(rid)), "iim_server_submit")
+        self.descs[rid.value] = desc
+        return rid.value
+
+    def step(self):
+        nn, nf = ctypes.c_int(), ctypes.c_int()
+        _check(load().iim_server_step(self.h, self._need, self.cap, ctypes.byref(nn), self._fin, self.cap,
+                                      ctypes.byref(nf)), "iim_server_step")
+        return [self._need[i] for i in range(nn.value)], [self._fin[i] for i in range(nf.value)]
+
+    def problem(self, rid: int) -> Problem:
+        h = load().iim_server_problem(self.h, ctypes.c_int64(rid))
+        if not h:
+            raise IIMError(1, f"request {rid} is not waiting for data")
+        return Problem.view(h, self.descs[rid])
+
+    def data_ready(self, rid: int):
+        _check(load().iim_server_data_ready(self.h, ctypes.c_int64(rid)), "iim_server_data_ready")
+
+    def take(self, rid: int):
+        """(x on the host, SolveInfo, latency seconds, status) of a finished request."""
+        import numpy as np
+        d = self.descs.pop(rid)
+        x = np.zeros(d.n ** d.dim)
+        info, lat = SolveInfo(), ctypes.c_double()
+        st = load().iim_server_take(self.h, ctypes.c_int64(rid), ctypes.c_void_p(x.ctypes.data), ctypes.byref(info),
+                                    ctypes.byref(lat))
+        return x, info, lat.value, st
+
+    def stats(self):
+        b, pk, q, r, runs = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+        _check(load().iim_server_stats(self.h, ctypes.byref(b), ctypes.byref(pk), ctypes.byref(q), ctypes.byref(r),
+                                       ctypes.byref(runs)))
+        return {"bytes_in_use": b.value, "peak_bytes": pk.value, "queued": q.value, "resident": r.value,
+                "runs": runs.value}
+
+
+def serve(server: Server, arrivals, set_data, realtime=True, idle_sleep=0.0):
+    """Drive a server through a stream of requests.
+
+    arrivals: list of (arrival time in seconds from now, Desc, user object), sorted by time;
+    set_data(problem_view, user) sets the data of a created request.  Returns
+    {request id: (x, info, latency, status, user)} and the wall time.  With realtime=False
+    every request is submitted at once.
+    """
+    import time
+    t0 = time.perf_counter()
+    pending = list(arrivals)
+    k = 0
+    users, out = {}, {}
+    outstanding = 0
+    while k < len(pending) or outstanding:
+        now = time.perf_counter() - t0
+        while k < len(pending) and (not realtime or pending[k][0] <= now):
+            _, desc, user = pending[k]
+            rid = server.submit(desc)
+            users[rid] = user
+            outstanding += 1
+            k += 1
+        need, fin = server.step()
+        for rid in need:
+            set_data(server.problem(rid), users[rid])
+            server.data_ready(rid)
+        for rid in fin:
+            x, info, lat, st = server.take(rid)
+            out[rid] = (x, info, lat, st, users.pop(rid))
+            outstanding -= 1
+        if idle_sleep and not need and not fin:
+            time.sleep(idle_sleep)
+    return out, time.perf_counter() - t0

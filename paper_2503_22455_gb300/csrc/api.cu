@@ -11,16 +11,41 @@ namespace iim {
 
 static std::atomic<int64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 static thread_local std::string g_err;
 void set_error(const std::string& msg) { g_err = msg; }
 
+// Workspace comes from the device's stream-ordered memory pool, allocated and freed
+// on the problem's stream: freeing a problem does not synchronise the device, so a
+// request that finishes does not stall the solves still running.  The pool keeps
+// freed memory for reuse (release threshold raised once per device).
+static void keep_pool_memory() {
+  static std::mutex mu;
+  static bool done[64] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
+  done[dev] = true;
+}
+
 void* dev_alloc(Problem& P, size_t bytes) {
   if (bytes == 0) bytes = 16;
+  keep_pool_memory();
   void* p = nullptr;
-  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+  if (cudaMallocAsync(&p, bytes, P.stream) != cudaSuccess) {
     cudaGetLastError();
-    set_error("cudaMalloc failed for " + std::to_string(bytes) + " bytes");
+    set_error("device allocation failed for " + std::to_string(bytes) + " bytes");
     return nullptr;
   }
   P.allocs.push_back(p);
@@ -28,15 +53,23 @@ void* dev_alloc(Problem& P, size_t bytes) {
   return p;
 }
 
+// the problem's stream has finished every use of the workspace when this runs
 static void free_all(Problem& P) {
-  for (void* p : P.allocs) cudaFree(p);
+  for (void* p : P.allocs) cudaFreeAsync(p, P.stream);
   P.allocs.clear();
+  P.bytes = 0;
   if (P.graph_exec) cudaGraphExecDestroy(P.graph_exec);
   if (P.graph) cudaGraphDestroy(P.graph);
+  if (P.setup_exec) cudaGraphExecDestroy(P.setup_exec);
+  if (P.setup_graph) cudaGraphDestroy(P.setup_graph);
+  P.setup_exec = nullptr;
+  P.setup_graph = nullptr;
   if (P.ev0) cudaEventDestroy(P.ev0);
   if (P.ev1) cudaEventDestroy(P.ev1);
   P.graph_exec = nullptr;
   P.graph = nullptr;
+  P.ev0 = nullptr;
+  P.ev1 = nullptr;
 }
 
 static int binom(int a, int b) {
@@ -79,7 +112,7 @@ static void box_weights(int q, int w, double out[kMaxW][8]) {
 
 // max rows of a least-squares set: lattice points of the half-ellipse (half
 // ellipsoid) at the largest growth, with a one-cell margin on every semi-axis
-static int rows_cap(int dim, int q) {
+int rows_cap(int dim, int q) {
   double an = q + 1.0 + 1.5 + 1.0, at = q / 2 + 1.0 + 1.5 + 1.0;
   double v = dim == 2 ? M_PI * an * at / 2.0 : 2.0 / 3.0 * M_PI * an * at * at;
   int cap = (int)std::ceil(v) + 8;
@@ -241,7 +274,8 @@ iim_status iim_problem_create(const iim_problem_desc* desc, const iim_options* o
     if (!ptr) IIM_FAIL(IIM_ERR_BUDGET);                                    \
   } while (0)
   IIM_ALLOC(P.d_monos, int, mono.size());
-  cudaMemcpy(P.d_monos, mono.data(), sizeof(int) * mono.size(), cudaMemcpyHostToDevice);
+  cudaMemcpyAsync(P.d_monos, mono.data(), sizeof(int) * mono.size(), cudaMemcpyHostToDevice, P.stream);
+  cudaStreamSynchronize(P.stream);
   IIM_ALLOC(P.d_status, int, 4);
   IIM_ALLOC(P.d_counts, int, kCountSlots);
   cudaMemsetAsync(P.d_status, 0, sizeof(int) * 4, P.stream);
@@ -379,16 +413,64 @@ iim_status iim_problem_create(const iim_problem_desc* desc, const iim_options* o
 #undef IIM_ALLOC
 }
 
-iim_status iim_problem_setup(iim_problem* H, const double* params) {
-  if (!H) return IIM_ERR_INVALID_ARG;
-  Problem& P = H->P;
-  if (params)
-    for (int k = 0; k < 8; ++k) P.desc.geom_params[k] = params[k];
+static iim_status setup_enqueue(Problem& P) {
   setup_geometry(P, false);
   iim_status st = setup_fits(P);
   if (st != IIM_OK) return st;
   setup_levels(P, false);
   mg_coarse_factor(P, P.stream);
+  return IIM_OK;
+}
+
+// The set-up is a fixed sequence of kernels with no host decision in it, so (with
+// use_graph) it is captured once per geometry and replayed as one graph launch.
+iim_status iim_problem_setup(iim_problem* H, const double* params) {
+  if (!H) return IIM_ERR_INVALID_ARG;
+  Problem& P = H->P;
+  if (params) {
+    bool changed = false;
+    for (int k = 0; k < 8; ++k) {
+      changed = changed || P.desc.geom_params[k] != params[k];
+      P.desc.geom_params[k] = params[k];
+    }
+    if (changed && P.setup_exec) {
+      cudaGraphExecDestroy(P.setup_exec);
+      cudaGraphDestroy(P.setup_graph);
+      P.setup_exec = nullptr;
+      P.setup_graph = nullptr;
+    }
+  }
+  if (!P.opt.use_graph) {
+    iim_status st = setup_enqueue(P);
+    if (st != IIM_OK) return st;
+    return cuda_check("setup");
+  }
+  if (!P.setup_exec) {
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return cuda_check("setup stream");
+    cudaStream_t own = P.stream;
+    P.stream = cs;
+    cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    const int64_t c0 = iim_launch_count();
+    iim_status st = setup_enqueue(P);
+    P.kern_setup = iim_launch_count() - c0;
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(cs, &g);
+    P.stream = own;
+    cudaStreamDestroy(cs);
+    if (st != IIM_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (cuda_check("setup capture") != IIM_OK || cudaGraphInstantiate(&P.setup_exec, g, 0) != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      P.setup_exec = nullptr;
+      return cuda_check("setup graph");
+    }
+    P.setup_graph = g;
+  }
+  cudaGraphLaunch(P.setup_exec, P.stream);
+  note_launches(P.kern_setup);
   return cuda_check("setup");
 }
 
@@ -427,6 +509,12 @@ iim_status iim_problem_sizes(iim_problem* H, int* K, int* B, int64_t* N, int64_t
     }
   }
   return cuda_check("sizes");
+}
+
+iim_status iim_problem_bytes(iim_problem* H, size_t* bytes) {
+  if (!H || !bytes) return IIM_ERR_INVALID_ARG;
+  *bytes = H->P.bytes;
+  return IIM_OK;
 }
 
 iim_status iim_control_points(iim_problem* H, double* xc, double* nrm) {

@@ -207,6 +207,7 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 // launch accounting (every kernel launch of the library goes through IIM_LAUNCH)
 void note_launch();
+void note_launches(int64_t k);         // a graph launch that runs k kernels
 #define IIM_LAUNCH(kernel, grid, block, smem, stream, ...)                \
   do {                                                                    \
     kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);           \

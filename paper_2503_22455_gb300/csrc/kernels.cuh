@@ -32,7 +32,58 @@ struct Level {
   void* f = nullptr;
 };
 
-struct SolverScalars;             // device-side FGMRES state (krylov.cu)
+// device-side FGMRES state of one solve (krylov.cu)
+struct SolverScalars {
+  double H[(kMaxRestart + 1) * kMaxRestart];   // H[i + (kMaxRestart+1) * j]
+  double g[kMaxRestart + 1];
+  double cs[kMaxRestart], sn[kMaxRestart];
+  double y[kMaxRestart];
+  double inv_norm[kMaxRestart + 1];            // 1/|v_i| for the unnormalised basis
+  double hcol[kMaxRestart + 2];
+  double w2_old, w2;
+  double bnorm, relres, est;
+  int iters, restarts, k, active, done, converged, reorth_needed, breakdown;
+  int m, max_iter, graph_mode, reorth;
+  int first;                                   // batched engine: the next residual is the first
+  double tol;
+  cudaGraphConditionalHandle h_while;
+  cudaGraphConditionalHandle h_if[kMaxRestart];
+};
+
+// parameters of the three operator kernels (operator.cu)
+struct StencilCoef {
+  double c0[2];            // d * a_0 * beta_sigma / h^2 for sigma = minus, plus
+  double cj[2][kMaxW];     // a_j * beta_sigma / h^2
+};
+
+struct GhostParams {
+  int nfit, w, rcap, bc, interface_, with_data;
+  double beta_p, beta_m;
+  const int* K;
+  const int32_t* fit_R;
+  const int32_t* fit_nodes;
+  const double* fit_coef;
+  const double* fit_cdat;
+  const double* g;          // ubar / qbar per control point
+  const double* j0;
+  const double* j1;
+  double* G;                // [nfit][w]
+};
+
+struct CorrectParams {
+  GridView g;
+  int w, q, with_data, n_aff_cap, nfit_cap;
+  const int* n_aff;
+  const int32_t* aff_node;
+  const int32_t* aff_fit;
+  const int32_t* aff_j;
+  const double* G;
+  const uint8_t* phase;
+  const double* box;        // [B] face data
+  double a[2 * kMaxW + 1];
+  double scale[2];          // beta_sigma / h^2
+  double box_w[kMaxW][8];
+};
 
 // slots of Problem::d_counts: control points, affected nodes, irregular rows of
 // level l at kCountLevel0 + l (at most kMaxLevels levels), unknowns of the coarsest level
@@ -112,6 +163,10 @@ struct Problem {
   cudaGraphExec_t graph_exec = nullptr;
   int64_t kern_start = 0, kern_restart = 0, kern_iter[kMaxRestart] = {0};
   cudaGraph_t graph = nullptr;
+  // CUDA graph of the set-up (geometry, fits, levels, coarse factor) for the current geometry
+  cudaGraph_t setup_graph = nullptr;
+  cudaGraphExec_t setup_exec = nullptr;
+  int64_t kern_setup = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   size_t bytes = 0;               // device bytes held
   std::vector<void*> allocs;
@@ -148,6 +203,7 @@ void krylov_orth_pass(Problem& P, int j, int which, cudaStream_t s);
 
 // api.cu
 void* dev_alloc(Problem& P, size_t bytes);
+int rows_cap(int dim, int q);                  // least-squares rows reserved per fit
 void set_error(const std::string& msg);
 
 }  // namespace iim

@@ -14,53 +14,45 @@
 // the true residual |b - A x| / |b| at every restart (x += Z y).
 // The whole solve is one CUDA graph: WHILE(not done) { IF(active) iteration 0;
 // ...; IF(active) iteration m-1; restart }, with the conditions set by kernels.
-#include "kernels.cuh"
+#include <algorithm>
+
+#include "engine.cuh"
 
 namespace iim {
 
-struct SolverScalars {
-  double H[(kMaxRestart + 1) * kMaxRestart];   // H[i + (kMaxRestart+1) * j]
-  double g[kMaxRestart + 1];
-  double cs[kMaxRestart], sn[kMaxRestart];
-  double y[kMaxRestart];
-  double inv_norm[kMaxRestart + 1];            // 1/|v_i| for the unnormalised basis
-  double hcol[kMaxRestart + 2];
-  double w2_old, w2;
-  double bnorm, relres, est;
-  int iters, restarts, k, active, done, converged, reorth_needed, breakdown;
-  int m, max_iter, graph_mode, reorth;
-  double tol;
-  cudaGraphConditionalHandle h_while;
-  cudaGraphConditionalHandle h_if[kMaxRestart];
-};
+
 
 constexpr int kRedThreads = 256;
 
+// Reductions run over a virtual grid of nvb blocks (the launch grid of a single
+// solve, or the work items of one solve inside a batched launch): block vb stores
+// its partial sums, and the last of the nvb blocks to finish combines them.
 template <int NV>
-__device__ inline void block_reduce_store(double (&acc)[NV], double* partial, int stride) {
+__device__ inline void block_reduce_store(double (&acc)[NV], double* partial, int stride, int vb, int nv = NV) {
   __shared__ double red[kRedThreads / 32][NV > 0 ? NV : 1];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
+    if (k >= nv) break;
     double v = warp_sum(acc[k]);
     if (lane == 0) red[wid][k] = v;
   }
   __syncthreads();
-  if (threadIdx.x < NV) {
+  if (threadIdx.x < nv) {
     double s = 0;
     for (int w = 0; w < kRedThreads / 32; ++w) s += red[w][threadIdx.x];
-    partial[(size_t)blockIdx.x * stride + threadIdx.x] = s;
+    partial[(size_t)vb * stride + threadIdx.x] = s;
   }
 }
 
-// returns true in exactly one thread block: the last one to finish (all partials visible)
-__device__ inline bool last_block(unsigned int* counter) {
+// true in exactly one of the nvb blocks: the last one to finish (all partials visible)
+__device__ inline bool last_block(unsigned int* counter, int nvb) {
   __shared__ bool is_last;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned int t = atomicAdd(counter, 1u);
-    is_last = (t == gridDim.x - 1);
+    is_last = (t == (unsigned int)nvb - 1);
   }
   __syncthreads();
   if (is_last) __threadfence();
@@ -92,22 +84,21 @@ __device__ inline void set_cond(SolverScalars* S, cudaGraphConditionalHandle h, 
 }
 
 // restart / start: V0 = b - Ax (Ax in ax), |V0|^2, |b|^2
-__global__ void __launch_bounds__(kRedThreads) k_residual(const double* __restrict__ b, const double* __restrict__ ax,
-                                                          double* __restrict__ v0, int64_t N, double* partial,
-                                                          unsigned int* counter, SolverScalars* S, int first,
-                                                          int* status) {
+__device__ inline void residual_body(const double* __restrict__ b, const double* __restrict__ ax,
+                                     double* __restrict__ v0, int64_t N, double* partial, unsigned int* counter,
+                                     SolverScalars* S, int first, int* status, int vb, int nvb) {
   double acc[2] = {0.0, 0.0};
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = (int64_t)vb * blockDim.x + threadIdx.x; i < N; i += (int64_t)nvb * blockDim.x) {
     double bi = b[i];
     double r = bi - ax[i];
     v0[i] = r;
     acc[0] = fma(r, r, acc[0]);
     acc[1] = fma(bi, bi, acc[1]);
   }
-  block_reduce_store<2>(acc, partial, 4);
-  if (!last_block(counter)) return;
+  block_reduce_store<2>(acc, partial, 4, vb);
+  if (!last_block(counter, nvb)) return;
   __shared__ double tot[4];
-  sum_partials(partial, gridDim.x, 4, 2, tot);
+  sum_partials(partial, nvb, 4, 2, tot);
   if (threadIdx.x == 0) {
     *counter = 0;
     double rn = sqrt(tot[0]);
@@ -118,6 +109,7 @@ __global__ void __launch_bounds__(kRedThreads) k_residual(const double* __restri
       S->done = 0;
       S->converged = 0;
       S->breakdown = 0;
+      S->first = 0;
     } else {
       S->restarts += 1;
     }
@@ -144,61 +136,94 @@ __global__ void __launch_bounds__(kRedThreads) k_residual(const double* __restri
   }
 }
 
-// h_i = inv_norm_i <V_i, w> (i <= j), |w|^2 ; w = V[j+1]
-template <int NV>
-__global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restrict__ V, int64_t Np, int j,
-                                                          double* partial, unsigned int* counter, SolverScalars* S,
-                                                          int second) {
+__global__ void __launch_bounds__(kRedThreads) k_residual(const double* __restrict__ b, const double* __restrict__ ax,
+                                                          double* __restrict__ v0, int64_t N, double* partial,
+                                                          unsigned int* counter, SolverScalars* S, int first,
+                                                          int* status) {
+  residual_body(b, ax, v0, N, partial, counter, S, first, status, blockIdx.x, gridDim.x);
+}
+
+// h_i = inv_norm_i <V_i, w> (i < nv = j + 1), |w|^2 ; w = V[j+1].  NVMAX bounds nv at
+// compile time (a single solve instantiates NVMAX = nv; the batched engine 16).
+template <int NVMAX>
+__device__ inline void multidot_body(const double* __restrict__ V, int64_t Np, int j, int nv, double* partial,
+                                     unsigned int* counter, SolverScalars* S, int second, int vb, int nvb) {
   if (second && !S->reorth_needed) return;
   const double* w = V + (size_t)(j + 1) * Np;
-  double acc[NV + 1];
+  double acc[NVMAX + 1];
 #pragma unroll
-  for (int k = 0; k <= NV; ++k) acc[k] = 0.0;
+  for (int k = 0; k <= NVMAX; ++k) acc[k] = 0.0;
   const int64_t N2 = Np / 2;
   const double2* w2 = reinterpret_cast<const double2*>(w);
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N2; e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = (int64_t)vb * blockDim.x + threadIdx.x; e < N2; e += (int64_t)nvb * blockDim.x) {
     double2 wv = w2[e];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
+    for (int k = 0; k < NVMAX; ++k) {
+      if (k >= nv) break;
       double2 vv = reinterpret_cast<const double2*>(V + (size_t)k * Np)[e];
       acc[k] = fma(vv.x, wv.x, acc[k]);
       acc[k] = fma(vv.y, wv.y, acc[k]);
     }
-    acc[NV] = fma(wv.x, wv.x, acc[NV]);
-    acc[NV] = fma(wv.y, wv.y, acc[NV]);
+    acc[NVMAX] = fma(wv.x, wv.x, acc[NVMAX]);
+    acc[NVMAX] = fma(wv.y, wv.y, acc[NVMAX]);
   }
-  block_reduce_store<NV + 1>(acc, partial, kMaxRestart + 4);
-  if (!last_block(counter)) return;
+  {
+    // partials [h_0 .. h_j, |w|^2]: component nv is acc[NVMAX] (static register indices)
+    __shared__ double red[kRedThreads / 32][NVMAX + 1];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k <= NVMAX; ++k) {
+      if (k < nv || k == NVMAX) {
+        double v = warp_sum(acc[k]);
+        if (lane == 0) red[wid][k < nv ? k : nv] = v;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x <= nv) {
+      double s = 0;
+      for (int w = 0; w < kRedThreads / 32; ++w) s += red[w][threadIdx.x];
+      partial[(size_t)vb * (kMaxRestart + 4) + threadIdx.x] = s;
+    }
+  }
+  if (!last_block(counter, nvb)) return;
   __shared__ double tot[kMaxRestart + 4];
-  sum_partials(partial, gridDim.x, kMaxRestart + 4, NV + 1, tot);
+  sum_partials(partial, nvb, kMaxRestart + 4, nv + 1, tot);
   if (threadIdx.x == 0) {
     *counter = 0;
     if (!second) {
-      for (int k = 0; k < NV; ++k) S->hcol[k] = tot[k] * S->inv_norm[k];
-      S->w2_old = tot[NV];
+      for (int k = 0; k < nv; ++k) S->hcol[k] = tot[k] * S->inv_norm[k];
+      S->w2_old = tot[nv];
     } else {
       // second pass: store the correction in y[] temporarily
-      for (int k = 0; k < NV; ++k) S->y[k] = tot[k] * S->inv_norm[k];
+      for (int k = 0; k < nv; ++k) S->y[k] = tot[k] * S->inv_norm[k];
     }
   }
 }
 
-// w -= sum_i c_i V_i with c_i = h_i inv_norm_i ; |w|^2
 template <int NV>
-__global__ void __launch_bounds__(kRedThreads) k_update(double* __restrict__ V, int64_t Np, int j, double* partial,
-                                                        unsigned int* counter, SolverScalars* S, int second) {
+__global__ void __launch_bounds__(kRedThreads) k_multidot(const double* __restrict__ V, int64_t Np, int j,
+                                                          double* partial, unsigned int* counter, SolverScalars* S,
+                                                          int second) {
+  multidot_body<NV>(V, Np, j, NV, partial, counter, S, second, blockIdx.x, gridDim.x);
+}
+
+// w -= sum_i c_i V_i with c_i = h_i inv_norm_i (i < nv) ; |w|^2
+template <int NVMAX>
+__device__ inline void update_body(double* __restrict__ V, int64_t Np, int j, int nv, double* partial,
+                                   unsigned int* counter, SolverScalars* S, int second, int vb, int nvb) {
   if (second && !S->reorth_needed) return;
-  __shared__ double c[NV];
-  if (threadIdx.x < NV) c[threadIdx.x] = (second ? S->y[threadIdx.x] : S->hcol[threadIdx.x]) * S->inv_norm[threadIdx.x];
+  __shared__ double c[NVMAX];
+  if (threadIdx.x < nv) c[threadIdx.x] = (second ? S->y[threadIdx.x] : S->hcol[threadIdx.x]) * S->inv_norm[threadIdx.x];
   __syncthreads();
   double* w = V + (size_t)(j + 1) * Np;
   double acc[1] = {0.0};
   const int64_t N2 = Np / 2;
   double2* w2 = reinterpret_cast<double2*>(w);
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N2; e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = (int64_t)vb * blockDim.x + threadIdx.x; e < N2; e += (int64_t)nvb * blockDim.x) {
     double2 wv = w2[e];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
+    for (int k = 0; k < NVMAX; ++k) {
+      if (k >= nv) break;
       double2 vv = reinterpret_cast<const double2*>(V + (size_t)k * Np)[e];
       wv.x = fma(-c[k], vv.x, wv.x);
       wv.y = fma(-c[k], vv.y, wv.y);
@@ -207,25 +232,30 @@ __global__ void __launch_bounds__(kRedThreads) k_update(double* __restrict__ V, 
     acc[0] = fma(wv.x, wv.x, acc[0]);
     acc[0] = fma(wv.y, wv.y, acc[0]);
   }
-  block_reduce_store<1>(acc, partial, kMaxRestart + 4);
-  if (!last_block(counter)) return;
+  block_reduce_store<1>(acc, partial, kMaxRestart + 4, vb);
+  if (!last_block(counter, nvb)) return;
   __shared__ double tot[kMaxRestart + 4];
-  sum_partials(partial, gridDim.x, kMaxRestart + 4, 1, tot);
+  sum_partials(partial, nvb, kMaxRestart + 4, 1, tot);
   if (threadIdx.x == 0) {
     *counter = 0;
     S->w2 = tot[0];
     if (!second) {
       S->reorth_needed = S->reorth && (tot[0] < 0.5 * S->w2_old);
     } else {
-      for (int k = 0; k < NV; ++k) S->hcol[k] += S->y[k];
+      for (int k = 0; k < nv; ++k) S->hcol[k] += S->y[k];
       S->reorth_needed = 0;
     }
   }
 }
 
+template <int NV>
+__global__ void __launch_bounds__(kRedThreads) k_update(double* __restrict__ V, int64_t Np, int j, double* partial,
+                                                        unsigned int* counter, SolverScalars* S, int second) {
+  update_body<NV>(V, Np, j, NV, partial, counter, S, second, blockIdx.x, gridDim.x);
+}
+
 // Givens rotations on column j, estimate, flags (one thread)
-__global__ void k_arnoldi_step(SolverScalars* S, int j, int* status) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ inline void arnoldi_body(SolverScalars* S, int j, int* status) {
   const int L = kMaxRestart + 1;
   double* H = S->H;
   for (int i = 0; i <= j; ++i) H[i + L * j] = S->hcol[i];
@@ -260,9 +290,13 @@ __global__ void k_arnoldi_step(SolverScalars* S, int j, int* status) {
   if (j + 1 < S->m) set_cond(S, S->h_if[j + 1], !stop);
 }
 
-// y = H^-1 g (k x k upper triangular)
-__global__ void k_solve_y(SolverScalars* S) {
+__global__ void k_arnoldi_step(SolverScalars* S, int j, int* status) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  arnoldi_body(S, j, status);
+}
+
+// y = H^-1 g (k x k upper triangular)
+__device__ inline void solve_y_body(SolverScalars* S) {
   const int L = kMaxRestart + 1, k = S->k;
   for (int i = k - 1; i >= 0; --i) {
     double s = S->g[i];
@@ -273,19 +307,29 @@ __global__ void k_solve_y(SolverScalars* S) {
   for (int i = k; i < kMaxRestart; ++i) S->y[i] = 0.0;
 }
 
+__global__ void k_solve_y(SolverScalars* S) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  solve_y_body(S);
+}
+
 // x += sum_{i<k} y_i Z_i
-__global__ void __launch_bounds__(256) k_xupdate(double* __restrict__ x, const double* __restrict__ Z, int64_t Np,
-                                                 int64_t N, const SolverScalars* S) {
+__device__ inline void xupdate_body(double* __restrict__ x, const double* __restrict__ Z, int64_t Np, int64_t N,
+                                    const SolverScalars* S, int vb, int nvb) {
   __shared__ double y[kMaxRestart];
   __shared__ int k;
   if (threadIdx.x < kMaxRestart) y[threadIdx.x] = S->y[threadIdx.x];
   if (threadIdx.x == 0) k = S->k;
   __syncthreads();
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = (int64_t)vb * blockDim.x + threadIdx.x; i < N; i += (int64_t)nvb * blockDim.x) {
     double acc = x[i];
     for (int c = 0; c < k; ++c) acc = fma(y[c], Z[(size_t)c * Np + i], acc);
     x[i] = acc;
   }
+}
+
+__global__ void __launch_bounds__(256) k_xupdate(double* __restrict__ x, const double* __restrict__ Z, int64_t Np,
+                                                 int64_t N, const SolverScalars* S) {
+  xupdate_body(x, Z, Np, N, S, blockIdx.x, gridDim.x);
 }
 
 __global__ void k_init_scalars(SolverScalars* S, int m, int max_iter, double tol, int graph_mode, int reorth) {
@@ -296,6 +340,9 @@ __global__ void k_init_scalars(SolverScalars* S, int m, int max_iter, double tol
   S->reorth = reorth;
   S->reorth_needed = 0;
   S->k = 0;
+  S->first = 1;
+  S->active = 0;
+  S->done = 0;
 }
 
 __global__ void k_set_handles(SolverScalars* S, cudaGraphConditionalHandle hw, cudaGraphConditionalHandle* hif, int m) {
@@ -312,7 +359,10 @@ iim_status krylov_alloc(Problem& P) {
   P.x = (double*)dev_alloc(P, sizeof(double) * P.Npad);
   P.tmp = (double*)dev_alloc(P, sizeof(double) * P.Npad);
   P.sc = (SolverScalars*)dev_alloc(P, sizeof(SolverScalars));
-  P.red_blocks = 2 * kNumSMs;
+  // reduction blocks: two per SM for large vectors, fewer for small ones (every thread
+  // takes at least four double2 pairs); the sums depend only on this count
+  const int64_t pairs_per_block = (int64_t)kRedThreads * 4;
+  P.red_blocks = (int)std::min<int64_t>(2 * kNumSMs, std::max<int64_t>(1, (P.Npad / 2 + pairs_per_block - 1) / pairs_per_block));
   P.partial = (double*)dev_alloc(P, sizeof(double) * (size_t)P.red_blocks * (kMaxRestart + 4));
   P.counter = (unsigned int*)dev_alloc(P, sizeof(unsigned int) * 4);
   if (!P.V || !P.Z || !P.x || !P.tmp || !P.sc || !P.partial || !P.counter) return IIM_ERR_BUDGET;
@@ -502,6 +552,120 @@ void krylov_read_info(Problem& P, iim_solve_info* info) {
   info->restarts = h.restarts;
   info->converged = h.converged;
   info->relres = h.relres;
+}
+
+
+// ---------------------------------------------------------------------------- batched engine
+// Roles for this tick from each slot's FGMRES state (one thread per slot)
+__global__ void k_eng_plan(EngArgs A) {
+  const int* L = A.list(kListAll);
+  const int count = L[0];
+  const int* slot = L + 2 + A.cap;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
+    SlotDev& s = A.slots[slot[e]];
+    const SolverScalars* S = s.sc;
+    s.role = S->done ? kRoleIdle : (S->active ? kRoleIter : kRoleRestart);
+    s.j = S->k;
+  }
+}
+
+__global__ void __launch_bounds__(32) k_eng_solve_y(EngArgs A) {
+  eng_for_items(A, kListAll, [&](int si, int) {
+    const SlotDev& s = A.slots[si];
+    if (s.role != kRoleRestart || threadIdx.x != 0) return;
+    solve_y_body(s.sc);
+  });
+}
+
+__global__ void __launch_bounds__(256) k_eng_xupdate(EngArgs A) {
+  eng_for_items(A, kListXup, [&](int si, int item) {
+    const SlotDev& s = A.slots[si];
+    if (s.role != kRoleRestart) return;
+    xupdate_body(s.x, s.Z, s.Npad, s.g.N, s.sc, item, s.xup_blocks);
+  });
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_eng_multidot(EngArgs A, int second) {
+  eng_for_items(A, kListRed, [&](int si, int item) {
+    const SlotDev& s = A.slots[si];
+    if (s.role != kRoleIter) return;
+    multidot_body<kMaxRestart>(s.V, s.Npad, s.j, s.j + 1, s.partial, s.counter, s.sc, second, item, s.red_blocks);
+  });
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_eng_update(EngArgs A, int second) {
+  eng_for_items(A, kListRed, [&](int si, int item) {
+    const SlotDev& s = A.slots[si];
+    if (s.role != kRoleIter) return;
+    update_body<kMaxRestart>(s.V, s.Npad, s.j, s.j + 1, s.partial, s.counter, s.sc, second, item, s.red_blocks);
+  });
+}
+
+__global__ void __launch_bounds__(32) k_eng_arnoldi(EngArgs A) {
+  eng_for_items(A, kListAll, [&](int si, int) {
+    const SlotDev& s = A.slots[si];
+    if (s.role != kRoleIter || threadIdx.x != 0) return;
+    arnoldi_body(s.sc, s.j, s.status);
+  });
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_eng_residual(EngArgs A) {
+  eng_for_items(A, kListRed, [&](int si, int item) {
+    const SlotDev& s = A.slots[si];
+    if (s.role != kRoleRestart) return;
+    residual_body(s.b, s.tmp, s.V, s.g.N, s.partial, s.counter, s.sc, s.sc->first, s.status, item, s.red_blocks);
+  });
+}
+
+// End of a tick: done flags per slot, the number of unfinished slots, the tick budget
+// and the loop condition of the run graph (one block)
+__global__ void __launch_bounds__(256) k_eng_tick_end(EngArgs A, int* live, int* done_flags, int* ticks_left,
+                                                      cudaGraphConditionalHandle h, int use_cond) {
+  const int* L = A.list(kListAll);
+  const int count = L[0];
+  const int* slot = L + 2 + A.cap;
+  int mine = 0;
+  for (int e = threadIdx.x; e < count; e += blockDim.x) {
+    const int si = slot[e];
+    const int d = A.slots[si].sc->done;
+    done_flags[si] = d;
+    mine += !d;
+  }
+  __shared__ int red[256 / 32];
+  for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mine;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int k = 0; k < 256 / 32; ++k) n += red[k];
+    *live = n;
+    const int t = *ticks_left - 1;
+    *ticks_left = t;
+    if (use_cond) cudaGraphSetConditional(h, (n > 0 && t > 0) ? 1u : 0u);
+  }
+}
+
+void eng_launch_krylov_head(const EngArgs& A, cudaStream_t s) {
+  IIM_LAUNCH(k_eng_plan, 4, 256, 0, s, A);
+  IIM_LAUNCH(k_eng_solve_y, eng_grid((const void*)k_eng_solve_y, 32, 0), 32, 0, s, A);
+  IIM_LAUNCH(k_eng_xupdate, eng_grid((const void*)k_eng_xupdate, 256, 0), 256, 0, s, A);
+}
+
+// ctl: [0] unfinished slots, [1] tick budget, [2 + slot] done flag of each slot
+void eng_launch_krylov_tail(const EngArgs& A, int* ctl, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
+  const int gr = eng_grid((const void*)k_eng_multidot, kRedThreads, 0);
+  const int gu = eng_grid((const void*)k_eng_update, kRedThreads, 0);
+  IIM_LAUNCH(k_eng_multidot, gr, kRedThreads, 0, s, A, 0);
+  IIM_LAUNCH(k_eng_update, gu, kRedThreads, 0, s, A, 0);
+  IIM_LAUNCH(k_eng_multidot, gr, kRedThreads, 0, s, A, 1);
+  IIM_LAUNCH(k_eng_update, gu, kRedThreads, 0, s, A, 1);
+  IIM_LAUNCH(k_eng_arnoldi, eng_grid((const void*)k_eng_arnoldi, 32, 0), 32, 0, s, A);
+  IIM_LAUNCH(k_eng_residual, eng_grid((const void*)k_eng_residual, kRedThreads, 0), kRedThreads, 0, s, A);
+  IIM_LAUNCH(k_eng_tick_end, 1, 256, 0, s, A, ctl, ctl + 2, ctl + 1, h, use_cond);
+}
+
+void eng_init_scalars(Problem& P, cudaStream_t s) {
+  IIM_LAUNCH(k_init_scalars, 1, 1, 0, s, P.sc, P.opt.restart, P.opt.max_iter, P.opt.tol, 0, P.opt.reorth);
 }
 
 }  // namespace iim

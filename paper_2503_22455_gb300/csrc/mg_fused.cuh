@@ -66,14 +66,14 @@ template <typename T>
 __device__ inline T tab2(const LevelK<T>& L, int r, int k) { return L.tab[(size_t)r * 5 + k]; }
 
 template <typename T, int TX, int TY, int MODE>
-__global__ void __launch_bounds__(256) k_mg2d(Fine2DParams<T> P) {
+__device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx, const int by) {
   constexpr int SX = TX + 2 * kH, SY = TY + 2 * kH, S = SX * SY;
   __shared__ T us[S];
   __shared__ T fs[S];
   __shared__ int as[S];
   const LevelK<T>& L = P.L;
   const int n = L.n;
-  const int x0 = blockIdx.x * TX - kH, y0 = blockIdx.y * TY - kH;
+  const int x0 = bx * TX - kH, y0 = by * TY - kH;
   const bool finest_in = MODE == 0 && P.v != nullptr;
   const T vs = finest_in ? (T)(P.vscale ? *P.vscale : 1.0) : (T)1;
   {
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(256) k_mg2d(Fine2DParams<T> P) {
     const LevelK<T>& C = P.C;
     for (int e = threadIdx.x; e < (TX / 2) * (TY / 2); e += blockDim.x) {
       const int cx = e % (TX / 2), cy = e / (TX / 2);
-      const int gcx = blockIdx.x * (TX / 2) + cx, gcy = blockIdx.y * (TY / 2) + cy;
+      const int gcx = bx * (TX / 2) + cx, gcy = by * (TY / 2) + cy;
       if (gcx >= C.n || gcy >= C.n) continue;
       const int64_t ci = (int64_t)gcy * C.n + gcx;
       const int b = (kH + 2 * cy) * SX + kH + 2 * cx;
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(256) k_mg2d(Fine2DParams<T> P) {
   }
   for (int e = threadIdx.x; e < TX * TY; e += blockDim.x) {
     const int tx = e % TX, ty = e / TX;
-    const int gx = blockIdx.x * TX + tx, gy = blockIdx.y * TY + ty;
+    const int gx = bx * TX + tx, gy = by * TY + ty;
     if (gx >= n || gy >= n) continue;
     const int64_t g = (int64_t)gy * n + gx;
     const int se = (ty + kH) * SX + tx + kH;
@@ -224,6 +224,11 @@ __global__ void __launch_bounds__(256) k_mg2d(Fine2DParams<T> P) {
     else P.u_out[g] = us[se];
     if (finest_in) L.f[g] = fs[se];
   }
+}
+
+template <typename T, int TX, int TY, int MODE>
+__global__ void __launch_bounds__(256) k_mg2d(Fine2DParams<T> P) {
+  mg2d_tile<T, TX, TY, MODE>(P, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------- coarse tail (one CTA)
@@ -296,7 +301,8 @@ struct NodeWalk {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kTailThreads) k_vcycle_tail(TailParams<T> P) {
+__device__ __forceinline__ void vcycle_tail_body(const TailParams<T>& P, const double* v_in, const double* vscale,
+                                                 double* z_out) {
   extern __shared__ unsigned char smraw[];
   const int tot = P.off[P.nlev];
   T* su = (T*)smraw;
@@ -316,10 +322,10 @@ __global__ void __launch_bounds__(kTailThreads) k_vcycle_tail(TailParams<T> P) {
   auto table = [&](int k) -> const T* { return P.stage_tables ? st + P.toff[k] : P.L[k].tab; };
   {
     const LevelK<T>& L = P.L[0];
-    const T vs = P.v ? (T)(P.vscale ? *P.vscale : 1.0) : (T)1;
+    const T vs = v_in ? (T)(vscale ? *vscale : 1.0) : (T)1;
     for (int i = tid; i < L.N; i += nt) {
       T f = 0;
-      if (L.aux[i] != -2) f = P.v ? (T)P.v[i] * (vs * (P.phase[i] ? P.inv_bp : P.inv_bm)) : L.f[i];
+      if (L.aux[i] != -2) f = v_in ? (T)v_in[i] * (vs * (P.phase[i] ? P.inv_bp : P.inv_bm)) : L.f[i];
       sf[i] = f;
     }
   }
@@ -442,9 +448,14 @@ __global__ void __launch_bounds__(kTailThreads) k_vcycle_tail(TailParams<T> P) {
   const LevelK<T>& L = P.L[0];
   for (int i = tid; i < L.N; i += nt) {
     const T u = su[i];
-    if (P.z) P.z[i] = (double)u;
+    if (z_out) z_out[i] = (double)u;
     else P.u_out[i] = u;
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTailThreads) k_vcycle_tail(TailParams<T> P) {
+  vcycle_tail_body<T>(P, P.v, P.vscale, P.z);
 }
 
 }  // namespace iim

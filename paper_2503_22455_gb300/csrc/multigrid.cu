@@ -9,8 +9,7 @@
 // is divided by beta_sigma when it enters the FP32 hierarchy.
 #include <utility>
 
-#include "kernels.cuh"
-#include "mg_fused.cuh"
+#include "engine.cuh"
 
 namespace iim {
 
@@ -61,11 +60,10 @@ __device__ inline T diag_of(const LevelView<T>& L, T dreg, int a) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_smooth(LevelView<T> L, T ih2, T dreg, T* __restrict__ u,
-                                                const T* __restrict__ f, int colour) {
+__device__ __forceinline__ void smooth_body(const LevelView<T>& L, T ih2, T dreg, T* __restrict__ u,
+                                            const T* __restrict__ f, int colour, int64_t t) {
   // one thread per node of the colour: node = 2 * t + parity fix-up along x
   const GridView& g = L.g;
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t rows = g.N / g.n;
   int64_t half = (g.n + 1) / 2;
   if (t >= rows * half) return;
@@ -83,12 +81,17 @@ __global__ void __launch_bounds__(256) k_smooth(LevelView<T> L, T ih2, T dreg, T
   u[i] = dg != (T)0 ? (f[i] - s) / dg : (T)0;
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_smooth(LevelView<T> L, T ih2, T dreg, T* __restrict__ u,
+                                                const T* __restrict__ f, int colour) {
+  smooth_body<T>(L, ih2, dreg, u, f, colour, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // coarse f = mean over the 2^d children of r = f - L u (zero at non-unknowns)
 template <typename T>
-__global__ void __launch_bounds__(256) k_resid_restrict(LevelView<T> F, T ih2, T dreg, const T* __restrict__ u,
-                                                        const T* __restrict__ f, GridView gc,
-                                                        const int32_t* __restrict__ aux_c, T* __restrict__ fc) {
-  int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void resid_restrict_body(const LevelView<T>& F, T ih2, T dreg, const T* __restrict__ u,
+                                                    const T* __restrict__ f, const GridView& gc,
+                                                    const int32_t* __restrict__ aux_c, T* __restrict__ fc, int64_t I) {
   if (I >= gc.N) return;
   if (aux_c[I] == -2) { fc[I] = (T)0; return; }
   int mc[3];
@@ -107,12 +110,18 @@ __global__ void __launch_bounds__(256) k_resid_restrict(LevelView<T> F, T ih2, T
   fc[I] = acc / (T)nch;
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_resid_restrict(LevelView<T> F, T ih2, T dreg, const T* __restrict__ u,
+                                                        const T* __restrict__ f, GridView gc,
+                                                        const int32_t* __restrict__ aux_c, T* __restrict__ fc) {
+  resid_restrict_body<T>(F, ih2, dreg, u, f, gc, aux_c, fc, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // u_fine += P e_coarse at fine unknowns
 template <typename T>
-__global__ void __launch_bounds__(256) k_prolong(GridView gf, const int32_t* __restrict__ aux_f, T* __restrict__ uf,
-                                                 GridView gc, const int32_t* __restrict__ aux_c,
-                                                 const T* __restrict__ ec, int neumann) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void prolong_body(const GridView& gf, const int32_t* __restrict__ aux_f, T* __restrict__ uf,
+                                             const GridView& gc, const int32_t* __restrict__ aux_c,
+                                             const T* __restrict__ ec, int neumann, int64_t i) {
   if (i >= gf.N) return;
   if (aux_f[i] == -2) return;
   int m[3];
@@ -144,16 +153,30 @@ __global__ void __launch_bounds__(256) k_prolong(GridView gf, const int32_t* __r
   uf[i] += acc;
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong(GridView gf, const int32_t* __restrict__ aux_f, T* __restrict__ uf,
+                                                 GridView gc, const int32_t* __restrict__ aux_c,
+                                                 const T* __restrict__ ec, int neumann) {
+  prolong_body<T>(gf, aux_f, uf, gc, aux_c, ec, neumann, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // f_fine = v * scale / beta_sigma at unknowns (FP64 -> level precision)
 template <typename T>
-__global__ void k_bridge_in(GridView g, const double* __restrict__ v, const double* __restrict__ scale,
-                            const uint8_t* __restrict__ phase, const int32_t* __restrict__ aux, double inv_bp,
-                            double inv_bm, T* __restrict__ f) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void bridge_in_body(const GridView& g, const double* __restrict__ v,
+                                               const double* __restrict__ scale, const uint8_t* __restrict__ phase,
+                                               const int32_t* __restrict__ aux, double inv_bp, double inv_bm,
+                                               T* __restrict__ f, int64_t i) {
   if (i >= g.N) return;
   if (aux[i] == -2) { f[i] = (T)0; return; }
   const T sc = (T)((scale ? *scale : 1.0) * (phase[i] ? inv_bp : inv_bm));
   f[i] = (T)v[i] * sc;
+}
+
+template <typename T>
+__global__ void k_bridge_in(GridView g, const double* __restrict__ v, const double* __restrict__ scale,
+                            const uint8_t* __restrict__ phase, const int32_t* __restrict__ aux, double inv_bp,
+                            double inv_bm, T* __restrict__ f) {
+  bridge_in_body<T>(g, v, scale, phase, aux, inv_bp, inv_bm, f, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 template <typename T>
@@ -370,10 +393,13 @@ static size_t tail_start(const Problem& P) {
   while (l + 1 < P.lv.size() && P.lv[l].g.N > kTailThreads) ++l;
   return l;
 }
+size_t mg_tail_start(const Problem& P) { return tail_start(P); }
 
+// Parameters of the single-CTA tail over levels l0 .. end; *smem gets its shared
+// memory bytes.  The irregular-row tables are staged in shared memory when the
+// total stays within smem_limit (staging changes where they are read, not the result).
 template <typename T>
-static void launch_tail(Problem& P, size_t l0, const double* v, const double* vscale, double* z, cudaStream_t s,
-                        T* u_out = nullptr) {
+TailParams<T> make_tail_params(Problem& P, size_t l0, T* u_out, size_t smem_limit, size_t* smem) {
   TailParams<T> tp;
   tp.u_out = u_out ? u_out : (T*)P.lv[l0].u;
   tp.nlev = (int)(P.lv.size() - l0);
@@ -394,7 +420,7 @@ static void launch_tail(Problem& P, size_t l0, const double* v, const double* vs
   }
   tp.toff[tp.nlev] = toff;
   const size_t base = (sizeof(T) * 2 + sizeof(int)) * (size_t)off;
-  tp.stage_tables = base + sizeof(T) * (size_t)toff <= 200 * 1024;
+  tp.stage_tables = base + sizeof(T) * (size_t)toff <= smem_limit;
   if (!tp.stage_tables) {
     toff = 0;
     for (int k = 0; k <= tp.nlev; ++k) tp.toff[k] = 0;
@@ -406,13 +432,25 @@ static void launch_tail(Problem& P, size_t l0, const double* v, const double* vs
   tp.map = P.coarse_map;
   const T* inv = (const T*)(sizeof(T) == 8 ? (void*)P.coarse_lu64 : (void*)P.coarse_lu32);
   tp.inv = inv + (size_t)P.coarse_nu * P.coarse_nu;
-  tp.v = v;
-  tp.vscale = vscale;
+  tp.v = nullptr;
+  tp.vscale = nullptr;
   tp.phase = P.phase;
   tp.inv_bp = (T)(1.0 / P.desc.beta_plus);
   tp.inv_bm = (T)(1.0 / P.desc.beta_minus);
+  tp.z = nullptr;
+  *smem = base + sizeof(T) * (size_t)toff;
+  return tp;
+}
+template TailParams<float> make_tail_params<float>(Problem&, size_t, float*, size_t, size_t*);
+
+template <typename T>
+static void launch_tail(Problem& P, size_t l0, const double* v, const double* vscale, double* z, cudaStream_t s,
+                        T* u_out = nullptr) {
+  size_t smem = 0;
+  TailParams<T> tp = make_tail_params<T>(P, l0, u_out, 200 * 1024, &smem);
+  tp.v = v;
+  tp.vscale = vscale;
   tp.z = z;
-  const size_t smem = base + sizeof(T) * (size_t)toff;
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_vcycle_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   IIM_LAUNCH(k_vcycle_tail<T>, 1, kTailThreads, smem, s, tp);
 }
@@ -573,6 +611,145 @@ void mg_coarse_factor(Problem& P, cudaStream_t s) {
     IIM_LAUNCH(k_coarse_lu<float>, 1, 1024, in_smem ? sm : 0, s, P.coarse_lu32, nu, P.coarse_piv,
                P.coarse_lu32 + (size_t)nu * nu, P.d_status, in_smem);
   }
+}
+
+
+// ---------------------------------------------------------------------------- batched engine
+// Grouped forms of the V-cycle kernels: each item is one block of the single-problem
+// launch (a tile of the 2D fused kernels, 256 nodes of the 3D kernels, the whole
+// tail), so a slot's V-cycle is the one its own solve would run.
+
+__device__ __forceinline__ const double* eng_vj(const SlotDev& s) { return s.V + (size_t)s.j * s.Npad; }
+__device__ __forceinline__ double* eng_zj(const SlotDev& s) { return s.Z + (size_t)s.j * s.Npad; }
+
+template <int TX, int TY, int MODE>
+__global__ void __launch_bounds__(256) k_eng_mg2d(EngArgs A, int list, int d, int in_sel, int out_sel, int res_sel) {
+  eng_for_items(A, list, [&](int si, int item) {
+    const SlotDev& s = A.slots[si];
+    if (s.role != kRoleIter) return;
+    Fine2DParams<float> fp;
+    fp.L = s.lev[d];
+    fp.C = s.lev[d + 1 < s.nlev ? d + 1 : d];
+    float* b0 = s.lev[d].u;
+    float* b1 = s.u2[d];
+    fp.u_in = MODE == 0 ? nullptr : (in_sel ? b1 : b0);
+    fp.u_out = out_sel ? b1 : b0;
+    fp.uc = nullptr;
+    if (MODE == 2) fp.uc = (d + 1 < s.nfine && res_sel) ? s.u2[d + 1] : s.lev[d + 1].u;
+    fp.neumann = s.neumann;
+    fp.v = (MODE == 0 && d == 0) ? eng_vj(s) : nullptr;
+    fp.vscale = &s.sc->inv_norm[s.j];
+    fp.phase = s.phase;
+    fp.inv_bp = s.inv_bp;
+    fp.inv_bm = s.inv_bm;
+    fp.z = (MODE == 3 && d == 0) ? eng_zj(s) : nullptr;
+    const int gx = (s.lev[d].n + TX - 1) / TX;
+    mg2d_tile<float, TX, TY, MODE>(fp, item % gx, item / gx);
+  });
+}
+
+__global__ void __launch_bounds__(kTailThreads) k_eng_tail(EngArgs A) {
+  eng_for_items(A, kListTail, [&](int si, int) {
+    const SlotDev& s = A.slots[si];
+    if (s.role != kRoleIter) return;
+    const bool top = s.nfine == 0;
+    vcycle_tail_body<float>(s.tail, top ? eng_vj(s) : nullptr, top ? &s.sc->inv_norm[s.j] : nullptr,
+                            top ? eng_zj(s) : nullptr);
+  });
+}
+
+__device__ __forceinline__ LevelView<float> eng_view(const SlotDev& s, int d) {
+  LevelView<float> v;
+  v.g.dim = s.lev[d].dim;
+  v.g.n = s.lev[d].n;
+  v.g.N = s.lev[d].N;
+  v.g.h = 2.0 / s.lev[d].n;
+  v.aux = s.lev[d].aux;
+  v.tab = s.lev[d].tab;
+  return v;
+}
+
+// 3D kernels, kind: 0 bridge in, 1 zero, 2 smooth, 3 residual + restriction, 4 prolongation, 5 bridge out
+template <int KIND>
+__global__ void __launch_bounds__(256) k_eng_mg3d(EngArgs A, int list, int d, int colour) {
+  eng_for_items(A, list, [&](int si, int item) {
+    const SlotDev& s = A.slots[si];
+    if (s.role != kRoleIter) return;
+    const int64_t i = (int64_t)item * 256 + threadIdx.x;
+    const LevelK<float>& K = s.lev[d];
+    const LevelView<float> V = eng_view(s, d);
+    if (KIND == 0) {
+      bridge_in_body<float>(V.g, eng_vj(s), &s.sc->inv_norm[s.j], s.phase, K.aux, 1.0 / s.GP.beta_p,
+                            1.0 / s.GP.beta_m, K.f, i);
+    } else if (KIND == 1) {
+      if (i < K.N) K.u[i] = 0.f;
+    } else if (KIND == 2) {
+      smooth_body<float>(V, K.ih2, K.dreg, K.u, K.f, colour, i);
+    } else if (KIND == 3) {
+      const LevelView<float> C = eng_view(s, d + 1);
+      resid_restrict_body<float>(V, K.ih2, K.dreg, K.u, K.f, C.g, C.aux, s.lev[d + 1].f, i);
+    } else if (KIND == 4) {
+      const LevelView<float> C = eng_view(s, d + 1);
+      prolong_body<float>(V.g, K.aux, K.u, C.g, C.aux, s.lev[d + 1].u, s.neumann, i);
+    } else {
+      if (i < K.N) eng_zj(s)[i] = (double)K.u[i];
+    }
+  });
+}
+
+void eng_mg2d_tile_items(int n, int shape, int* gx, int* gy) {
+  *gx = ceil_div(n, kShapeTX[shape]);
+  *gy = ceil_div(n, kShapeTY[shape]);
+}
+
+template <int TX, int TY>
+static void launch_eng_mg2d(const EngArgs& A, const EngMgStep& st, cudaStream_t s) {
+  const int list = kListMg2d + st.depth * kEngShapes + st.shape;
+#define IIM_ENG_MG2D(MODE)                                                                                     \
+  IIM_LAUNCH((k_eng_mg2d<TX, TY, MODE>), eng_grid((const void*)k_eng_mg2d<TX, TY, MODE>, 256, 0), 256, 0, s, A, \
+             list, st.depth, st.in_sel, st.out_sel, st.res_sel)
+  switch (st.mode) {
+    case 0: IIM_ENG_MG2D(0); break;
+    case 1: IIM_ENG_MG2D(1); break;
+    case 2: IIM_ENG_MG2D(2); break;
+    case 3: IIM_ENG_MG2D(3); break;
+    default: IIM_ENG_MG2D(4); break;
+  }
+#undef IIM_ENG_MG2D
+}
+
+void eng_launch_mg(const EngArgs& A, const EngMgStep& st, size_t tail_smem, cudaStream_t s) {
+  if (st.kind == 0) {
+    switch (st.shape) {
+      case 0: launch_eng_mg2d<32, 8>(A, st, s); break;
+      case 1: launch_eng_mg2d<64, 8>(A, st, s); break;
+      case 2: launch_eng_mg2d<32, 16>(A, st, s); break;
+      default: launch_eng_mg2d<64, 16>(A, st, s); break;
+    }
+    return;
+  }
+  if (st.kind == 1) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_eng_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr = true;
+    }
+    IIM_LAUNCH(k_eng_tail, eng_grid((const void*)k_eng_tail, kTailThreads, tail_smem), kTailThreads, tail_smem, s, A);
+    return;
+  }
+  const int k3 = st.kind - 2;
+  const int d = st.depth;
+#define IIM_ENG_MG3D(KIND, LIST)                                                                             \
+  IIM_LAUNCH(k_eng_mg3d<KIND>, eng_grid((const void*)k_eng_mg3d<KIND>, 256, 0), 256, 0, s, A, LIST, d, st.colour)
+  switch (k3) {
+    case 0: IIM_ENG_MG3D(0, kList3dN + 0); break;
+    case 1: IIM_ENG_MG3D(1, kList3dN + d); break;
+    case 2: IIM_ENG_MG3D(2, kList3dCol + d); break;
+    case 3: IIM_ENG_MG3D(3, kList3dCoarse + d); break;
+    case 4: IIM_ENG_MG3D(4, kList3dN + d); break;
+    default: IIM_ENG_MG3D(5, kList3dN + 0); break;
+  }
+#undef IIM_ENG_MG3D
 }
 
 }  // namespace iim

@@ -15,21 +15,15 @@
 #include <mutex>
 #include <string>
 
-#include "kernels.cuh"
+#include "engine.cuh"
 
 namespace iim {
 
-struct StencilCoef {
-  double c0[2];            // d * a_0 * beta_sigma / h^2 for sigma = minus, plus
-  double cj[2][kMaxW];     // a_j * beta_sigma / h^2
-};
 
 template <int D, int W>
-__global__ void __launch_bounds__(256) k_ho_stencil(GridView g, StencilCoef C, int interface_,
-                                                    const double* __restrict__ u,
-                                                    const uint8_t* __restrict__ phase, double* __restrict__ w) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= g.N) return;
+__device__ __forceinline__ void ho_stencil_node(const GridView& g, const StencilCoef& C, int interface_,
+                                                const double* __restrict__ u, const uint8_t* __restrict__ phase,
+                                                double* __restrict__ w, int64_t i) {
   const int n = g.n;
   const uint8_t ph = phase[i];
   if (!interface_ && !ph) { w[i] = 0.0; return; }
@@ -67,19 +61,15 @@ __global__ void __launch_bounds__(256) k_ho_stencil(GridView g, StencilCoef C, i
   w[i] = acc;
 }
 
-struct GhostParams {
-  int nfit, w, rcap, bc, interface_, with_data;
-  double beta_p, beta_m;
-  const int* K;
-  const int32_t* fit_R;
-  const int32_t* fit_nodes;
-  const double* fit_coef;
-  const double* fit_cdat;
-  const double* g;          // ubar / qbar per control point
-  const double* j0;
-  const double* j1;
-  double* G;                // [nfit][w]
-};
+template <int D, int W>
+__global__ void __launch_bounds__(256) k_ho_stencil(GridView g, StencilCoef C, int interface_,
+                                                    const double* __restrict__ u,
+                                                    const uint8_t* __restrict__ phase, double* __restrict__ w) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.N) return;
+  ho_stencil_node<D, W>(g, C, interface_, u, phase, w, i);
+}
+
 
 // Eight lanes per control point: each lane accumulates an eighth of the X_c terms
 // of every row (sequential FMAs, no per-term reduction), then two shuffle steps
@@ -95,8 +85,7 @@ __device__ inline double quad_sum(double v) {
 }
 
 template <int W>
-__global__ void __launch_bounds__(256) k_ho_ghost(GhostParams P, const double* __restrict__ u) {
-  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void ho_ghost_body(const GhostParams& P, const double* __restrict__ u, int gid) {
   const int c = gid / kGhostLanes, q = gid % kGhostLanes;
   const int K = *P.K;
   const bool live = c < K;                       // every lane takes part in the shuffles
@@ -151,24 +140,14 @@ __global__ void __launch_bounds__(256) k_ho_ghost(GhostParams P, const double* _
   }
 }
 
-struct CorrectParams {
-  GridView g;
-  int w, q, with_data, n_aff_cap, nfit_cap;
-  const int* n_aff;
-  const int32_t* aff_node;
-  const int32_t* aff_fit;
-  const int32_t* aff_j;
-  const double* G;
-  const uint8_t* phase;
-  const double* box;        // [B] face data
-  double a[2 * kMaxW + 1];
-  double scale[2];          // beta_sigma / h^2
-  double box_w[kMaxW][8];
-};
+template <int W>
+__global__ void __launch_bounds__(256) k_ho_ghost(GhostParams P, const double* __restrict__ u) {
+  ho_ghost_body<W>(P, u, blockIdx.x * blockDim.x + threadIdx.x);
+}
 
-__global__ void __launch_bounds__(256) k_ho_correct(CorrectParams P, const double* __restrict__ u,
-                                                    double* __restrict__ w) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
+
+__device__ __forceinline__ void ho_correct_body(const CorrectParams& P, const double* __restrict__ u,
+                                                double* __restrict__ w, int t) {
   if (t >= *P.n_aff || t >= P.n_aff_cap) return;
   const GridView& g = P.g;
   const int n = g.n, d = g.dim, W = P.w;
@@ -220,6 +199,11 @@ __global__ void __launch_bounds__(256) k_ho_correct(CorrectParams P, const doubl
     }
   }
   w[i] += P.scale[ph ? 1 : 0] * acc;
+}
+
+__global__ void __launch_bounds__(256) k_ho_correct(CorrectParams P, const double* __restrict__ u,
+                                                    double* __restrict__ w) {
+  ho_correct_body(P, u, w, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 static StencilCoef stencil_coef(const Problem& P) {
@@ -419,6 +403,105 @@ iim_status ho_apply_noalloc(Problem& P, const double* u, double* w, bool with_da
     for (int mm = 0; mm < 8; ++mm) CP.box_w[k][mm] = P.box_w[k][mm];
   if (P.aff_cap > 0) IIM_LAUNCH(k_ho_correct, ceil_div(P.aff_cap, 64), 64, 0, s, CP, u, w);
   return IIM_OK;
+}
+
+
+// ---------------------------------------------------------------------------- batched engine
+// Grouped forms of the three operator kernels.  A stencil item is four blocks of
+// the single-problem launch; ghost and correction items are one block each.
+template <int D, int W>
+__global__ void __launch_bounds__(kEngThreads) k_eng_stencil(EngArgs A) {
+  eng_for_items(A, kListStencil + (D - 2) * 2 + (W - 2), [&](int si, int item) {
+    const SlotDev& s = A.slots[si];
+    if (s.role == kRoleIdle) return;
+    const double* u;
+    double* w;
+    eng_apply_io(s, u, w);
+    const int64_t base = (int64_t)item * (4 * kEngThreads) + threadIdx.x;
+    const int64_t N = s.g.N;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t i = base + k * kEngThreads;
+      if (i < N) ho_stencil_node<D, W>(s.g, s.C, s.iface, u, s.phase, w, i);
+    }
+  });
+}
+
+template <int W>
+__global__ void __launch_bounds__(64) k_eng_ghost(EngArgs A) {
+  eng_for_items(A, kListGhost + (W - 2), [&](int si, int item) {
+    const SlotDev& s = A.slots[si];
+    if (s.role == kRoleIdle) return;
+    const double* u;
+    double* w;
+    eng_apply_io(s, u, w);
+    ho_ghost_body<W>(s.GP, u, item * 64 + threadIdx.x);
+  });
+}
+
+__global__ void __launch_bounds__(64) k_eng_correct(EngArgs A) {
+  eng_for_items(A, kListCorrect, [&](int si, int item) {
+    const SlotDev& s = A.slots[si];
+    if (s.role == kRoleIdle) return;
+    const double* u;
+    double* w;
+    eng_apply_io(s, u, w);
+    ho_correct_body(s.CP, u, w, item * 64 + threadIdx.x);
+  });
+}
+
+void eng_launch_apply(const EngArgs& A, const unsigned char* present, cudaStream_t s) {
+#define IIM_ENG_ST(D, W)                                                                                       \
+  if (present[kListStencil + (D - 2) * 2 + (W - 2)])                                                          \
+    IIM_LAUNCH((k_eng_stencil<D, W>), eng_grid((const void*)k_eng_stencil<D, W>, kEngThreads, 0), kEngThreads, 0, s, A);
+  IIM_ENG_ST(2, 2) IIM_ENG_ST(2, 3) IIM_ENG_ST(3, 2) IIM_ENG_ST(3, 3)
+#undef IIM_ENG_ST
+  if (present[kListGhost + 0]) IIM_LAUNCH(k_eng_ghost<2>, eng_grid((const void*)k_eng_ghost<2>, 64, 0), 64, 0, s, A);
+  if (present[kListGhost + 1]) IIM_LAUNCH(k_eng_ghost<3>, eng_grid((const void*)k_eng_ghost<3>, 64, 0), 64, 0, s, A);
+  if (present[kListCorrect]) IIM_LAUNCH(k_eng_correct, eng_grid((const void*)k_eng_correct, 64, 0), 64, 0, s, A);
+}
+
+// the operator's per-problem parameters (homogeneous: the data enter through b)
+void eng_operator_params(Problem& P, StencilCoef* C, GhostParams* GP, CorrectParams* CP) {
+  *C = stencil_coef(P);
+  GhostParams& G = *GP;
+  G.nfit = P.nfit_cap;
+  G.w = P.w;
+  G.rcap = P.rcap;
+  G.bc = P.desc.bc;
+  G.interface_ = P.desc.bc == IIM_BC_INTERFACE;
+  G.with_data = 0;
+  G.beta_p = P.desc.beta_plus;
+  G.beta_m = P.desc.beta_minus;
+  G.K = P.d_counts + 0;
+  G.fit_R = P.fit_R;
+  G.fit_nodes = P.fit_nodes;
+  G.fit_coef = P.fit_coef;
+  G.fit_cdat = P.fit_cdat;
+  G.g = P.d_g;
+  G.j0 = P.d_j0;
+  G.j1 = P.d_j1;
+  G.G = P.G;
+  CorrectParams& Q = *CP;
+  Q.g = P.g;
+  Q.w = P.w;
+  Q.q = P.q;
+  Q.with_data = 0;
+  Q.n_aff_cap = P.aff_cap;
+  Q.nfit_cap = P.nfit_cap;
+  Q.n_aff = P.d_counts + 1;
+  Q.aff_node = P.aff_node;
+  Q.aff_fit = P.aff_fit;
+  Q.aff_j = P.aff_j;
+  Q.G = P.G;
+  Q.phase = P.phase;
+  Q.box = P.d_box;
+  for (int k = 0; k < 2 * kMaxW + 1; ++k) Q.a[k] = k < 2 * P.w + 1 ? P.a[k] : 0.0;
+  const double h2 = P.g.h * P.g.h;
+  Q.scale[0] = P.desc.beta_minus / h2;
+  Q.scale[1] = P.desc.beta_plus / h2;
+  for (int k = 0; k < kMaxW; ++k)
+    for (int mm = 0; mm < 8; ++mm) Q.box_w[k][mm] = P.box_w[k][mm];
 }
 
 }  // namespace iim

@@ -1,0 +1,323 @@
+// Request loop over the batched engine: requests are admitted while the device
+// memory they need fits a budget, set up on their own streams while the engine
+// runs the resident solves, join the engine at the next run (continuous batching
+// at the granularity of a run of a few ticks) and leave it when their solve ends.
+// Latency is measured from submission to the moment the solution is on the host.
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace iim {
+
+// Device bytes a problem of this descriptor will hold, before it exists: the
+// per-node workspace of create exactly, and the fits for a body whose control-point
+// count is about 3n (2D) or 1.5 n^2 (3D).  It only decides when to try an
+// admission; the exact size, known once the problem exists, is what is charged.
+static size_t estimate_bytes(const iim_problem_desc& d, const iim_options& o) {
+  const double N = (double)d.n * d.n * (d.dim == 3 ? d.n : 1);
+  const double vec = 8.0 * (2 * o.restart + 3);               // V, Z, x, tmp
+  const double grid = 1.0 + 8.0 * d.dim + 8.0 + 8.0;          // phase, edge flags/ids, affected flags/ids, b
+  const double mg = (d.dim == 2 ? 4.0 / 3.0 : 8.0 / 7.0) * (1.0 + 12.0 + 12.0);   // phase, aux/flag/idx, u/u2/f
+  const double K = d.dim == 2 ? 3.0 * d.n : 1.5 * (double)d.n * d.n;
+  const int w = d.order / 2, rc = rows_cap(d.dim, d.order);
+  const double nfit = 1.25 * K * (d.bc == IIM_BC_INTERFACE ? 2 : 1) + 64;
+  const double fit = nfit * (4.0 * rc + 8.0 * (w + 1) * rc + 16.0 * w + 64.0) + K * 160.0;
+  return (size_t)(N * (vec + grid + mg) + fit) + (1 << 20);
+}
+
+using Clock = std::chrono::steady_clock;
+
+enum ReqState { kQueued = 0, kNeedData, kReady, kRunning, kRetired, kFinished, kFailed };
+
+struct Request {
+  int64_t id = 0;
+  iim_problem_desc desc;
+  double t_submit = 0, t_done = 0;
+  int state = kQueued;
+  iim_problem* prob = nullptr;
+  cudaStream_t stream = nullptr;
+  size_t bytes = 0;
+  size_t known_bytes = 0;        // exact size once the request has been created
+  int slot = -1;
+  iim_solve_info info;
+  std::vector<double> x;
+  iim_status error = IIM_OK;
+};
+
+struct Server {
+  iim_options opt;
+  size_t budget = 0, in_use = 0, peak = 0;
+  int max_slots = 0, ticks_per_run = 1;
+  iim_engine* engine = nullptr;
+  cudaStream_t stream = nullptr;
+  std::vector<cudaStream_t> free_streams;
+  std::map<int64_t, Request*> reqs;
+  std::deque<Request*> queue;
+  std::vector<Request*> slot_req;
+  std::vector<int> done_buf;
+  int64_t next_id = 1;
+  bool run_in_flight = false;
+  int resident = 0;
+  int64_t runs = 0;
+  Clock::time_point t0;
+  double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+};
+
+}  // namespace iim
+
+using namespace iim;
+
+struct iim_problem {
+  Problem P;
+};
+struct iim_server {
+  Server S;
+};
+
+static void free_problem(Server& S, Request* r) {
+  if (r->prob) {
+    iim_problem_destroy(r->prob);
+    r->prob = nullptr;
+    S.in_use -= r->bytes;
+  }
+  if (r->stream) S.free_streams.push_back(r->stream);
+  r->stream = nullptr;
+}
+
+extern "C" {
+
+iim_status iim_server_create(const iim_options* opt, size_t hbm_budget, int max_slots, int ticks_per_run,
+                             iim_server** out) {
+  if (!opt || !out || max_slots < 1 || ticks_per_run < 1 || hbm_budget == 0) return IIM_ERR_INVALID_ARG;
+  *out = nullptr;
+  iim_server* H = new iim_server();
+  Server& S = H->S;
+  S.opt = *opt;
+  S.budget = hbm_budget;
+  S.max_slots = max_slots;
+  S.ticks_per_run = ticks_per_run;
+  S.t0 = Clock::now();
+  if (cudaStreamCreateWithFlags(&S.stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete H;
+    return IIM_ERR_CUDA;
+  }
+  iim_status st = iim_engine_create(opt, max_slots, S.stream, &S.engine);
+  if (st != IIM_OK) {
+    cudaStreamDestroy(S.stream);
+    delete H;
+    return st;
+  }
+  S.slot_req.assign(max_slots, nullptr);
+  S.done_buf.assign(max_slots, 0);
+  *out = H;
+  return IIM_OK;
+}
+
+void iim_server_destroy(iim_server* H) {
+  if (!H) return;
+  Server& S = H->S;
+  if (S.stream) cudaStreamSynchronize(S.stream);
+  for (auto& kv : S.reqs) {
+    Request* r = kv.second;
+    if (r->slot >= 0) iim_engine_release(S.engine, r->slot, nullptr, nullptr);
+    free_problem(S, r);
+    delete r;
+  }
+  iim_engine_destroy(S.engine);
+  for (cudaStream_t s : S.free_streams) cudaStreamDestroy(s);
+  cudaStreamDestroy(S.stream);
+  delete H;
+}
+
+iim_status iim_server_submit(iim_server* H, const iim_problem_desc* desc, int64_t* id) {
+  if (!H || !desc || !id) return IIM_ERR_INVALID_ARG;
+  Server& S = H->S;
+  if (estimate_bytes(*desc, S.opt) > S.budget) {
+    set_error("server: the request alone exceeds the memory budget");
+    return IIM_ERR_BUDGET;
+  }
+  Request* r = new Request();
+  r->id = S.next_id++;
+  r->desc = *desc;
+  r->t_submit = S.now();
+  std::memset(&r->info, 0, sizeof(r->info));
+  S.reqs[r->id] = r;
+  S.queue.push_back(r);
+  *id = r->id;
+  return IIM_OK;
+}
+
+iim_status iim_server_step(iim_server* H, int64_t* need_data, int cap_need, int* n_need, int64_t* finished,
+                           int cap_fin, int* n_fin) {
+  if (!H) return IIM_ERR_INVALID_ARG;
+  Server& S = H->S;
+  int nn = 0, nf = 0;
+  std::vector<Request*> retired;
+  // 1. the last run: release the slots that finished
+  if (S.run_in_flight) {
+    int nd = 0;
+    iim_status st = iim_engine_poll(S.engine, 0, nullptr, S.done_buf.data(), &nd, nullptr);
+    if (st == IIM_OK) {
+      S.run_in_flight = false;
+      for (int k = 0; k < nd; ++k) {
+        Request* r = S.slot_req[S.done_buf[k]];
+        if (!r) continue;
+        iim_engine_release(S.engine, r->slot, nullptr, &r->info);
+        S.slot_req[r->slot] = nullptr;
+        r->slot = -1;
+        r->state = kRetired;
+        --S.resident;
+        retired.push_back(r);
+      }
+    } else if (st != IIM_ERR_TIMEOUT) {
+      return st;
+    }
+  }
+  // 2. join the requests whose data are set, and launch the next run
+  if (!S.run_in_flight) {
+    for (auto& kv : S.reqs) {
+      Request* r = kv.second;
+      if (r->state != kReady) continue;
+      int slot = -1;
+      iim_status st = iim_engine_admit(S.engine, r->prob, nullptr, &slot);
+      if (st == IIM_ERR_CAPACITY) break;
+      if (st != IIM_OK) {
+        r->state = kFailed;
+        r->error = st;
+        r->t_done = S.now();
+        free_problem(S, r);
+        if (finished && nf < cap_fin) finished[nf++] = r->id;
+        continue;
+      }
+      r->slot = slot;
+      r->state = kRunning;
+      S.slot_req[slot] = r;
+      ++S.resident;
+    }
+    if (S.resident > 0) {
+      iim_status st = iim_engine_run(S.engine, S.ticks_per_run);
+      if (st != IIM_OK) return st;
+      S.run_in_flight = true;
+      ++S.runs;
+    }
+  }
+  // 3. solutions of the retired requests to the host (beside the new run), then free
+  for (Request* r : retired) {
+    Problem& P = r->prob->P;
+    r->x.resize((size_t)P.g.N);
+    cudaMemcpyAsync(r->x.data(), P.x, sizeof(double) * P.g.N, cudaMemcpyDeviceToHost, P.stream);
+    cudaStreamSynchronize(P.stream);
+    r->t_done = S.now();
+    r->state = r->info.status == IIM_OK ? kFinished : kFailed;
+    r->error = (iim_status)r->info.status;
+    free_problem(S, r);
+    if (finished && nf < cap_fin) finished[nf++] = r->id;
+  }
+  // 4. admission by budget, in submission order: create and set up (on the request's stream)
+  while (!S.queue.empty()) {
+    Request* r = S.queue.front();
+    const size_t need = r->known_bytes ? r->known_bytes : estimate_bytes(r->desc, S.opt);
+    if (S.in_use + need > S.budget) break;
+    S.queue.pop_front();
+    if (!S.free_streams.empty()) {
+      r->stream = S.free_streams.back();
+      S.free_streams.pop_back();
+    } else if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return IIM_ERR_CUDA;
+    }
+    iim_status st = iim_problem_create(&r->desc, &S.opt, r->stream, &r->prob);
+    if (st != IIM_OK) {
+      r->state = kFailed;
+      r->error = st;
+      r->prob = nullptr;
+      r->t_done = S.now();
+      free_problem(S, r);
+      if (finished && nf < cap_fin) finished[nf++] = r->id;
+      continue;
+    }
+    r->bytes = r->prob->P.bytes;
+    if (S.in_use + r->bytes > S.budget) {
+      // larger than estimated: give the memory back and wait for room
+      r->known_bytes = r->bytes;
+      iim_problem_destroy(r->prob);
+      r->prob = nullptr;
+      S.free_streams.push_back(r->stream);
+      r->stream = nullptr;
+      if (r->known_bytes > S.budget) {
+        r->state = kFailed;
+        r->error = IIM_ERR_BUDGET;
+        r->t_done = S.now();
+        if (finished && nf < cap_fin) finished[nf++] = r->id;
+        continue;
+      }
+      S.queue.push_front(r);
+      break;
+    }
+    S.in_use += r->bytes;
+    S.peak = S.in_use > S.peak ? S.in_use : S.peak;
+    r->state = kNeedData;
+    if (need_data && nn < cap_need) need_data[nn++] = r->id;
+  }
+  if (n_need) *n_need = nn;
+  if (n_fin) *n_fin = nf;
+  return IIM_OK;
+}
+
+iim_problem* iim_server_problem(iim_server* H, int64_t id) {
+  if (!H) return nullptr;
+  auto it = H->S.reqs.find(id);
+  if (it == H->S.reqs.end() || it->second->state != kNeedData) return nullptr;
+  return it->second->prob;
+}
+
+iim_status iim_server_data_ready(iim_server* H, int64_t id) {
+  if (!H) return IIM_ERR_INVALID_ARG;
+  auto it = H->S.reqs.find(id);
+  if (it == H->S.reqs.end() || it->second->state != kNeedData) return IIM_ERR_INVALID_ARG;
+  // the data copies and the right-hand side have read the caller's buffers once this returns
+  cudaStreamSynchronize(it->second->stream);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("server data: ") + cudaGetErrorString(e));
+    return IIM_ERR_CUDA;
+  }
+  it->second->state = kReady;
+  return IIM_OK;
+}
+
+iim_status iim_server_take(iim_server* H, int64_t id, double* x_host, iim_solve_info* info, double* latency_s) {
+  if (!H) return IIM_ERR_INVALID_ARG;
+  Server& S = H->S;
+  auto it = S.reqs.find(id);
+  if (it == S.reqs.end()) return IIM_ERR_INVALID_ARG;
+  Request* r = it->second;
+  if (r->state != kFinished && r->state != kFailed) return IIM_ERR_TIMEOUT;
+  if (x_host && !r->x.empty()) std::memcpy(x_host, r->x.data(), sizeof(double) * r->x.size());
+  if (info) *info = r->info;
+  if (latency_s) *latency_s = r->t_done - r->t_submit;
+  const iim_status st = r->state == kFinished ? IIM_OK : (r->error != IIM_OK ? r->error : IIM_ERR_NOT_CONVERGED);
+  S.reqs.erase(it);
+  delete r;
+  return st;
+}
+
+iim_status iim_server_stats(iim_server* H, size_t* bytes_in_use, size_t* peak_bytes, int* queued, int* resident,
+                            int64_t* runs) {
+  if (!H) return IIM_ERR_INVALID_ARG;
+  Server& S = H->S;
+  if (bytes_in_use) *bytes_in_use = S.in_use;
+  if (peak_bytes) *peak_bytes = S.peak;
+  if (queued) *queued = (int)S.queue.size();
+  if (resident) *resident = S.resident;
+  if (runs) *runs = S.runs;
+  return IIM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,75 @@
+"""The request loop: results are the same alone and in the mix.
+
+A stream of mixed 2D/3D requests goes through a server whose memory budget
+holds only a few of them at a time, so requests wait in the queue and enter the
+engine while others are still running.  Every request's solution must equal,
+bit for bit, the solution of the same request served alone (and of iim_solve),
+and the budget must never be exceeded.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.gpu_helpers import gpu_problem, need_gpu, set_gpu_data
+
+pytestmark = pytest.mark.gpu
+
+
+def _trace():
+    # small sizes of the serving mix: 2D 64..256, 3D ellipsoids at 64 (|kappa h| < 1/4 needs n >= 49)
+    return W.serving_trace(count=10, rate=1e9, seed=5, n2_lo=64, n2_hi=256, n3_lo=64, n3_hi=64, frac_3d=0.3)
+
+
+@pytest.fixture(scope="module")
+def env():
+    return need_gpu()
+
+
+def _serve(iim, specs, budget, ticks_per_run=3):
+    S = iim.Server(iim.default_options(), budget_bytes=budget, max_slots=8, ticks_per_run=ticks_per_run)
+    arrivals = [(0.0, iim.desc_from_spec(sp), sp) for sp in specs]
+    out, wall = iim.serve(S, arrivals, lambda view, sp: set_gpu_data(view, sp), realtime=False)
+    stats = S.stats()
+    S.close()
+    return [out[rid] for rid in sorted(out)], stats
+
+
+def test_served_results_equal_alone_and_single_solves(env):
+    torch, iim = env
+    specs = [sp for _, sp in _trace()]
+    assert any(sp.dim == 3 for sp in specs) and any(sp.dim == 2 for sp in specs)
+    # budget: the two largest requests at a time -> queueing and admission mid-run
+    sizes = []
+    for sp in specs:
+        P = gpu_problem(iim, sp)
+        sizes.append(P.device_bytes())
+        P.close()
+    budget = int(2.5 * max(sizes))
+    mixed, stats = _serve(iim, specs, budget)
+    assert stats["peak_bytes"] <= budget
+    assert stats["runs"] > 3
+    assert len(mixed) == len(specs)
+    for (x, info, lat, st, sp) in mixed:
+        assert st == 0 and info.converged and info.relres <= 1e-10, (sp.name, info.as_dict())
+        assert lat > 0
+    for (x, info, lat, st, sp) in mixed:
+        (alone,), _ = _serve(iim, [sp], 1 << 36)
+        assert np.array_equal(alone[0], x), sp.name
+        assert alone[1].iters == info.iters
+    # and the plain single solve of two of them
+    for (x, info, lat, st, sp) in mixed[:2]:
+        P = gpu_problem(iim, sp)
+        set_gpu_data(P, sp)
+        xs, si = P.solve()
+        assert np.array_equal(xs.cpu().numpy(), x) and si.iters == info.iters
+        P.close()
+
+
+def test_request_larger_than_budget_is_refused(env):
+    torch, iim = env
+    sp = W.circle_dirichlet_64(64)
+    S = iim.Server(iim.default_options(), budget_bytes=1 << 20, max_slots=2, ticks_per_run=2)
+    with pytest.raises(iim.IIMError) as e:
+        S.submit(iim.desc_from_spec(sp))
+    assert e.value.status == 7
+    S.close()

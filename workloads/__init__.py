@@ -134,31 +134,34 @@ def sin2x_sin3y_cosz() -> Manufactured:
 
 
 def sin_cos_2d(a1, b1, a2, b2) -> Manufactured:
-    """u = sin(a1 x + b1) cos(a2 y + b2) (batch / serving draws)."""
-    u = lambda X: np.sin(a1 * X[..., 0] + b1) * np.cos(a2 * X[..., 1] + b2)
-    g = lambda X: np.stack([a1 * np.cos(a1 * X[..., 0] + b1) * np.cos(a2 * X[..., 1] + b2),
-                            -a2 * np.sin(a1 * X[..., 0] + b1) * np.sin(a2 * X[..., 1] + b2)], axis=-1)
-    lap = lambda X: -(a1 * a1 + a2 * a2) * u(X)
+    """u = sin(a1 x + b1) cos(a2 y + b2) (batch / serving draws).
+
+    Every callable takes an optional array namespace ``xp`` (numpy by default, or
+    torch for device tensors)."""
+    u = lambda X, xp=np: xp.sin(a1 * X[..., 0] + b1) * xp.cos(a2 * X[..., 1] + b2)
+    g = lambda X, xp=np: xp.stack([a1 * xp.cos(a1 * X[..., 0] + b1) * xp.cos(a2 * X[..., 1] + b2),
+                                   -a2 * xp.sin(a1 * X[..., 0] + b1) * xp.sin(a2 * X[..., 1] + b2)], axis=-1)
+    lap = lambda X, xp=np: -(a1 * a1 + a2 * a2) * u(X, xp)
     return Manufactured(u, g, lap)
 
 
 def sin_sin_cos_3d(a, b) -> Manufactured:
-    """u = sin(a0 x + b0) sin(a1 y + b1) cos(a2 z + b2)."""
-    s = lambda X: (np.sin(a[0] * X[..., 0] + b[0]), np.sin(a[1] * X[..., 1] + b[1]),
-                   np.cos(a[2] * X[..., 2] + b[2]))
-    c = lambda X: (np.cos(a[0] * X[..., 0] + b[0]), np.cos(a[1] * X[..., 1] + b[1]),
-                   -np.sin(a[2] * X[..., 2] + b[2]))
+    """u = sin(a0 x + b0) sin(a1 y + b1) cos(a2 z + b2) (array namespace as in sin_cos_2d)."""
+    s = lambda X, xp: (xp.sin(a[0] * X[..., 0] + b[0]), xp.sin(a[1] * X[..., 1] + b[1]),
+                       xp.cos(a[2] * X[..., 2] + b[2]))
+    c = lambda X, xp: (xp.cos(a[0] * X[..., 0] + b[0]), xp.cos(a[1] * X[..., 1] + b[1]),
+                       -xp.sin(a[2] * X[..., 2] + b[2]))
 
-    def u(X):
-        p, q, r = s(X)
+    def u(X, xp=np):
+        p, q, r = s(X, xp)
         return p * q * r
 
-    def g(X):
-        p, q, r = s(X)
-        dp, dq, dr = c(X)
-        return np.stack([a[0] * dp * q * r, a[1] * p * dq * r, a[2] * p * q * dr], axis=-1)
+    def g(X, xp=np):
+        p, q, r = s(X, xp)
+        dp, dq, dr = c(X, xp)
+        return xp.stack([a[0] * dp * q * r, a[1] * p * dq * r, a[2] * p * q * dr], axis=-1)
 
-    lap = lambda X: -(a[0] ** 2 + a[1] ** 2 + a[2] ** 2) * u(X)
+    lap = lambda X, xp=np: -(a[0] ** 2 + a[1] ** 2 + a[2] ** 2) * u(X, xp)
     return Manufactured(u, g, lap)
 
 
@@ -233,6 +236,22 @@ def source_term(spec: ProblemSpec, X: np.ndarray, phase_plus: np.ndarray) -> np.
         fm = spec.beta_minus * s.lap_minus(X)
         return np.where(phase_plus, fp, fm)
     return np.where(phase_plus, fp, 0.0)
+
+
+def source_term_device(spec: ProblemSpec, phase_plus):
+    """source_term on the device for the boundary problems of the batch and serving
+    mixes: ``phase_plus`` is the problem's phase (torch uint8/bool, flat order); the
+    result is a flat float64 torch tensor on the same device.  Needs a solution
+    family written for an array namespace (sin_cos_2d, sin_sin_cos_3d)."""
+    import torch
+    n, d = spec.n, spec.dim
+    x = -1.0 + (torch.arange(n, dtype=torch.float64, device=phase_plus.device) + 0.5) * (2.0 / n)
+    X = torch.stack(torch.meshgrid(*([x] * d), indexing="ij"), dim=-1)
+    lap = spec.solution.lap_plus(X, torch)
+    flat = lap.permute(*reversed(range(d))).reshape(-1)          # order "F": x0 fastest
+    if spec.bc == INTERFACE:
+        raise ValueError("source_term_device covers boundary problems only")
+    return torch.where(phase_plus.bool(), spec.beta_plus * flat, torch.zeros((), dtype=flat.dtype, device=flat.device))
 
 
 def boundary_data(spec: ProblemSpec, xc: np.ndarray, normal: np.ndarray):
