@@ -44,6 +44,17 @@ def parse():
     ap.add_argument("--no-roofline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="host-driven FGMRES loop (for kernel-level profiling)")
     ap.add_argument("--batch", type=int, default=8, help="independent problems solved concurrently per step")
+    ap.add_argument("--solver", default="engine", choices=["engine", "pool"],
+                    help="engine: the batch advances in lock step through the batched engine; pool: one solve "
+                         "graph per problem on a pool of streams")
+    ap.add_argument("--workload", default="star1024", choices=["star1024", "batch512", "serve", "ellipsoid256"],
+                    help="star1024: the headline line; batch512: 512 mixed 2D problems through the batched "
+                         "engine; serve: a Poisson request stream through the request loop; ellipsoid256: "
+                         "the 256^3 Neumann ellipsoid in the FP32-MG, BF16-residual-MG and all-FP64 forms")
+    ap.add_argument("--count", type=int, default=0, help="problems (batch512) or requests (serve); 0 = default")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
+    ap.add_argument("--ticks-per-run", type=int, default=4, help="serve: engine ticks between admissions")
+    ap.add_argument("--slots", type=int, default=256, help="serve: problems resident at once at most")
     return ap.parse_args()
 
 
@@ -160,6 +171,266 @@ def star_angle(index, batch):
     return 2 * math.pi * index / (5 * max(batch, 1))
 
 
+def _boundary_inputs(P, spec):
+    """Device inputs of a boundary problem at its own control points: f on the device
+    (source_term_device), control-point and box data from the host."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    xc, nc = P.control_points()
+    g, _, _ = W.boundary_data(spec, xc.cpu().numpy(), nc.cpu().numpy())
+    f = W.source_term_device(spec, P.phase())
+    box = W.box_data(spec)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    return f, dev(g), (dev(box) if box.size else None)
+
+
+def run_batch(args):
+    """512 mixed 2D problems (50% interior Dirichlet, 50% exterior Neumann with a Dirichlet
+    box, (4,5)/(6,7), ellipses and 5-7 lobe stars, n in 64..512) per step: device set-up,
+    data and solve of all of them through the batched engine (persistent kernels, one
+    graph launch), next to the same problems through per-problem graphs on a stream pool."""
+    import torch
+
+    import paper_2503_22455_gb300 as iim
+    import workloads as W
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    _load_lib(iim)
+    count = args.count or 512
+    K, Wm = args.steps, args.warmup
+    specs = W.batch_specs(count, seed=2503 + 7919 * rank)
+    main = torch.cuda.current_stream()
+    pool = [torch.cuda.Stream() for _ in range(16)]
+    opts = iim.default_options(tol=1e-10, mg_precision=iim.MG_FP32)
+    probs = [iim.Problem(iim.desc_from_spec(sp), opts, pool[i % len(pool)]) for i, sp in enumerate(specs)]
+    inputs = []
+    for P, sp in zip(probs, specs):
+        with torch.cuda.stream(P.stream):
+            inputs.append(_boundary_inputs(P, sp))
+    torch.cuda.synchronize()
+    xs = [torch.zeros(P.N, dtype=torch.float64, device="cuda") for P in probs]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    E = iim.Engine(opts, max_slots=count, stream=main)
+    tuned = {"done": False}
+
+    def prepare():
+        start = torch.cuda.Event()
+        start.record(main)
+        for P, (f, g, box) in zip(probs, inputs):
+            P.stream.wait_event(start)
+            with torch.cuda.stream(P.stream):
+                P.setup()
+                P.set_data(f, g, None, None, box)
+
+    def step_engine():
+        l0 = iim.launch_count()
+        t0 = E.stats()[1]
+        prepare()
+        slots = [E.admit(P) for P in probs]
+        if not tuned["done"]:
+            tuned["ms"] = E.autotune(reps=3)
+            tuned["done"] = True
+        E.run()
+        E.poll(wait=True)
+        infos = [E.release(sl, x) for sl, x in zip(slots, xs)]
+        kpt, t1 = E.stats()
+        launches = iim.launch_count() - l0 - 1 + kpt * (t1 - t0)
+        return infos, t1 - t0, launches
+
+    def step_pool():
+        prepare()
+        for st in pool:
+            main.wait_stream(st)
+        infos, _ = iim.batch_solve(probs, xs)
+        return infos
+
+    for _ in range(Wm):
+        step_engine()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    iters, ticks, launches = [], [], 0
+    for k in range(K):
+        flush.zero_()
+        ev[k][0].record(main)
+        infos, nt, nl = step_engine()
+        ev[k][1].record(main)
+        ticks.append(nt)
+        launches += nl
+        for inf in infos:
+            if not inf.converged:
+                raise RuntimeError(f"batch step {k}: {inf.as_dict()}")
+            iters.append(inf.iters)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world)
+    value = whole_job_rate(count * K, world, total_ms)
+    # the same steps through per-problem graphs on a stream pool
+    step_pool()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pool_ms = []
+    for k in range(min(K, 3)):
+        flush.zero_()
+        a.record(main)
+        step_pool()
+        b.record(main)
+        torch.cuda.synchronize()
+        pool_ms.append(a.elapsed_time(b))
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": K, "warmup": Wm,
+        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "mg_dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batch{count}_mixed_2d", "problems_per_step": count, "n": "64..512 step 32",
+                   "mix": "50% interior Dirichlet / 50% exterior Neumann + Dirichlet box; 50% (4,5) / 50% (6,7); "
+                          "ellipses and 5-7 lobe stars", "tol": 1e-10, "l2": "flushed between steps",
+                   "step": "per problem: setup+data+solve; solves through the batched engine"},
+        "iters_mean": statistics.mean(iters), "ticks_per_step": statistics.mean(ticks),
+        "kernels_per_tick": E.stats()[0], "autotune_vcycle_ms": tuned.get("ms"), "tile_shapes": E.shapes(),
+        "stream_pool_solves_per_s": count * 1e3 / statistics.mean(pool_ms),
+        "gpu_launches": launches, "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    E.close()
+
+
+def run_serve(args):
+    """Poisson request stream (mean rate 200/s, 2000 requests, seed 22455): 2D n 128..1024
+    (stars), 3D n 64..192 (ellipsoids), interior Dirichlet / exterior Neumann, admitted by
+    a budget of 60% of free device memory into the request loop; p50/p99 latency from
+    submission to the solution on the host, and completed solves per second."""
+    import numpy as np
+    import torch
+
+    import paper_2503_22455_gb300 as iim
+    import workloads as W
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    _load_lib(iim)
+    count = args.count or 2000
+    trace = W.serving_trace(count=count, rate=args.rate, seed=22455 + rank)
+    opts = iim.default_options(tol=1e-10, mg_precision=iim.MG_FP32)
+    free, total = torch.cuda.mem_get_info()
+    budget = int(0.6 * free)
+
+    def set_data(view, spec):
+        f, g, box = _boundary_inputs(view, spec)
+        view.set_data(f, g, None, None, box)
+
+    # warm-up: a few requests through a separate server (library, kernels, allocator)
+    warm = iim.Server(opts, budget_bytes=budget, max_slots=args.slots, ticks_per_run=args.ticks_per_run)
+    iim.serve(warm, [(0.0, iim.desc_from_spec(sp), sp) for _, sp in trace[:8]], set_data, realtime=False)
+    warm.close()
+    S = iim.Server(opts, budget_bytes=budget, max_slots=args.slots, ticks_per_run=args.ticks_per_run)
+    clocks = Clocks(local)
+    clocks.start()
+    arrivals = [(t, iim.desc_from_spec(sp), sp) for t, sp in trace]
+    host = {}
+    out, wall = iim.serve(S, arrivals, set_data, realtime=True, timings=host)
+    clk = clocks.stop()
+    stats = S.stats()
+    lat = np.array([o[2] for o in out.values()])
+    ok = [o for o in out.values() if o[3] == 0 and o[1].converged]
+    err = [abs(o[3]) for o in out.values() if o[3] != 0]
+    res = {
+        "metric": "IIM serving: solves/s and p50/p99 latency (s), rel. resid 1e-10", "value": len(ok) / wall,
+        "unit": "solves/s", "n_gpus": world, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "mg_dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"serve_poisson_{count}", "rate_per_s": args.rate, "requests": count,
+                   "mix": "75% 2D stars n 128..1024, 25% 3D ellipsoids n 64..192; Dirichlet / Neumann; (4,5)/(6,7) 2D",
+                   "budget_bytes": budget, "slots": args.slots, "ticks_per_run": args.ticks_per_run, "tol": 1e-10},
+        "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+        "mean_latency_s": float(lat.mean()), "wall_s": wall, "completed": len(ok), "failed": len(err),
+        "offered_rate": count / trace[-1][0], "peak_bytes": stats["peak_bytes"], "engine_runs": stats["runs"],
+        "host_seconds": {"loop_step": host["step_s"], "client_set_data": host["set_data_s"], "take": host["take_s"],
+                         "server_copy_out": stats["host_copy_s"], "server_create_threads": stats["host_create_s"]},
+        "requests_2d": sum(1 for _, sp in trace if sp.dim == 2), "requests_3d": sum(1 for _, sp in trace if sp.dim == 3),
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(res))
+    S.close()
+
+
+def run_ellipsoid(args):
+    """The 256^3 exterior Neumann ellipsoid with a Dirichlet box, (4,5) scheme: per form
+    (FP32 multigrid, FP32 multigrid with BF16-rounded restricted residuals, all FP64),
+    steps of set-up + data + solve to 1e-10, with the error against the manufactured
+    solution.  L2 is flushed between steps (every vector is far larger than L2 anyway)."""
+    import numpy as np
+    import torch
+
+    import paper_2503_22455_gb300 as iim
+    import workloads as W
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    _load_lib(iim)
+    n = args.n if args.n != 1024 else 256
+    spec = W.ellipsoid_neumann_256(n)
+    main = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    X = None
+    forms = {}
+    for name, prec in (("fp32_mg", iim.MG_FP32), ("fp32_mg_bf16_residual", iim.MG_FP32_BF16R),
+                       ("fp64", iim.MG_FP64)):
+        P = iim.Problem(iim.desc_from_spec(spec), iim.default_options(tol=1e-10, mg_precision=prec), main)
+        xc, nc = P.control_points()
+        g, _, _ = W.boundary_data(spec, xc.cpu().numpy(), nc.cpu().numpy())
+        ph = P.phase().cpu().numpy().astype(bool)
+        if X is None:
+            X = W.node_coords(n, 3)
+            exact = W.to_flat(spec.solution.u_plus(X))
+        f = W.to_flat(W.source_term(spec, X, W.from_flat(ph, n, 3)))
+        box = W.box_data(spec)
+        dv = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+        fd, gd, bd = dv(f), dv(g), dv(box)
+        x = torch.zeros(P.N, dtype=torch.float64, device="cuda")
+        times, iters = [], []
+        for k in range(args.warmup + args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(main)
+            P.setup()
+            P.set_data(fd, gd, None, None, bd)
+            x.zero_()
+            _, info = P.solve(x)
+            b.record(main)
+            torch.cuda.synchronize()
+            if not info.converged:
+                raise RuntimeError(f"{name}: {info.as_dict()}")
+            if k >= args.warmup:
+                times.append(a.elapsed_time(b))
+                iters.append(info.iters)
+        err = float(np.max(np.abs(x.cpu().numpy() - exact)[ph]))
+        forms[name] = {"solves_per_s": 1e3 / statistics.mean(times), "ms_per_solve": statistics.mean(times),
+                       "iters": statistics.mean(iters), "max_err_vs_exact": err, "device_bytes": P.device_bytes()}
+        P.close()
+        del fd, gd, bd, x
+        torch.cuda.empty_cache()
+    out = {"metric": METRIC, "value": forms["fp32_mg"]["solves_per_s"], "unit": "solves/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": forms["fp32_mg"]["ms_per_solve"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "mg_dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": f"ellipsoid_neumann_{n}_o4", "n": n, "order": 4, "bc": "neumann (exterior)",
+                      "box": "dirichlet", "tol": 1e-10, "step": "setup+data+solve"},
+           "forms": forms}
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def _load_lib(iim):
+    import __graft_entry__ as ge
+    try:
+        iim.load()
+    except ImportError:
+        ge.build()
+        iim.load()
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -169,13 +440,8 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    import __graft_entry__ as ge
     import paper_2503_22455_gb300 as iim
-    try:
-        iim.load()
-    except ImportError:
-        ge.build()
-        iim.load()
+    _load_lib(iim)
     import workloads as W
 
     n, B = args.n, max(1, args.batch)
@@ -190,8 +456,12 @@ def run_ours(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2 (129 MB)
     torch.cuda.synchronize()
 
-    def step(s, problems, xvec):
-        """Set-up + data + solve of every problem of the batch, concurrently on their streams."""
+    engine = iim.Engine(opts, max_slots=B, stream=main) if args.solver == "engine" else None
+
+    def step(s, problems, xvec, use_engine=True):
+        """Set-up + data of every problem of the batch on its own stream, then the solves:
+        through the batched engine (one graph launch for the whole batch) or one solve
+        graph per problem on a stream pool."""
         l0 = iim.launch_count()
         start = torch.cuda.Event()
         start.record(main)
@@ -203,6 +473,14 @@ def run_ours(args):
                 f, j0, j1, box = inputs[i][0][s]
                 P.set_data(f, None, j0, j1, box)
                 xvec[i].zero_()
+        if engine is not None and use_engine:
+            t0 = engine.stats()[1]
+            slots = [engine.admit(P, x) for P, x in zip(problems, xvec)]
+            engine.run()
+            engine.poll(wait=True)
+            infos = [engine.release(sl, x) for sl, x in zip(slots, xvec)]
+            kpt, t1 = engine.stats()
+            return infos, iim.launch_count() - l0 - 1 + kpt * (t1 - t0)
         if len(problems) == 1 and args.no_graph:
             _, info = problems[0].solve(xvec[0])
             infos = [info]
@@ -275,7 +553,9 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "n": n, "order": 6, "bc": "interface", "box": "dirichlet",
                    "geometry": "star r=0.5+0.1 sin(5 theta), rotated per problem", "tol": 1e-10,
                    "krylov": "FGMRES(10), right", "preconditioner": "SW multigrid V(2,2), fp32",
-                   "batch": B, "l2": "flushed between steps", "step": "per problem: setup+data+solve"},
+                   "batch": B, "l2": "flushed between steps", "step": "per problem: setup+data+solve",
+                   "solver": "batched engine (lock-step ticks, one graph launch per step)" if engine is not None
+                   else "per-problem solve graphs on a stream pool"},
         "latency_ms_single_solve": statistics.median(lat),
         "iters_mean": statistics.mean(iters), "err_vs_exact": err_exact,
         "fp64_form": fp64_form,
@@ -301,13 +581,13 @@ def fp64_run(args, iim, torch, specs0, streams, inputs, step, flush, Wm, main):
     opts = iim.default_options(tol=1e-10, mg_precision=iim.MG_FP64)
     probs = [iim.Problem(iim.desc_from_spec(sp), opts, s) for sp, s in zip(specs0, streams)]
     xs = [torch.zeros(P.N, dtype=torch.float64, device="cuda") for P in probs]
-    step(0, probs, xs)
+    step(0, probs, xs, use_engine=False)            # the engine runs the FP32 multigrid only
     t, it = [], []
     for k in range(args.fp64_steps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(main)
-        infos, _ = step(Wm + k, probs, xs)
+        infos, _ = step(Wm + k, probs, xs, use_engine=False)
         b.record(main)
         torch.cuda.synchronize()
         t.append(a.elapsed_time(b))
@@ -434,5 +714,11 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "batch512":
+        run_batch(a)
+    elif a.workload == "serve":
+        run_serve(a)
+    elif a.workload == "ellipsoid256":
+        run_ellipsoid(a)
     else:
         run_ours(a)

@@ -62,7 +62,9 @@ typedef enum {
 enum { IIM_GEOM_CIRCLE = 0, IIM_GEOM_ELLIPSE = 1, IIM_GEOM_STAR = 2, IIM_GEOM_SPHERE = 3, IIM_GEOM_ELLIPSOID = 4 };
 enum { IIM_BC_DIRICHLET = 0, IIM_BC_NEUMANN = 1, IIM_BC_INTERFACE = 2 };
 enum { IIM_BOX_NONE = 0, IIM_BOX_DIRICHLET = 1 };
-enum { IIM_MG_FP32 = 0, IIM_MG_FP64 = 1 };
+/* Multigrid precision: FP32, FP64, or FP32 with every restricted residual (the
+ * right-hand side of the coarser level) rounded to BF16 where it is stored. */
+enum { IIM_MG_FP32 = 0, IIM_MG_FP64 = 1, IIM_MG_FP32_BF16R = 2 };
 
 /* Problem statement (paper Sec. 2.1-2.2).
  * geom_params by kind (phi = -g if plus_inside else g, g < 0 inside the body):
@@ -89,7 +91,7 @@ typedef struct {
   int restart;           /* FGMRES restart m (Sec. 4.1: 10), 1..16 */
   int max_iter;          /* total FGMRES iterations */
   int nu1, nu2;          /* pre/post red-black Gauss-Seidel sweeps */
-  int mg_precision;      /* IIM_MG_FP32 or IIM_MG_FP64 */
+  int mg_precision;      /* IIM_MG_FP32, IIM_MG_FP64 or IIM_MG_FP32_BF16R */
   int use_graph;         /* 1: the solve runs as one CUDA graph with device-side control */
   int reorth;            /* 1: second Gram-Schmidt pass when |w| drops by more than 1/sqrt(2) */
 } iim_options;
@@ -221,7 +223,9 @@ typedef struct iim_engine iim_engine;
 
 /* Create an engine for up to max_slots problems solved with opt (tol, restart,
  * max_iter and reorth are taken per problem from the problem's own options;
- * nu1, nu2 and the FP32 multigrid are engine-wide: nu1, nu2 >= 2). */
+ * nu1, nu2 and the FP32 multigrid are engine-wide: nu1, nu2 >= 2).  With
+ * opt.use_graph = 0 a run enqueues the tick kernels one by one and reads the
+ * unfinished-slot count after every tick (same results; for kernel profiling). */
 iim_status iim_engine_create(const iim_options* opt, int max_slots, void* stream, iim_engine** out);
 void iim_engine_destroy(iim_engine* e);
 
@@ -269,8 +273,9 @@ iim_status iim_engine_autotune(iim_engine* e, int reps, double* best_ms);
  *
  * Requests are queued by iim_server_submit and admitted, in submission order,
  * while the device memory they will hold fits hbm_budget bytes.  An admitted
- * request's problem is created and set up on its own stream, beside the
- * engine's work; the caller then sets its data and marks it ready.  Ready
+ * request's problem is created and set up on its own stream by one of the
+ * server's creation threads, beside the engine's work; the caller then sets its
+ * data and marks it ready.  Ready
  * requests join the engine between runs of ticks_per_run ticks, and leave it
  * when their solve ends: their solution is copied to the host and their device
  * memory returned to the budget, so that queued requests can enter while
@@ -280,9 +285,10 @@ iim_status iim_engine_autotune(iim_engine* e, int reps, double* best_ms);
  * ---------------------------------------------------------------------- */
 typedef struct iim_server iim_server;
 
-/* opt as for iim_engine_create; max_slots problems on the device at once. */
+/* opt as for iim_engine_create; max_slots problems on the device at once;
+ * create_threads host threads create and set up admitted requests (1..64). */
 iim_status iim_server_create(const iim_options* opt, size_t hbm_budget, int max_slots, int ticks_per_run,
-                             iim_server** out);
+                             int create_threads, iim_server** out);
 /* Frees every request still held (running solves are cancelled). */
 void iim_server_destroy(iim_server* s);
 
@@ -310,10 +316,12 @@ iim_status iim_server_data_ready(iim_server* s, int64_t id);
  * it.  Returns the request's final status; IIM_ERR_TIMEOUT while it is not finished. */
 iim_status iim_server_take(iim_server* s, int64_t id, double* x_host, iim_solve_info* info, double* latency_s);
 
-/* Device bytes held by requests now and at most so far, queued requests,
- * requests in the engine, engine runs launched. */
+/* Device bytes held (or reserved) by requests now and at most so far, queued
+ * requests, requests in the engine, engine runs launched, and host seconds
+ * (double[3], may be NULL): in iim_server_step, in copying solutions to the host,
+ * and in creating requests (summed over the creation threads). */
 iim_status iim_server_stats(iim_server* s, size_t* bytes_in_use, size_t* peak_bytes, int* queued, int* resident,
-                            int64_t* runs);
+                            int64_t* runs, double* host_seconds);
 
 /* Profiling: average device time (microseconds) of one launch of an internal
  * kernel, timed with CUDA events on the problem's stream over ``reps`` back to

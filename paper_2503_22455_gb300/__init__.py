@@ -19,7 +19,7 @@ STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "curvature", 3: "rank", 4: "s
                 6: "breakdown", 7: "budget", 8: "timeout", 9: "cuda", 10: "geometry", 11: "capacity"}
 GEOM = {"circle": 0, "ellipse": 1, "star": 2, "sphere": 3, "ellipsoid": 4}
 BC = {"dirichlet": 0, "neumann": 1, "interface": 2}
-MG_FP32, MG_FP64 = 0, 1
+MG_FP32, MG_FP64, MG_FP32_BF16R = 0, 1, 2
 
 
 class IIMError(RuntimeError):
@@ -89,7 +89,7 @@ SIGNATURES = {
     "iim_engine_get_shapes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "iim_engine_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "iim_server_create": (ctypes.c_int, [ctypes.POINTER(Options), ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
-                                         ctypes.POINTER(ctypes.c_void_p)]),
+                                         ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "iim_server_destroy": (None, [ctypes.c_void_p]),
     "iim_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Desc), ctypes.POINTER(ctypes.c_int64)]),
     "iim_server_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
@@ -101,7 +101,8 @@ SIGNATURES = {
                                        ctypes.POINTER(ctypes.c_double)]),
     "iim_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t),
                                         ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int),
-                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)]),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_double)]),
     "iim_last_error": (ctypes.c_char_p, []),
     "iim_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -429,12 +430,12 @@ class Server:
     """Request loop over an engine (see iim.h): submit, step, set data, take."""
 
     def __init__(self, options: Options | None = None, budget_bytes: int = 1 << 34, max_slots: int = 64,
-                 ticks_per_run: int = 4, cap: int = 4096):
+                 ticks_per_run: int = 4, cap: int = 4096, create_threads: int = 8):
         lib = load()
         self.options = options or default_options()
         h = ctypes.c_void_p()
         _check(lib.iim_server_create(ctypes.byref(self.options), ctypes.c_size_t(int(budget_bytes)), int(max_slots),
-                                     int(ticks_per_run), ctypes.byref(h)), "iim_server_create")
+                                     int(ticks_per_run), int(create_threads), ctypes.byref(h)), "iim_server_create")
         self.h = h
         self.cap = cap
         self._need = (ctypes.c_int64 * cap)()
@@ -485,19 +486,21 @@ class Server:
 
     def stats(self):
         b, pk, q, r, runs = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+        hs = (ctypes.c_double * 3)()
         _check(load().iim_server_stats(self.h, ctypes.byref(b), ctypes.byref(pk), ctypes.byref(q), ctypes.byref(r),
-                                       ctypes.byref(runs)))
+                                       ctypes.byref(runs), hs))
         return {"bytes_in_use": b.value, "peak_bytes": pk.value, "queued": q.value, "resident": r.value,
-                "runs": runs.value}
+                "runs": runs.value, "host_step_s": hs[0], "host_copy_s": hs[1], "host_create_s": hs[2]}
 
 
-def serve(server: Server, arrivals, set_data, realtime=True, idle_sleep=0.0):
+def serve(server: Server, arrivals, set_data, realtime=True, idle_sleep=0.0, timings=None):
     """Drive a server through a stream of requests.
 
     arrivals: list of (arrival time in seconds from now, Desc, user object), sorted by time;
     set_data(problem_view, user) sets the data of a created request.  Returns
     {request id: (x, info, latency, status, user)} and the wall time.  With realtime=False
-    every request is submitted at once.
+    every request is submitted at once.  timings (a dict) receives the caller-side host
+    seconds spent in step, set_data and take.
     """
     import time
     t0 = time.perf_counter()
@@ -505,6 +508,7 @@ def serve(server: Server, arrivals, set_data, realtime=True, idle_sleep=0.0):
     k = 0
     users, out = {}, {}
     outstanding = 0
+    t_step = t_data = t_take = 0.0
     while k < len(pending) or outstanding:
         now = time.perf_counter() - t0
         while k < len(pending) and (not realtime or pending[k][0] <= now):
@@ -513,14 +517,23 @@ def serve(server: Server, arrivals, set_data, realtime=True, idle_sleep=0.0):
             users[rid] = user
             outstanding += 1
             k += 1
+        a = time.perf_counter()
         need, fin = server.step()
+        b = time.perf_counter()
         for rid in need:
             set_data(server.problem(rid), users[rid])
             server.data_ready(rid)
+        c = time.perf_counter()
         for rid in fin:
             x, info, lat, st = server.take(rid)
             out[rid] = (x, info, lat, st, users.pop(rid))
             outstanding -= 1
+        d = time.perf_counter()
+        t_step += b - a
+        t_data += c - b
+        t_take += d - c
         if idle_sleep and not need and not fin:
             time.sleep(idle_sleep)
+    if timings is not None:
+        timings.update({"step_s": t_step, "set_data_s": t_data, "take_s": t_take})
     return out, time.perf_counter() - t0

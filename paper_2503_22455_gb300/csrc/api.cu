@@ -162,7 +162,8 @@ static iim_status validate(const iim_problem_desc* d, const iim_options* o) {
   if (!(d->beta_plus > 0) || (d->bc == IIM_BC_INTERFACE && !(d->beta_minus > 0))) return IIM_ERR_INVALID_ARG;
   if (o->restart < 1 || o->restart > kMaxRestart || o->max_iter < 1 || !(o->tol > 0)) return IIM_ERR_INVALID_ARG;
   if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 + o->nu2 < 1) return IIM_ERR_INVALID_ARG;
-  if (o->mg_precision != IIM_MG_FP32 && o->mg_precision != IIM_MG_FP64) return IIM_ERR_INVALID_ARG;
+  if (o->mg_precision != IIM_MG_FP32 && o->mg_precision != IIM_MG_FP64 && o->mg_precision != IIM_MG_FP32_BF16R)
+    return IIM_ERR_INVALID_ARG;
   return IIM_OK;
 }
 
@@ -352,6 +353,7 @@ iim_status iim_problem_create(const iim_problem_desc* desc, const iim_options* o
     L.g.n = sizes[l];
     L.g.N = (int64_t)sizes[l] * sizes[l] * (d == 3 ? sizes[l] : 1);
     L.g.h = 2.0 / sizes[l];
+    L.f_bf16 = l > 0 && opt->mg_precision == IIM_MG_FP32_BF16R;
     if (l == 0) L.phase = P.phase;
     else IIM_ALLOC(L.phase, uint8_t, L.g.N);
     IIM_ALLOC(L.aux, int32_t, L.g.N);

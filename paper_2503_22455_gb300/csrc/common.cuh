@@ -1,6 +1,7 @@
 // Shared definitions of the GB300 IIM solver library (device code and host glue).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -202,6 +203,12 @@ __device__ inline float warp_sumf(float v) {
 }
 
 __device__ inline void set_status(int* st, int code) { atomicCAS(st, 0, code); }
+
+// a restricted residual as stored: unchanged, or rounded to BF16 (round to nearest even)
+__device__ inline float store_residual(float v, int bf16) {
+  return bf16 ? __bfloat162float(__float2bfloat16_rn(v)) : v;
+}
+__device__ inline double store_residual(double v, int) { return v; }
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 

@@ -56,7 +56,8 @@ struct Engine {
   iim_options opt;
   cudaStream_t stream = nullptr;
   SlotDev* d_slots = nullptr;
-  int* d_lists = nullptr;
+  int* d_lists = nullptr;               // the host's lists
+  int* d_dyn = nullptr;                 // this tick's lists (plan kernel)
   int* d_ctl = nullptr;                 // [0] unfinished slots, [1] tick budget, [2 + slot] done flags
   int* h_ctl = nullptr;                 // pinned mirror
   cudaEvent_t ev_run = nullptr;
@@ -82,7 +83,8 @@ struct Engine {
 static EngArgs eng_args(const Engine& E) {
   EngArgs A;
   A.slots = E.d_slots;
-  A.lists = E.d_lists;
+  A.lists = E.d_dyn;
+  A.stat = E.d_lists;
   A.cap = E.cap;
   return A;
 }
@@ -247,12 +249,12 @@ static void enqueue_mg(Engine& E, cudaStream_t s) {
   for (const EngMgStep& st : E.mg_steps) eng_launch_mg(A, st, kEngTailSmem, s);
 }
 
-static void enqueue_tick(Engine& E, cudaGraphConditionalHandle h, cudaStream_t s) {
+static void enqueue_tick(Engine& E, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
   const EngArgs A = eng_args(E);
-  eng_launch_krylov_head(A, s);
+  eng_launch_krylov_head(A, E.d_dyn, s);
   enqueue_mg(E, s);
   eng_launch_apply(A, E.present, s);
-  eng_launch_krylov_tail(A, E.d_ctl, h, 1, s);
+  eng_launch_krylov_tail(A, E.d_ctl, h, use_cond, s);
 }
 
 static iim_status capture(Engine& E) {
@@ -281,7 +283,7 @@ static iim_status capture(Engine& E) {
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
   const int64_t l0 = iim_launch_count();
-  enqueue_tick(E, h, s);
+  enqueue_tick(E, h, 1, s);
   E.kernels_per_tick = iim_launch_count() - l0;
   cudaStreamEndCapture(s, &body);
   cudaError_t e = cudaGetLastError();
@@ -309,8 +311,13 @@ static iim_status sync_lists(Engine& E) {
     for (int k = 0; k < kListCount; ++k) E.present[k] = E.present[k] || E.list_items[k] > 0;
   cudaMemcpyAsync(E.d_lists, E.h_lists.data(), sizeof(int) * E.h_lists.size(), cudaMemcpyHostToDevice, E.stream);
   E.dirty = false;
-  if (need) return capture(E);
-  return IIM_OK;
+  if (!need) return IIM_OK;
+  if (!E.opt.use_graph) {
+    build_mg_program(E, E.present);
+    E.captured = true;
+    return IIM_OK;
+  }
+  return capture(E);
 }
 
 static iim_status eng_cuda(const char* what) {
@@ -328,20 +335,11 @@ static void destroy_engine(Engine* E) {
   if (E->graph) cudaGraphDestroy(E->graph);
   if (E->d_slots) cudaFree(E->d_slots);
   if (E->d_lists) cudaFree(E->d_lists);
+  if (E->d_dyn) cudaFree(E->d_dyn);
   if (E->d_ctl) cudaFree(E->d_ctl);
   if (E->h_ctl) cudaFreeHost(E->h_ctl);
   if (E->ev_run) cudaEventDestroy(E->ev_run);
   delete E;
-}
-
-__global__ void k_eng_force_iter(EngArgs A) {
-  const int* L = A.list(kListAll);
-  const int count = L[0];
-  const int* slot = L + 2 + A.cap;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
-    A.slots[slot[e]].role = kRoleIter;
-    A.slots[slot[e]].j = 0;
-  }
 }
 
 }  // namespace iim
@@ -360,7 +358,7 @@ extern "C" {
 iim_status iim_engine_create(const iim_options* opt, int max_slots, void* stream, iim_engine** out) {
   if (!opt || !out || max_slots < 1 || max_slots > (1 << 16)) return IIM_ERR_INVALID_ARG;
   *out = nullptr;
-  if (opt->mg_precision != IIM_MG_FP32 || opt->nu1 < 2 || opt->nu2 < 2) {
+  if ((opt->mg_precision != IIM_MG_FP32 && opt->mg_precision != IIM_MG_FP32_BF16R) || opt->nu1 < 2 || opt->nu2 < 2) {
     set_error("the engine runs the FP32 multigrid with nu1, nu2 >= 2");
     return IIM_ERR_INVALID_ARG;
   }
@@ -375,6 +373,7 @@ iim_status iim_engine_create(const iim_options* opt, int max_slots, void* stream
   default_shapes(*E);
   bool ok = cudaMalloc(&E->d_slots, sizeof(SlotDev) * (size_t)max_slots) == cudaSuccess &&
             cudaMalloc(&E->d_lists, sizeof(int) * eng_list_ints(max_slots)) == cudaSuccess &&
+            cudaMalloc(&E->d_dyn, sizeof(int) * eng_dyn_ints(max_slots)) == cudaSuccess &&
             cudaMalloc(&E->d_ctl, sizeof(int) * (2 + (size_t)max_slots)) == cudaSuccess &&
             cudaMallocHost(&E->h_ctl, sizeof(int) * (2 + (size_t)max_slots)) == cudaSuccess &&
             cudaEventCreateWithFlags(&E->ev_run, cudaEventDisableTiming) == cudaSuccess;
@@ -385,6 +384,7 @@ iim_status iim_engine_create(const iim_options* opt, int max_slots, void* stream
     return IIM_ERR_BUDGET;
   }
   cudaMemsetAsync(E->d_lists, 0, sizeof(int) * eng_list_ints(max_slots), E->stream);
+  cudaMemsetAsync(E->d_dyn, 0, sizeof(int) * eng_dyn_ints(max_slots), E->stream);
   cudaMemsetAsync(E->d_ctl, 0, sizeof(int) * (2 + (size_t)max_slots), E->stream);
   std::memset(E->h_ctl, 0, sizeof(int) * (2 + (size_t)max_slots));
   iim_status st = eng_cuda("engine create");
@@ -406,7 +406,7 @@ iim_status iim_engine_admit(iim_engine* H, iim_problem* p, const double* x0_dev,
   if (!H || !p) return IIM_ERR_INVALID_ARG;
   Engine& E = *H->E;
   Problem& P = p->P;
-  if (P.opt.mg_precision != IIM_MG_FP32 || P.opt.nu1 != E.opt.nu1 || P.opt.nu2 != E.opt.nu2) {
+  if (P.opt.mg_precision == IIM_MG_FP64 || P.opt.nu1 != E.opt.nu1 || P.opt.nu2 != E.opt.nu2) {
     set_error("engine: the problem's multigrid options differ from the engine's");
     return IIM_ERR_INVALID_ARG;
   }
@@ -468,8 +468,20 @@ iim_status iim_engine_run(iim_engine* H, int max_ticks) {
   iim_status st = sync_lists(E);
   if (st != IIM_OK) return st;
   cudaMemcpyAsync(E.d_ctl + 1, &max_ticks, sizeof(int), cudaMemcpyHostToDevice, E.stream);
-  cudaGraphLaunch(E.exec, E.stream);
-  note_launch();
+  if (E.opt.use_graph) {
+    cudaGraphLaunch(E.exec, E.stream);
+    note_launch();
+  } else {
+    // the same ticks as separate launches (for kernel-level profiling): the host reads
+    // the unfinished-slot count after every tick
+    for (int t = 0; t < max_ticks; ++t) {
+      enqueue_tick(E, 0, 0, E.stream);
+      cudaMemcpyAsync(E.h_ctl, E.d_ctl, sizeof(int) * 2, cudaMemcpyDeviceToHost, E.stream);
+      cudaStreamSynchronize(E.stream);
+      if (E.h_ctl[0] == 0) break;
+    }
+    E.kernels_per_tick = 0;
+  }
   cudaMemcpyAsync(E.h_ctl, E.d_ctl, sizeof(int) * (2 + (size_t)E.cap), cudaMemcpyDeviceToHost, E.stream);
   cudaEventRecord(E.ev_run, E.stream);
   E.run_pending = true;
@@ -608,7 +620,7 @@ iim_status iim_engine_autotune(iim_engine* H, int reps, double* best_ms) {
     for (int k = 0; k < kListCount; ++k) pres[k] = E.list_items[k] > 0;
     build_mg_program(E, pres);
     cudaMemcpyAsync(E.d_lists, E.h_lists.data(), sizeof(int) * E.h_lists.size(), cudaMemcpyHostToDevice, E.stream);
-    IIM_LAUNCH(k_eng_force_iter, 4, 256, 0, E.stream, A);
+    eng_launch_plan(A, E.d_dyn, 1, E.stream);          // every slot ITER at j = 0
     enqueue_mg(E, E.stream);
     cudaEventRecord(a, E.stream);
     for (int r = 0; r < reps; ++r) enqueue_mg(E, E.stream);

@@ -30,6 +30,7 @@ struct Level {
   void* u = nullptr;              // level vectors, float or double by mg precision
   void* u2 = nullptr;             // second u buffer: fused kernels read one and write the other
   void* f = nullptr;
+  int f_bf16 = 0;                 // the level's right-hand side (a restricted residual) is rounded to BF16
 };
 
 // device-side FGMRES state of one solve (krylov.cu)

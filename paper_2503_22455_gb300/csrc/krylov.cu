@@ -556,21 +556,85 @@ void krylov_read_info(Problem& P, iim_solve_info* info) {
 
 
 // ---------------------------------------------------------------------------- batched engine
-// Roles for this tick from each slot's FGMRES state (one thread per slot)
-__global__ void k_eng_plan(EngArgs A) {
-  const int* L = A.list(kListAll);
+// Plan of a tick (one block per per-tick list).  The role of a slot follows from its
+// FGMRES state (or is ITER for every slot with force_iter, for the autotuner); block 0
+// writes roles and iteration indices into the slot descriptors, and block k copies
+// static list k keeping the slots whose role uses it, with their item prefix sums.
+__global__ void __launch_bounds__(1024) k_eng_plan(EngArgs A, int* dyn, int force_iter) {
+  const int b = blockIdx.x;
+  auto role_of = [&](int si) -> int {
+    if (force_iter) return kRoleIter;
+    const SolverScalars* S = A.slots[si].sc;
+    return S->done ? kRoleIdle : (S->active ? kRoleIter : kRoleRestart);
+  };
+  if (b == 0) {
+    const int* L = A.slist(kListAll);
+    const int count = L[0];
+    const int* slot = L + 2 + A.cap;
+    for (int e = threadIdx.x; e < count; e += blockDim.x) {
+      SlotDev& sd = A.slots[slot[e]];
+      sd.role = role_of(slot[e]);
+      sd.j = force_iter ? 0 : sd.sc->k;
+    }
+  }
+  const int mask = eng_list_mask(b);
+  const int* L = A.slist(eng_list_source(b));
   const int count = L[0];
+  const int* pre = L + 1;
   const int* slot = L + 2 + A.cap;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
-    SlotDev& s = A.slots[slot[e]];
-    const SolverScalars* S = s.sc;
-    s.role = S->done ? kRoleIdle : (S->active ? kRoleIter : kRoleRestart);
-    s.j = S->k;
+  int* D = dyn + (size_t)b * (2 * A.cap + 2);
+  int* dpre = D + 1;
+  int* dslot = D + 2 + A.cap;
+  __shared__ int wn[32], wi[32];
+  __shared__ int base_n, base_i, tot_n, tot_i;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (threadIdx.x == 0) { base_n = 0; base_i = 0; }
+  __syncthreads();
+  for (int c0 = 0; c0 < count; c0 += blockDim.x) {
+    const int e = c0 + threadIdx.x;
+    int keep = 0, items = 0, si = 0;
+    if (e < count) {
+      si = slot[e];
+      items = pre[e + 1] - pre[e];
+      keep = ((mask >> role_of(si)) & 1) && items > 0;
+      if (!keep) items = 0;
+    }
+    // block-wide exclusive scans of keep and items
+    int in = keep, ii = items;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int yn = __shfl_up_sync(0xffffffffu, in, o), yi = __shfl_up_sync(0xffffffffu, ii, o);
+      if (lane >= o) { in += yn; ii += yi; }
+    }
+    if (lane == 31) { wn[wid] = in; wi[wid] = ii; }
+    __syncthreads();
+    if (wid == 0) {
+      int vn = lane < nw ? wn[lane] : 0, vi = lane < nw ? wi[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int yn = __shfl_up_sync(0xffffffffu, vn, o), yi = __shfl_up_sync(0xffffffffu, vi, o);
+        if (lane >= o) { vn += yn; vi += yi; }
+      }
+      if (lane < nw) { wn[lane] = vn; wi[lane] = vi; }
+      if (lane == nw - 1) { tot_n = vn; tot_i = vi; }
+    }
+    __syncthreads();
+    const int xn = in - keep + (wid > 0 ? wn[wid - 1] : 0);
+    const int xi = ii - items + (wid > 0 ? wi[wid - 1] : 0);
+    if (keep) {
+      dslot[base_n + xn] = si;
+      dpre[base_n + xn] = base_i + xi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) { base_n += tot_n; base_i += tot_i; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    D[0] = base_n;
+    dpre[base_n] = base_i;
   }
 }
 
 __global__ void __launch_bounds__(32) k_eng_solve_y(EngArgs A) {
-  eng_for_items(A, kListAll, [&](int si, int) {
+  eng_for_items(A, kDynAllRestart, [&](int si, int) {
     const SlotDev& s = A.slots[si];
     if (s.role != kRoleRestart || threadIdx.x != 0) return;
     solve_y_body(s.sc);
@@ -602,7 +666,7 @@ __global__ void __launch_bounds__(kRedThreads) k_eng_update(EngArgs A, int secon
 }
 
 __global__ void __launch_bounds__(32) k_eng_arnoldi(EngArgs A) {
-  eng_for_items(A, kListAll, [&](int si, int) {
+  eng_for_items(A, kDynAllIter, [&](int si, int) {
     const SlotDev& s = A.slots[si];
     if (s.role != kRoleIter || threadIdx.x != 0) return;
     arnoldi_body(s.sc, s.j, s.status);
@@ -610,7 +674,7 @@ __global__ void __launch_bounds__(32) k_eng_arnoldi(EngArgs A) {
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_eng_residual(EngArgs A) {
-  eng_for_items(A, kListRed, [&](int si, int item) {
+  eng_for_items(A, kDynRedRestart, [&](int si, int item) {
     const SlotDev& s = A.slots[si];
     if (s.role != kRoleRestart) return;
     residual_body(s.b, s.tmp, s.V, s.g.N, s.partial, s.counter, s.sc, s.sc->first, s.status, item, s.red_blocks);
@@ -621,7 +685,7 @@ __global__ void __launch_bounds__(kRedThreads) k_eng_residual(EngArgs A) {
 // and the loop condition of the run graph (one block)
 __global__ void __launch_bounds__(256) k_eng_tick_end(EngArgs A, int* live, int* done_flags, int* ticks_left,
                                                       cudaGraphConditionalHandle h, int use_cond) {
-  const int* L = A.list(kListAll);
+  const int* L = A.slist(kListAll);
   const int count = L[0];
   const int* slot = L + 2 + A.cap;
   int mine = 0;
@@ -645,8 +709,12 @@ __global__ void __launch_bounds__(256) k_eng_tick_end(EngArgs A, int* live, int*
   }
 }
 
-void eng_launch_krylov_head(const EngArgs& A, cudaStream_t s) {
-  IIM_LAUNCH(k_eng_plan, 4, 256, 0, s, A);
+void eng_launch_plan(const EngArgs& A, int* dyn, int force_iter, cudaStream_t s) {
+  IIM_LAUNCH(k_eng_plan, kDynCount, 1024, 0, s, A, dyn, force_iter);
+}
+
+void eng_launch_krylov_head(const EngArgs& A, int* dyn, cudaStream_t s) {
+  eng_launch_plan(A, dyn, 0, s);
   IIM_LAUNCH(k_eng_solve_y, eng_grid((const void*)k_eng_solve_y, 32, 0), 32, 0, s, A);
   IIM_LAUNCH(k_eng_xupdate, eng_grid((const void*)k_eng_xupdate, 256, 0), 256, 0, s, A);
 }

@@ -26,6 +26,7 @@ struct LevelK {
   const T* tab;
   T* u;
   T* f;
+  int f_bf16;     // f holds restricted residuals rounded to BF16
 };
 
 template <typename T>
@@ -42,6 +43,7 @@ static LevelK<T> levk(const Level& L) {
   k.tab = (const T*)(sizeof(T) == 8 ? (const void*)L.tab64 : (const void*)L.tab32);
   k.u = (T*)L.u;
   k.f = (T*)L.f;
+  k.f_bf16 = L.f_bf16;
   return k;
 }
 
@@ -211,7 +213,7 @@ __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx
       const int64_t ci = (int64_t)gcy * C.n + gcx;
       const int b = (kH + 2 * cy) * SX + kH + 2 * cx;
       const T acc = (fs[b] + fs[b + 1]) + (fs[b + SX] + fs[b + SX + 1]);
-      C.f[ci] = C.aux[ci] == -2 ? (T)0 : acc * (T)0.25;
+      C.f[ci] = C.aux[ci] == -2 ? (T)0 : store_residual(acc * (T)0.25, C.f_bf16);
     }
   }
   for (int e = threadIdx.x; e < TX * TY; e += blockDim.x) {
@@ -383,7 +385,7 @@ __device__ __forceinline__ void vcycle_tail_body(const TailParams<T>& P, const d
         }
         acc *= wch;
       }
-      sf[P.off[k + 1] + I] = acc;
+      sf[P.off[k + 1] + I] = store_residual(acc, C.f_bf16);
     }
     __syncthreads();
   }

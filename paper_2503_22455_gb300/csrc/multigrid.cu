@@ -91,7 +91,8 @@ __global__ void __launch_bounds__(256) k_smooth(LevelView<T> L, T ih2, T dreg, T
 template <typename T>
 __device__ __forceinline__ void resid_restrict_body(const LevelView<T>& F, T ih2, T dreg, const T* __restrict__ u,
                                                     const T* __restrict__ f, const GridView& gc,
-                                                    const int32_t* __restrict__ aux_c, T* __restrict__ fc, int64_t I) {
+                                                    const int32_t* __restrict__ aux_c, T* __restrict__ fc, int64_t I,
+                                                    int f_bf16) {
   if (I >= gc.N) return;
   if (aux_c[I] == -2) { fc[I] = (T)0; return; }
   int mc[3];
@@ -107,14 +108,15 @@ __device__ __forceinline__ void resid_restrict_body(const LevelView<T>& F, T ih2
     T r = f[i] - (diag_of(F, dreg, a) * u[i] + offdiag_sum(F, ih2, i, m, a, u));
     acc += r;
   }
-  fc[I] = acc / (T)nch;
+  fc[I] = store_residual(acc / (T)nch, f_bf16);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_resid_restrict(LevelView<T> F, T ih2, T dreg, const T* __restrict__ u,
                                                         const T* __restrict__ f, GridView gc,
-                                                        const int32_t* __restrict__ aux_c, T* __restrict__ fc) {
-  resid_restrict_body<T>(F, ih2, dreg, u, f, gc, aux_c, fc, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+                                                        const int32_t* __restrict__ aux_c, T* __restrict__ fc,
+                                                        int f_bf16) {
+  resid_restrict_body<T>(F, ih2, dreg, u, f, gc, aux_c, fc, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, f_bf16);
 }
 
 // u_fine += P e_coarse at fine unknowns
@@ -536,7 +538,8 @@ static void vcycle(Problem& P, size_t l, size_t lt, cudaStream_t s) {
   for (int it = 0; it < P.opt.nu1; ++it)
     for (int c = 0; c < 2; ++c) IIM_LAUNCH(k_smooth<T>, ceil_div(ncol, Tn), Tn, 0, s, V, K.ih2, K.dreg, u, f, c);
   Level& C = P.lv[l + 1];
-  IIM_LAUNCH(k_resid_restrict<T>, ceil_div(C.g.N, Tn), Tn, 0, s, V, K.ih2, K.dreg, u, f, C.g, C.aux, (T*)C.f);
+  IIM_LAUNCH(k_resid_restrict<T>, ceil_div(C.g.N, Tn), Tn, 0, s, V, K.ih2, K.dreg, u, f, C.g, C.aux, (T*)C.f,
+             C.f_bf16);
   vcycle<T>(P, l + 1, lt, s);
   IIM_LAUNCH(k_prolong<T>, ceil_div(L.g.N, Tn), Tn, 0, s, L.g, L.aux, u, C.g, C.aux, (const T*)C.u,
              P.desc.bc == IIM_BC_NEUMANN);
@@ -687,7 +690,7 @@ __global__ void __launch_bounds__(256) k_eng_mg3d(EngArgs A, int list, int d, in
       smooth_body<float>(V, K.ih2, K.dreg, K.u, K.f, colour, i);
     } else if (KIND == 3) {
       const LevelView<float> C = eng_view(s, d + 1);
-      resid_restrict_body<float>(V, K.ih2, K.dreg, K.u, K.f, C.g, C.aux, s.lev[d + 1].f, i);
+      resid_restrict_body<float>(V, K.ih2, K.dreg, K.u, K.f, C.g, C.aux, s.lev[d + 1].f, i, s.lev[d + 1].f_bf16);
     } else if (KIND == 4) {
       const LevelView<float> C = eng_view(s, d + 1);
       prolong_body<float>(V.g, K.aux, K.u, C.g, C.aux, s.lev[d + 1].u, s.neumann, i);

@@ -1,13 +1,17 @@
 // Request loop over the batched engine: requests are admitted while the device
-// memory they need fits a budget, set up on their own streams while the engine
-// runs the resident solves, join the engine at the next run (continuous batching
-// at the granularity of a run of a few ticks) and leave it when their solve ends.
-// Latency is measured from submission to the moment the solution is on the host.
+// memory they need fits a budget, created and set up by a pool of host threads on
+// their own streams while the engine runs the resident solves, join the engine at
+// the next run (continuous batching at the granularity of a run of a few ticks) and
+// leave it when their solve ends.  Latency is measured from submission to the
+// moment the solution is on the host.
 #include <chrono>
+#include <condition_variable>
 #include <cstring>
 #include <deque>
 #include <map>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "kernels.cuh"
@@ -32,7 +36,7 @@ static size_t estimate_bytes(const iim_problem_desc& d, const iim_options& o) {
 
 using Clock = std::chrono::steady_clock;
 
-enum ReqState { kQueued = 0, kNeedData, kReady, kRunning, kRetired, kFinished, kFailed };
+enum ReqState { kQueued = 0, kCreating, kNeedData, kReady, kRunning, kRetired, kFinished, kFailed };
 
 struct Request {
   int64_t id = 0;
@@ -42,7 +46,9 @@ struct Request {
   iim_problem* prob = nullptr;
   cudaStream_t stream = nullptr;
   size_t bytes = 0;
+  size_t reserved = 0;           // budget held while it is being created
   size_t known_bytes = 0;        // exact size once the request has been created
+  iim_status create_status = IIM_OK;
   int slot = -1;
   iim_solve_info info;
   std::vector<double> x;
@@ -64,9 +70,42 @@ struct Server {
   bool run_in_flight = false;
   int resident = 0;
   int64_t runs = 0;
+  double t_step = 0, t_copy = 0, t_create = 0;   // host seconds: step calls, result copies, creation (workers)
   Clock::time_point t0;
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+  // creation workers
+  std::vector<std::thread> workers;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Request*> to_create;
+  std::vector<Request*> created;
+  bool stop = false;
+  int device = 0;
+  int creating = 0;
 };
+
+// worker: create the problem (allocation, set-up on the request's own stream, and the
+// host waits inside create) away from the loop's thread
+static void create_worker(Server* S) {
+  cudaSetDevice(S->device);
+  for (;;) {
+    Request* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv.wait(lk, [&] { return S->stop || !S->to_create.empty(); });
+      if (S->stop && S->to_create.empty()) return;
+      r = S->to_create.front();
+      S->to_create.pop_front();
+    }
+    const auto t = Clock::now();
+    r->create_status = iim_problem_create(&r->desc, &S->opt, r->stream, &r->prob);
+    if (r->create_status != IIM_OK) r->prob = nullptr;
+    const double dt = std::chrono::duration<double>(Clock::now() - t).count();
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->t_create += dt;
+    S->created.push_back(r);
+  }
+}
 
 }  // namespace iim
 
@@ -92,8 +131,10 @@ static void free_problem(Server& S, Request* r) {
 extern "C" {
 
 iim_status iim_server_create(const iim_options* opt, size_t hbm_budget, int max_slots, int ticks_per_run,
-                             iim_server** out) {
-  if (!opt || !out || max_slots < 1 || ticks_per_run < 1 || hbm_budget == 0) return IIM_ERR_INVALID_ARG;
+                             int create_threads, iim_server** out) {
+  if (!opt || !out || max_slots < 1 || ticks_per_run < 1 || hbm_budget == 0 || create_threads < 1 ||
+      create_threads > 64)
+    return IIM_ERR_INVALID_ARG;
   *out = nullptr;
   iim_server* H = new iim_server();
   Server& S = H->S;
@@ -115,6 +156,8 @@ iim_status iim_server_create(const iim_options* opt, size_t hbm_budget, int max_
   }
   S.slot_req.assign(max_slots, nullptr);
   S.done_buf.assign(max_slots, 0);
+  cudaGetDevice(&S.device);
+  for (int k = 0; k < create_threads; ++k) S.workers.emplace_back(create_worker, &S);
   *out = H;
   return IIM_OK;
 }
@@ -122,6 +165,13 @@ iim_status iim_server_create(const iim_options* opt, size_t hbm_budget, int max_
 void iim_server_destroy(iim_server* H) {
   if (!H) return;
   Server& S = H->S;
+  {
+    std::lock_guard<std::mutex> lk(S.mu);
+    S.stop = true;
+    S.to_create.clear();
+  }
+  S.cv.notify_all();
+  for (auto& t : S.workers) t.join();
   if (S.stream) cudaStreamSynchronize(S.stream);
   for (auto& kv : S.reqs) {
     Request* r = kv.second;
@@ -157,6 +207,7 @@ iim_status iim_server_step(iim_server* H, int64_t* need_data, int cap_need, int*
                            int cap_fin, int* n_fin) {
   if (!H) return IIM_ERR_INVALID_ARG;
   Server& S = H->S;
+  const auto t_enter = Clock::now();
   int nn = 0, nf = 0;
   std::vector<Request*> retired;
   // 1. the last run: release the slots that finished
@@ -210,16 +261,61 @@ iim_status iim_server_step(iim_server* H, int64_t* need_data, int cap_need, int*
   // 3. solutions of the retired requests to the host (beside the new run), then free
   for (Request* r : retired) {
     Problem& P = r->prob->P;
+    const auto tc = Clock::now();
     r->x.resize((size_t)P.g.N);
     cudaMemcpyAsync(r->x.data(), P.x, sizeof(double) * P.g.N, cudaMemcpyDeviceToHost, P.stream);
     cudaStreamSynchronize(P.stream);
+    S.t_copy += std::chrono::duration<double>(Clock::now() - tc).count();
     r->t_done = S.now();
     r->state = r->info.status == IIM_OK ? kFinished : kFailed;
     r->error = (iim_status)r->info.status;
     free_problem(S, r);
     if (finished && nf < cap_fin) finished[nf++] = r->id;
   }
-  // 4. admission by budget, in submission order: create and set up (on the request's stream)
+  // 4. requests the workers have created: check the exact size against the budget
+  std::vector<Request*> got;
+  {
+    std::lock_guard<std::mutex> lk(S.mu);
+    got.swap(S.created);
+  }
+  for (Request* r : got) {
+    --S.creating;
+    S.in_use -= r->reserved;
+    r->reserved = 0;
+    if (r->create_status != IIM_OK) {
+      r->state = kFailed;
+      r->error = r->create_status;
+      r->t_done = S.now();
+      S.free_streams.push_back(r->stream);
+      r->stream = nullptr;
+      if (finished && nf < cap_fin) finished[nf++] = r->id;
+      continue;
+    }
+    r->bytes = r->prob->P.bytes;
+    if (S.in_use + r->bytes > S.budget) {
+      // larger than estimated and no room now: give the memory back and wait for room
+      r->known_bytes = r->bytes;
+      iim_problem_destroy(r->prob);
+      r->prob = nullptr;
+      S.free_streams.push_back(r->stream);
+      r->stream = nullptr;
+      if (r->known_bytes > S.budget) {
+        r->state = kFailed;
+        r->error = IIM_ERR_BUDGET;
+        r->t_done = S.now();
+        if (finished && nf < cap_fin) finished[nf++] = r->id;
+      } else {
+        r->state = kQueued;
+        S.queue.push_front(r);
+      }
+      continue;
+    }
+    S.in_use += r->bytes;
+    S.peak = S.in_use > S.peak ? S.in_use : S.peak;
+    r->state = kNeedData;
+    if (need_data && nn < cap_need) need_data[nn++] = r->id;
+  }
+  // 5. admission by budget, in submission order: reserve and hand to the workers
   while (!S.queue.empty()) {
     Request* r = S.queue.front();
     const size_t need = r->known_bytes ? r->known_bytes : estimate_bytes(r->desc, S.opt);
@@ -232,39 +328,18 @@ iim_status iim_server_step(iim_server* H, int64_t* need_data, int cap_need, int*
       cudaGetLastError();
       return IIM_ERR_CUDA;
     }
-    iim_status st = iim_problem_create(&r->desc, &S.opt, r->stream, &r->prob);
-    if (st != IIM_OK) {
-      r->state = kFailed;
-      r->error = st;
-      r->prob = nullptr;
-      r->t_done = S.now();
-      free_problem(S, r);
-      if (finished && nf < cap_fin) finished[nf++] = r->id;
-      continue;
+    r->reserved = need;
+    S.in_use += need;
+    r->state = kCreating;
+    ++S.creating;
+    {
+      std::lock_guard<std::mutex> lk(S.mu);
+      S.to_create.push_back(r);
     }
-    r->bytes = r->prob->P.bytes;
-    if (S.in_use + r->bytes > S.budget) {
-      // larger than estimated: give the memory back and wait for room
-      r->known_bytes = r->bytes;
-      iim_problem_destroy(r->prob);
-      r->prob = nullptr;
-      S.free_streams.push_back(r->stream);
-      r->stream = nullptr;
-      if (r->known_bytes > S.budget) {
-        r->state = kFailed;
-        r->error = IIM_ERR_BUDGET;
-        r->t_done = S.now();
-        if (finished && nf < cap_fin) finished[nf++] = r->id;
-        continue;
-      }
-      S.queue.push_front(r);
-      break;
-    }
-    S.in_use += r->bytes;
-    S.peak = S.in_use > S.peak ? S.in_use : S.peak;
-    r->state = kNeedData;
-    if (need_data && nn < cap_need) need_data[nn++] = r->id;
+    S.cv.notify_one();
   }
+  S.peak = S.in_use > S.peak ? S.in_use : S.peak;
+  S.t_step += std::chrono::duration<double>(Clock::now() - t_enter).count();
   if (n_need) *n_need = nn;
   if (n_fin) *n_fin = nf;
   return IIM_OK;
@@ -309,9 +384,15 @@ iim_status iim_server_take(iim_server* H, int64_t id, double* x_host, iim_solve_
 }
 
 iim_status iim_server_stats(iim_server* H, size_t* bytes_in_use, size_t* peak_bytes, int* queued, int* resident,
-                            int64_t* runs) {
+                            int64_t* runs, double* host_seconds) {
   if (!H) return IIM_ERR_INVALID_ARG;
   Server& S = H->S;
+  if (host_seconds) {
+    std::lock_guard<std::mutex> lk(S.mu);
+    host_seconds[0] = S.t_step;
+    host_seconds[1] = S.t_copy;
+    host_seconds[2] = S.t_create;
+  }
   if (bytes_in_use) *bytes_in_use = S.in_use;
   if (peak_bytes) *peak_bytes = S.peak;
   if (queued) *queued = (int)S.queue.size();

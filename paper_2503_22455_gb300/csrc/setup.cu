@@ -741,6 +741,7 @@ __device__ inline void q8_sum(double& v) {
   v += __shfl_xor_sync(0xffffffffu, v, 1, 8);
 }
 
+template <int M>
 __global__ void __launch_bounds__(32) k_fit_quad(FitParams P, QuadFitSmem Lq, int* __restrict__ overflow) {
   extern __shared__ double smq[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -748,7 +749,7 @@ __global__ void __launch_bounds__(32) k_fit_quad(FitParams P, QuadFitSmem Lq, in
   const int f = (blockIdx.x * (blockDim.x >> 5) + wib) * 4 + qf;
   const GridView& g = P.g;
   const int nfit_here = P.interface_ ? 2 * (*P.K) : *P.K;
-  const int M = P.M, LDQ = Lq.LDQ(), n = g.n;
+  const int LDQ = Lq.LDQ(), n = g.n;
   double* base = smq + (size_t)(wib * 4 + qf) * Lq.doubles();
   double* V = base;                      // [M][LDQ]
   double* S = V + (size_t)M * LDQ;       // [4][LDQ]
@@ -862,7 +863,9 @@ __global__ void __launch_bounds__(32) k_fit_quad(FitParams P, QuadFitSmem Lq, in
     V[(size_t)col * LDQ + row] = row == 0 ? (col == 0 ? 1.0 : 0.0) : monomial(P.monos + 3 * col, rel + 2 * (row - 1), 2);
   }
   __syncwarp();
-  // Householder QR, rows over the 8 lanes
+  // Householder QR, rows over the 8 lanes.  The trailing columns go four at a time
+  // (four independent products and reductions in flight); each product and update is
+  // the same sequence of operations as one column at a time.
   for (int k = 0; k < M; ++k) {
     double* vk = V + (size_t)k * LDQ;
     double s = 0;
@@ -879,13 +882,26 @@ __global__ void __launch_bounds__(32) k_fit_quad(FitParams P, QuadFitSmem Lq, in
     }
     __syncwarp();
     const double bk = m > 0 ? beta[k] : 0.0;
-    for (int j = k + 1; j < M; ++j) {
-      double* vj = V + (size_t)j * LDQ;
-      double d = 0;
-      for (int r = k + ql; r < m; r += 8) d = fma(vk[r], vj[r], d);
-      q8_sum(d);
-      d *= bk;
-      for (int r = k + ql; r < m; r += 8) vj[r] = fma(-d, vk[r], vj[r]);
+    for (int c0 = k + 1; c0 < M; c0 += 4) {
+      double d[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int r = k + ql; r < m; r += 8) {
+        const double v = vk[r];
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (c0 + t < M) d[t] = fma(v, V[(size_t)(c0 + t) * LDQ + r], d[t]);
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (c0 + t < M) {
+          q8_sum(d[t]);
+          d[t] *= bk;
+        }
+      for (int r = k + ql; r < m; r += 8) {
+        const double v = vk[r];
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (c0 + t < M) V[(size_t)(c0 + t) * LDQ + r] = fma(-d[t], v, V[(size_t)(c0 + t) * LDQ + r]);
+      }
     }
     __syncwarp();
   }
@@ -899,11 +915,10 @@ __global__ void __launch_bounds__(32) k_fit_quad(FitParams P, QuadFitSmem Lq, in
   }
   for (int k = ql; k < M; k += 8) ialpha[k] = active ? 1.0 / alpha[k] : 0.0;
   __syncwarp();
-  // stencil rows, one target after the other (rows over the 8 lanes)
+  // stencil rows of all targets together (rows over the 8 lanes)
   const int nt = (P.bc == IIM_BC_DIRICHLET) ? P.w : P.w + 1;
   for (int t = 0; t < nt; ++t) {
     double* y = Y + t * M;
-    double* srow = S + t * LDQ;
     if (t < P.w) {
       int mlo0 = (int)(lo % n), mlo1 = (int)(lo / n);
       int gm0 = mlo0, gm1 = mlo1;
@@ -917,25 +932,49 @@ __global__ void __launch_bounds__(32) k_fit_quad(FitParams P, QuadFitSmem Lq, in
         y[col] = (e[0] + e[1] == 1) ? (e[0] ? nrm[0] : nrm[1]) * ih : 0.0;
       }
     }
-    __syncwarp();
-    for (int i = 0; i < M; ++i) {                  // y = R^-T c
-      double part = 0;
-      for (int l = ql; l < i; l += 8) part = fma(V[(size_t)i * LDQ + l], y[l], part);
-      q8_sum(part);
-      if (ql == 0) y[i] = (y[i] - part) * ialpha[i];
-      __syncwarp();
+  }
+  __syncwarp();
+  for (int i = 0; i < M; ++i) {                    // y_t = R^-T c_t
+    double part[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int l = ql; l < i; l += 8) {
+      const double rv = V[(size_t)i * LDQ + l];
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (t < nt) part[t] = fma(rv, Y[t * M + l], part[t]);
     }
-    for (int r = ql; r < m; r += 8) srow[r] = r < M ? y[r] : 0.0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (t < nt) q8_sum(part[t]);
+    if (ql == 0)
+      for (int t = 0; t < nt; ++t) Y[t * M + i] = (Y[t * M + i] - part[t]) * ialpha[i];
     __syncwarp();
-    for (int k = M - 1; k >= 0; --k) {              // s = Q [y; 0]
-      const double* vk = V + (size_t)k * LDQ;
-      double d = 0;
-      for (int r = k + ql; r < m; r += 8) d = fma(vk[r], srow[r], d);
-      q8_sum(d);
-      d *= (m > 0 ? beta[k] : 0.0);
-      for (int r = k + ql; r < m; r += 8) srow[r] = fma(-d, vk[r], srow[r]);
-      __syncwarp();
+  }
+  for (int t = 0; t < nt; ++t)
+    for (int r = ql; r < m; r += 8) S[t * LDQ + r] = r < M ? Y[t * M + r] : 0.0;
+  __syncwarp();
+  for (int k = M - 1; k >= 0; --k) {                // s_t = Q [y_t; 0]
+    const double* vk = V + (size_t)k * LDQ;
+    double d[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int r = k + ql; r < m; r += 8) {
+      const double v = vk[r];
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (t < nt) d[t] = fma(v, S[t * LDQ + r], d[t]);
     }
+    const double bk = m > 0 ? beta[k] : 0.0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (t < nt) {
+        q8_sum(d[t]);
+        d[t] *= bk;
+      }
+    for (int r = k + ql; r < m; r += 8) {
+      const double v = vk[r];
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (t < nt) S[t * LDQ + r] = fma(-d[t], v, S[t * LDQ + r]);
+    }
+    __syncwarp();
   }
   if (!active) return;
   const int rows = P.w + 1;
@@ -1163,16 +1202,18 @@ iim_status setup_fits(Problem& P) {
     return IIM_ERR_CUDA;
   }
   cudaMemsetAsync(P.fit_overflow, 0, sizeof(int) * P.nfit_cap, P.stream);
-  if (P.g.dim == 2 && P.M <= 28) {
+  if (P.g.dim == 2 && (P.M == 15 || P.M == 28)) {
     QuadFitSmem Q;
     Q.M = P.M;
     const size_t smq = sizeof(double) * Q.doubles() * 4;       // one warp, four fits
-    e = cudaFuncSetAttribute(k_fit_quad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
+    const void* kq = P.M == 15 ? (const void*)k_fit_quad<15> : (const void*)k_fit_quad<28>;
+    e = cudaFuncSetAttribute(kq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
     if (e != cudaSuccess) {
       set_error(std::string("least-squares kernel shared memory: ") + cudaGetErrorString(e));
       return IIM_ERR_CUDA;
     }
-    IIM_LAUNCH(k_fit_quad, ceil_div(P.nfit_cap, 4), 32, smq, P.stream, F, Q, P.fit_overflow);
+    if (P.M == 15) IIM_LAUNCH(k_fit_quad<15>, ceil_div(P.nfit_cap, 4), 32, smq, P.stream, F, Q, P.fit_overflow);
+    else IIM_LAUNCH(k_fit_quad<28>, ceil_div(P.nfit_cap, 4), 32, smq, P.stream, F, Q, P.fit_overflow);
   } else {
     IIM_LAUNCH(k_fit_warp, ceil_div(P.nfit_cap, wpb), 32 * wpb, smw, P.stream, F, W, P.fit_overflow);
   }

@@ -365,9 +365,14 @@ def batch_specs(count: int = 512, seed: int = 2503, n_lo: int = 64, n_hi: int = 
         interior = rng.random() < 0.5
         c = rng.uniform(-0.15, 0.15, size=2)
         if rng.random() < 0.5:
-            a0, a1 = rng.uniform(0.3, 0.55, size=2)
-            if not interior:
-                a0, a1 = 0.6 * a0, 0.6 * a1 + 0.1
+            # semi-axes redrawn until the ellipse's largest curvature a_max / a_min^2 keeps
+            # |kappa h| < 0.2 (the bound is 1/4, Eq. 3)
+            while True:
+                a0, a1 = rng.uniform(0.3, 0.55, size=2)
+                if not interior:
+                    a0, a1 = 0.6 * a0, 0.6 * a1 + 0.1
+                if max(a0, a1) / min(a0, a1) ** 2 * (2.0 / n) < 0.2:
+                    break
             geom = Geometry(ELLIPSE, (c[0], c[1], a0, a1, rng.uniform(0, np.pi)), plus_inside=interior)
         else:
             m = int(rng.choice([5, 6, 7]))
