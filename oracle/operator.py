@@ -33,7 +33,7 @@ import numpy as np
 from workloads import DIRICHLET, NEUMANN, INTERFACE, BOX_DIRICHLET
 from .fits import build_fit
 from .geometry import Crossings, LevelSet, phase_plus
-from .stencils import second_derivative
+from .stencils import first_derivative, second_derivative
 
 
 class GeometryError(Exception):
@@ -269,6 +269,85 @@ class IIMOperator:
         beta = np.where(plus_flat, self.beta_p, self.beta_m)
         out = beta * acc_flat / (self.h * self.h)
         out[~self.unknown.ravel(order="F")] = 0.0
+        return out
+
+    def boundary_values(self, u_flat, data):
+        """The boundary quantity the data do not prescribe, at every control point
+        (canonical order), Sec. 2.4: Dirichlet -> n . grad u(x_c) from the fit's derivative
+        row (Eq. 5 without beta; n out of Omega+); Neumann -> u(x_c) from Eq. 6."""
+        if self.bc == INTERFACE:
+            raise ValueError("boundary values are defined for boundary problems")
+        K = self.cross.count
+        out = np.zeros(K)
+        if self.bc == DIRICHLET:
+            g = data["g"]
+            for c in range(K):
+                f = self.fits[(c, True)] if (c, True) in self.fits else self._fit(c, True)
+                out[c] = f.deriv[0] * g[c] + f.deriv[1:] @ u_flat[f.nodes]
+            return out
+        for c in range(K):
+            if (c, True) not in self.fits:
+                self._fit(c, True)
+        cv = self.control_values(u_flat, data, True)
+        for c in range(K):
+            out[c] = cv[(c, True)]
+        return out
+
+    def gradient(self, u_flat, data=None, include_data=True):
+        """grad u at every unknown node, shape (d, n^d): the centred first-derivative
+        stencil of the scheme's order applied to the same extension of u as the Laplacian
+        (u in phase, the fit's ghost values past the first crossing, box ghosts), Sec. 2.4."""
+        n, d, w = self.n, self.d, self.w
+        data = data or {}
+        b = first_derivative(self.order)
+        u = u_flat.reshape((n,) * d, order="F")
+        G = self.ghost_values(u_flat, data, include_data)
+        out = np.zeros((d, n ** d))
+        for ax in range(d):
+            acc = np.zeros((n,) * d)
+            for s in (-1, 1):
+                for j in range(1, w + 1):
+                    shifted = np.zeros((n,) * d)
+                    same = np.zeros((n,) * d, dtype=bool)
+                    src = [slice(None)] * d
+                    dst = [slice(None)] * d
+                    if s > 0:
+                        src[ax], dst[ax] = slice(j, n), slice(0, n - j)
+                    else:
+                        src[ax], dst[ax] = slice(0, n - j), slice(j, n)
+                    shifted[tuple(dst)] = u[tuple(src)]
+                    same[tuple(dst)] = self.plus[tuple(src)] == self.plus[tuple(dst)]
+                    acc += b[w + j * s] * np.where(same, shifted, 0.0)
+            acc_flat = acc.ravel(order="F")
+            for (node, rax, s, jstar, c, side) in self.iim_rec:
+                if rax != ax:
+                    continue
+                m = self._unflat(node)
+                for j in range(jstar, w + 1):
+                    p = m.copy()
+                    p[ax] += j * s
+                    if 0 <= p[ax] < n and self.plus[tuple(p)] == side:
+                        continue
+                    acc_flat[node] += b[w + j * s] * G[(c, side)][j - jstar]
+            if self.box_rec:
+                bd = data.get("box") if include_data else None
+                for (node, rax, s, jstar) in self.box_rec:
+                    if rax != ax:
+                        continue
+                    m = self._unflat(node)
+                    line_nodes = []
+                    for mm in range(2, self.q + 2):
+                        p = m.copy()
+                        p[ax] = n - mm if s > 0 else mm - 1
+                        line_nodes.append(self._flat(p))
+                    vals = u_flat[line_nodes]
+                    face = bd[self._box_index(m, ax, s)] if include_data else 0.0
+                    for j in range(jstar, w + 1):
+                        k = j - jstar + 1
+                        acc_flat[node] += b[w + j * s] * (self.box_w[k - 1, 0] * face + self.box_w[k - 1, 1:] @ vals)
+            acc_flat = acc_flat / self.h
+            acc_flat[~self.unknown.ravel(order="F")] = 0.0
+            out[ax] = acc_flat
         return out
 
     def apply_at(self, u_flat, nodes, data=None, include_data=False):

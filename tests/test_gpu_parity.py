@@ -105,3 +105,16 @@ def test_vcycle_fp32(env):
     O = OracleProblem(spec)
     v = np.random.default_rng(8).standard_normal(P.N)
     assert rel_err(P.precondition(dev(v)).cpu().numpy(), O.precondition(v)) < 1e-5
+
+
+@pytest.mark.parametrize("nu", [(3, 3), (1, 2)])
+@pytest.mark.parametrize("case", ["star_interface_6_128", "neumann_ext_6_80"])
+def test_vcycle_fp64_other_sweep_counts(env, case, nu):
+    """nu1 = nu2 = 2 runs two fused tile kernels per level; other sweep counts run the
+    separate kernels (3, 3: with the plain-sweep kernel; 1, 2: the generic path)."""
+    torch, iim = env
+    spec = CASES[case]()
+    P = gpu_problem(iim, spec, mg_precision=iim.MG_FP64, nu1=nu[0], nu2=nu[1])
+    O = OracleProblem(spec, nu1=nu[0], nu2=nu[1])
+    v = np.random.default_rng(9).standard_normal(P.N) * O.unk_flat
+    assert rel_err(P.precondition(dev(v)).cpu().numpy(), O.precondition(v)) < 1e-12
