@@ -22,7 +22,7 @@ from __future__ import annotations
 import numpy as np
 import scipy.linalg as sla
 
-from workloads import NEUMANN
+from workloads import BOX_NONE, NEUMANN
 from .sw import SWLevel
 
 
@@ -45,6 +45,16 @@ class Multigrid:
         c = self.levels[-1]
         self.c_unk = np.nonzero(c.unk_flat)[0]
         Ac = c.A[self.c_unk][:, self.c_unk].toarray()
+        # pure Neumann (no box): the coarse operator annihilates constants; the coarsest
+        # level solves the augmented system [A 1; 1^T 0] (Sec. 2.3 augmentation)
+        self.augmented = bc == NEUMANN and box_bc == BOX_NONE
+        if self.augmented and self.c_unk.size:
+            k = self.c_unk.size
+            Aa = np.zeros((k + 1, k + 1))
+            Aa[:k, :k] = Ac
+            Aa[:k, k] = 1.0
+            Aa[k, :k] = 1.0
+            Ac = Aa
         self.c_lu = sla.lu_factor(Ac) if self.c_unk.size else None
 
     # transfers -----------------------------------------------------------------
@@ -112,7 +122,10 @@ class Multigrid:
         c = self.levels[-1]
         u = np.zeros(c.n ** self.dim)
         if self.c_unk.size:
-            u[self.c_unk] = sla.lu_solve(self.c_lu, f[self.c_unk])
+            rhs = f[self.c_unk]
+            if self.augmented:
+                rhs = np.append(rhs, 0.0)
+            u[self.c_unk] = sla.lu_solve(self.c_lu, rhs)[:self.c_unk.size]
         return u
 
     def vcycle(self, f, lev=0):

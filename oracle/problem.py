@@ -51,7 +51,35 @@ class OracleProblem:
     def precondition(self, v):
         return self.mg.precondition(v, self.plus_flat)
 
-    def solve(self, f, data, tol=1e-13, restart=10, max_iter=1000):
+    @property
+    def singular(self):
+        """Pure Neumann problem (no outer box): L 1 = 0, solution defined up to a constant."""
+        return self.spec.bc == W.NEUMANN and self.spec.box_bc == W.BOX_NONE
+
+    def solve(self, f, data, tol=1e-13, restart=10, max_iter=1000, gamma=0.0):
+        """Solve L u = b.  Singular (pure Neumann) problems solve the augmented system of
+        Sec. 2.3, [L 1; 1^T 0][u; alpha] = [b; gamma] with 1 over the unknowns, by the same
+        FGMRES; the preconditioner is the V-cycle on u and the identity on alpha.
+        info["alpha"] is the shift that makes b + alpha 1 compatible."""
         b = self.op.rhs(f, data)
-        x, info = fgmres(self.op.apply, self.precondition, b, tol=tol, restart=restart, max_iter=max_iter)
-        return x, info, b
+        if not self.singular:
+            x, info = fgmres(self.op.apply, self.precondition, b, tol=tol, restart=restart, max_iter=max_iter)
+            return x, info, b
+        unk = self.unk_flat.astype(float)
+        N = b.size
+
+        def apply_aug(z):
+            out = np.empty(N + 1)
+            out[:N] = self.op.apply(z[:N]) + z[N] * unk
+            out[N] = unk @ z[:N]
+            return out
+
+        def precond_aug(v):
+            out = np.empty(N + 1)
+            out[:N] = self.precondition(v[:N])
+            out[N] = v[N]
+            return out
+
+        xa, info = fgmres(apply_aug, precond_aug, np.append(b, gamma), tol=tol, restart=restart, max_iter=max_iter)
+        info["alpha"] = xa[N]
+        return xa[:N], info, b
