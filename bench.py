@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
     ap.add_argument("--ticks-per-run", type=int, default=4, help="serve: engine ticks between admissions")
     ap.add_argument("--slots", type=int, default=256, help="serve: problems resident at once at most")
+    ap.add_argument("--engines", type=int, default=2,
+                    help="batched engines, each on its own stream with a share of the problems")
     return ap.parse_args()
 
 
@@ -203,7 +205,7 @@ def run_batch(args):
     specs = W.batch_specs(count, seed=2503 + 7919 * rank)
     main = torch.cuda.current_stream()
     pool = [torch.cuda.Stream() for _ in range(16)]
-    opts = iim.default_options(tol=1e-10, mg_precision=iim.MG_FP32)
+    opts = iim.default_options(tol=1e-10, mg_precision=iim.MG_FP32, use_graph=0 if args.no_graph else 1)
     probs = [iim.Problem(iim.desc_from_spec(sp), opts, pool[i % len(pool)]) for i, sp in enumerate(specs)]
     inputs = []
     for P, sp in zip(probs, specs):
@@ -212,7 +214,10 @@ def run_batch(args):
     torch.cuda.synchronize()
     xs = [torch.zeros(P.N, dtype=torch.float64, device="cuda") for P in probs]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    E = iim.Engine(opts, max_slots=count, stream=main)
+    ne = max(1, args.engines)
+    eng_streams = [main] + [torch.cuda.Stream() for _ in range(ne - 1)]
+    engines = [iim.Engine(opts, max_slots=(count + ne - 1) // ne, stream=st) for st in eng_streams]
+    E = engines[0]
     tuned = {"done": False}
 
     def prepare():
@@ -224,20 +229,37 @@ def run_batch(args):
                 P.setup()
                 P.set_data(f, g, None, None, box)
 
+    split = []
+
     def step_engine():
         l0 = iim.launch_count()
-        t0 = E.stats()[1]
+        t0 = [e.stats()[1] for e in engines]
         prepare()
-        slots = [E.admit(P) for P in probs]
+        for st in pool:
+            main.wait_stream(st)
+        mid = torch.cuda.Event(enable_timing=True)
+        mid.record(main)
+        for st in eng_streams[1:]:
+            st.wait_event(mid)
+        slots = [engines[i % ne].admit(P) for i, P in enumerate(probs)]
         if not tuned["done"]:
-            tuned["ms"] = E.autotune(reps=3)
+            tuned["ms"] = [e.autotune(reps=3) for e in engines]
             tuned["done"] = True
-        E.run()
-        E.poll(wait=True)
-        infos = [E.release(sl, x) for sl, x in zip(slots, xs)]
-        kpt, t1 = E.stats()
-        launches = iim.launch_count() - l0 - 1 + kpt * (t1 - t0)
-        return infos, t1 - t0, launches
+        for e in engines:
+            e.run()
+        for e in engines:
+            e.poll(wait=True)
+        infos = [engines[i % ne].release(sl, x) for i, (sl, x) in enumerate(zip(slots, xs))]
+        for st in eng_streams[1:]:
+            main.wait_stream(st)
+        launches = iim.launch_count() - l0 - ne
+        nt = 0
+        for e, a in zip(engines, t0):
+            kpt, t1 = e.stats()
+            launches += kpt * (t1 - a)
+            nt = max(nt, t1 - a)
+        split.append(mid)
+        return infos, nt, launches
 
     def step_pool():
         prepare()
@@ -253,6 +275,7 @@ def run_batch(args):
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     iters, ticks, launches = [], [], 0
+    split.clear()
     for k in range(K):
         flush.zero_()
         ev[k][0].record(main)
@@ -268,6 +291,7 @@ def run_batch(args):
     clk = clocks.stop()
     total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world)
     value = whole_job_rate(count * K, world, total_ms)
+    setup_ms = statistics.mean(ev[k][0].elapsed_time(split[k]) for k in range(K))
     # the same steps through per-problem graphs on a stream pool
     step_pool()
     torch.cuda.synchronize()
@@ -288,14 +312,17 @@ def run_batch(args):
                    "mix": "50% interior Dirichlet / 50% exterior Neumann + Dirichlet box; 50% (4,5) / 50% (6,7); "
                           "ellipses and 5-7 lobe stars", "tol": 1e-10, "l2": "flushed between steps",
                    "step": "per problem: setup+data+solve; solves through the batched engine"},
-        "iters_mean": statistics.mean(iters), "ticks_per_step": statistics.mean(ticks),
-        "kernels_per_tick": E.stats()[0], "autotune_vcycle_ms": tuned.get("ms"), "tile_shapes": E.shapes(),
+        "iters_mean": statistics.mean(iters), "iters_max": max(iters), "ticks_per_step": statistics.mean(ticks),
+        "setup_data_ms_per_step": setup_ms, "engine_ms_per_step": total_ms / K - setup_ms,
+        "engines": ne, "kernels_per_tick": E.stats()[0], "autotune_vcycle_ms": tuned.get("ms"),
+        "tile_shapes": E.shapes(),
         "stream_pool_solves_per_s": count * 1e3 / statistics.mean(pool_ms),
         "gpu_launches": launches, "clocks": clk,
     }
     if rank == 0:
         print(json.dumps(out))
-    E.close()
+    for e in engines:
+        e.close()
 
 
 def run_serve(args):
@@ -456,7 +483,10 @@ def run_ours(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2 (129 MB)
     torch.cuda.synchronize()
 
-    engine = iim.Engine(opts, max_slots=B, stream=main) if args.solver == "engine" else None
+    ne = max(1, min(args.engines, B))
+    eng_streams = [main] + [torch.cuda.Stream() for _ in range(ne - 1)]
+    engines = [iim.Engine(opts, max_slots=B, stream=st) for st in eng_streams] if args.solver == "engine" else None
+    engine = engines[0] if engines else None
 
     def step(s, problems, xvec, use_engine=True):
         """Set-up + data of every problem of the batch on its own stream, then the solves:
@@ -473,14 +503,23 @@ def run_ours(args):
                 f, j0, j1, box = inputs[i][0][s]
                 P.set_data(f, None, j0, j1, box)
                 xvec[i].zero_()
-        if engine is not None and use_engine:
-            t0 = engine.stats()[1]
-            slots = [engine.admit(P, x) for P, x in zip(problems, xvec)]
-            engine.run()
-            engine.poll(wait=True)
-            infos = [engine.release(sl, x) for sl, x in zip(slots, xvec)]
-            kpt, t1 = engine.stats()
-            return infos, iim.launch_count() - l0 - 1 + kpt * (t1 - t0)
+        if engines is not None and use_engine:
+            # problem i goes to engine i mod ne; the engines run concurrently on their streams
+            use = engines[:min(ne, len(problems))]
+            t0 = [E.stats()[1] for E in use]
+            slots = [use[i % len(use)].admit(P, x) for i, (P, x) in enumerate(zip(problems, xvec))]
+            for E in use:
+                E.run()
+            for E in use:
+                E.poll(wait=True)
+            infos = [use[i % len(use)].release(sl, x) for i, (sl, x) in enumerate(zip(slots, xvec))]
+            for st in eng_streams[1:]:
+                main.wait_stream(st)
+            kern = iim.launch_count() - l0 - len(use)
+            for E, a in zip(use, t0):
+                kpt, t1 = E.stats()
+                kern += kpt * (t1 - a)
+            return infos, kern
         if len(problems) == 1 and args.no_graph:
             _, info = problems[0].solve(xvec[0])
             infos = [info]
@@ -541,7 +580,10 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         e2e = e2e_run(probs, torch, inputs, Wm, K, world, main)
-    roof = None if args.no_roofline else roofline(probs[0], iim, torch, main)
+    roof = None
+    if not args.no_roofline:
+        applies = statistics.mean(iters) + 4                  # iterations + start/restarts
+        roof = roofline(probs[0], iim, torch, main, applies)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(n, statistics.mean(iters))
@@ -554,8 +596,8 @@ def run_ours(args):
                    "geometry": "star r=0.5+0.1 sin(5 theta), rotated per problem", "tol": 1e-10,
                    "krylov": "FGMRES(10), right", "preconditioner": "SW multigrid V(2,2), fp32",
                    "batch": B, "l2": "flushed between steps", "step": "per problem: setup+data+solve",
-                   "solver": "batched engine (lock-step ticks, one graph launch per step)" if engine is not None
-                   else "per-problem solve graphs on a stream pool"},
+                   "solver": f"batched engines x{ne} (lock-step ticks, one graph launch per engine and step)"
+                   if engine is not None else "per-problem solve graphs on a stream pool"},
         "latency_ms_single_solve": statistics.median(lat),
         "iters_mean": statistics.mean(iters), "err_vs_exact": err_exact,
         "fp64_form": fp64_form,
@@ -621,30 +663,55 @@ def e2e_run(probs, torch, inputs, Wm, K, world, main):
             "d2h_bytes_per_step": probs[0].N * 8 * len(probs)}
 
 
-def roofline(P, iim, torch, stream):
-    """Dominant kernel: the FP64 high-order stencil (bound by the FP64 pipe).
+# DRAM bytes per launch from the ncu capture summarised in profiles/ (None once the
+# kernel changed after the capture)
+NCU_TRAFFIC = {}
 
-    Algorithmic FP64 work per unknown node: w(2d-1) adds to pair the 2dw
-    neighbours by |j|, w multiply-adds and one multiply -> w(2d+1)+1 flop
-    (16 for the 2D sixth-order stencil).  Timed live with CUDA events on the
-    problem's stream over repeated launches of the same kernel on the solve's
-    own vectors.
+
+def roofline(P, iim, torch, stream, applies_per_solve):
+    """Roofline of the dominant kernel of a solve (by device time per solve), both bound by
+    the FP64 pipe: the least-squares fits (once per solve) and the high-order stencil
+    (once per operator application).  Timed live with CUDA events on the problem's stream
+    over repeated launches of the same kernel on the problem's own data.
+
+    Algorithmic work: fits, per fit of m rows and M monomials, Householder QR
+    2 m M^2 - 2/3 M^3 plus w+1 target rows (M^2 for R^-T, 4 m M for Q), summed over the
+    launch's fits; stencil, w(2d+1)+1 flop per unknown (16 for the 2D sixth-order
+    stencil: pair sums by |j|, then one FMA per |j| and one multiply).
     """
     import ctypes
     lib = iim.load()
-    us = ctypes.c_double()
-    reps = 50
-    st = lib.iim_kernel_time(P.h, 0, reps, ctypes.byref(us))
-    if st != 0:
-        return None
-    d, w = 2, 3
-    flops = (w * (2 * d + 1) + 1) * P.n_unknowns
-    achieved = flops / (us.value * 1e-6) / 1e12
     pk, src = peaks()
     peak = fp64_peak_tflops(pk.get("sm_max_mhz", 2070.0))
-    return {"kernel": "k_ho_stencil<2,3>", "bound": "alu", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s (FP64)", "frac": achieved / peak, "traffic": None, "us_per_launch": us.value,
-            "peak_note": "152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock"}
+    out = {}
+    us = ctypes.c_double()
+    if lib.iim_kernel_time(P.h, 8, 20, ctypes.byref(us)) == 0:
+        nfit, rows, M = iim.fit_stats(P)
+        w = P.desc.order // 2
+        flops = 2.0 * M * M * rows - 2.0 / 3.0 * M ** 3 * nfit + (w + 1) * (M * M * nfit + 4.0 * M * rows)
+        out["k_fit_quad"] = {"kernel": f"k_fit_quad<{M}>", "flop": flops, "us": us.value,
+                             "us_per_solve": us.value}
+    if lib.iim_kernel_time(P.h, 0, 50, ctypes.byref(us)) == 0:
+        d, w = P.dim, P.desc.order // 2
+        flops = (w * (2 * d + 1) + 1) * P.n_unknowns
+        out["k_ho_stencil"] = {"kernel": f"k_ho_stencil<{d},{w}>", "flop": flops, "us": us.value,
+                               "us_per_solve": us.value * applies_per_solve}
+    if not out:
+        return None
+    top = max(out.values(), key=lambda r: r["us_per_solve"])
+    achieved = top["flop"] / (top["us"] * 1e-6) / 1e12
+
+    def entry(r):
+        a = r["flop"] / (r["us"] * 1e-6) / 1e12
+        return {"kernel": r["kernel"], "achieved": a, "frac": a / peak, "us_per_launch": r["us"],
+                "flop_per_launch": r["flop"], "us_per_solve": r["us_per_solve"]}
+
+    return {"kernel": top["kernel"], "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s (FP64)",
+            "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(top["kernel"]), "us_per_launch": top["us"],
+            "flop_per_launch": top["flop"],
+            "peak_note": "derived FP64 peak: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock (measured 0.598 TFMA/s "
+                         "at 1.995 GHz agrees); the measured copy and bf16 peaks do not apply to FP64 work",
+            "kernels": [entry(r) for r in out.values()]}
 
 
 def cpu_baseline(n, gpu_iters):

@@ -323,14 +323,34 @@ iim_status iim_server_take(iim_server* s, int64_t id, double* x_host, iim_solve_
 iim_status iim_server_stats(iim_server* s, size_t* bytes_in_use, size_t* peak_bytes, int* queued, int* resident,
                             int64_t* runs, double* host_seconds);
 
+/* Boundary quantity the data do not prescribe, at every control point (K values,
+ * the order of iim_control_points), from the same least-squares fits (Sec. 2.4):
+ * Dirichlet problems: n . grad u(x_c) (n out of Omega+); Neumann problems: u(x_c)
+ * (Eq. 6, with the qbar set by iim_set_data).  u_dev: n^d values (a solution).
+ * Interface problems: IIM_ERR_INVALID_ARG.  Asynchronous. */
+iim_status iim_boundary_values(iim_problem* p, const double* u_dev, double* out_dev);
+
+/* grad u at every unknown node (Sec. 2.4): the centred first-derivative stencil of
+ * the scheme's order (4 or 6) applied to the same extension of u as the operator
+ * (u in its phase, the fits' ghost values with the problem's data past the first
+ * control point, the outer-box ghosts).  grad_dev: dim x n^d values, axis-major
+ * (component k of node i at k n^d + i); zero at nodes that are not unknowns.
+ * Asynchronous. */
+iim_status iim_gradient(iim_problem* p, const double* u_dev, double* grad_dev);
+
 /* Profiling: average device time (microseconds) of one launch of an internal
  * kernel, timed with CUDA events on the problem's stream over ``reps`` back to
  * back launches on the problem's own vectors (after 3 untimed launches).
  * which: 0 high-order stencil, 1 ghost values, 2 corrections (Eq. 12 operator
  * kernels); 3 one red half sweep on the finest level; 4 FGMRES multi-dot and
- * 5 update over restart/2 + 1 vectors; 6 a whole V-cycle; 7 the whole operator.
+ * 5 update over restart/2 + 1 vectors; 6 a whole V-cycle; 7 the whole operator;
+ * 8 the least-squares fits of the set-up (Sec. 2.1-2.2).
  * Overwrites the problem's work vectors: call it between solves.  Synchronises. */
 iim_status iim_kernel_time(iim_problem* p, int which, int reps, double* us);
+
+/* Least-squares fits of the current set-up: their number, the sum of their rows
+ * (|X_c| + 1 each) and the monomial count M (for work estimates).  Synchronises. */
+iim_status iim_problem_fit_stats(iim_problem* p, int64_t* nfit, int64_t* rows_sum, int* monomials);
 
 /* Kernel launches issued by this library in the calling process so far. */
 int64_t iim_launch_count(void);

@@ -63,10 +63,14 @@ SIGNATURES = {
                                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "iim_control_points": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "iim_problem_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "iim_problem_fit_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                             ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]),
     "iim_phase": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "iim_set_data": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 5),
     "iim_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "iim_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "iim_boundary_values": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "iim_gradient": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "iim_apply_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "iim_precondition": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "iim_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(SolveInfo)]),
@@ -289,6 +293,18 @@ class Problem:
         _check(load().iim_apply_noalloc(self.h, _ptr(u), _ptr(w), int(include_data)), "iim_apply_noalloc")
         return w
 
+    def boundary_values(self, u):
+        """Unprescribed boundary quantity at the control points (see iim_boundary_values)."""
+        out = self._empty(max(self.K, 1))
+        _check(load().iim_boundary_values(self.h, _ptr(u), _ptr(out)), "iim_boundary_values")
+        return out[:self.K]
+
+    def gradient(self, u):
+        """grad u, shape (dim, N) (see iim_gradient)."""
+        g = self._empty(self.dim, self.N)
+        _check(load().iim_gradient(self.h, _ptr(u), _ptr(g)), "iim_gradient")
+        return g
+
     def rhs(self):
         b = self._empty(self.N)
         _check(load().iim_rhs(self.h, _ptr(b)))
@@ -334,7 +350,14 @@ def batch_solve(problems, xs, check=True):
 
 
 KERNELS = {"stencil": 0, "ghost": 1, "correct": 2, "smooth_fine": 3, "multidot": 4, "update": 5, "vcycle": 6,
-           "operator": 7}
+           "operator": 7, "fits": 8}
+
+
+def fit_stats(problem):
+    """(number of fits, sum of their rows, monomials M) of the problem's current set-up."""
+    nf, rs, m = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+    _check(load().iim_problem_fit_stats(problem.h, ctypes.byref(nf), ctypes.byref(rs), ctypes.byref(m)))
+    return nf.value, rs.value, m.value
 
 
 def kernel_time(problem, which, reps=50) -> float:

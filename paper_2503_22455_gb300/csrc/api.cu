@@ -340,8 +340,11 @@ iim_status iim_problem_create(const iim_problem_desc* desc, const iim_options* o
   cudaMemsetAsync(P.d_j0, 0, sizeof(double) * P.K_cap, P.stream);
   cudaMemsetAsync(P.d_j1, 0, sizeof(double) * P.K_cap, P.stream);
   cudaMemsetAsync(P.d_box, 0, sizeof(double) * (P.B > 0 ? P.B : 1), P.stream);
-  IIM_ALLOC(P.b, double, N);
-  cudaMemsetAsync(P.b, 0, sizeof(double) * N, P.stream);
+  // pure Neumann: L 1 = 0; the solve runs on the augmented system [L 1; 1^T 0] (Sec. 2.3),
+  // whose last entry (the shift alpha, the constraint gamma = 0) follows the grid vector
+  P.aug = desc->bc == IIM_BC_NEUMANN && desc->box_bc == IIM_BOX_NONE;
+  IIM_ALLOC(P.b, double, N + 1);
+  cudaMemsetAsync(P.b, 0, sizeof(double) * (N + 1), P.stream);
   // multigrid levels
   std::vector<int> sizes = level_sizes(n, d);
   if ((int)sizes.size() > kMaxLevels) IIM_FAIL(IIM_ERR_INVALID_ARG);
@@ -396,10 +399,12 @@ iim_status iim_problem_create(const iim_problem_desc* desc, const iim_options* o
       IIM_FAIL(IIM_ERR_INVALID_ARG);
     }
     P.coarse_nu = nu;
+    P.coarse_n = nu > 0 ? nu + P.aug : 0;
+    const size_t cn = (size_t)P.coarse_n;
     IIM_ALLOC(P.coarse_map, int32_t, nu > 0 ? nu : 1);
-    IIM_ALLOC(P.coarse_piv, int32_t, nu > 0 ? nu : 1);
-    IIM_ALLOC(P.coarse_lu64, double, 2 * (size_t)nu * nu + 1);
-    IIM_ALLOC(P.coarse_lu32, float, 2 * (size_t)nu * nu + 1);
+    IIM_ALLOC(P.coarse_piv, int32_t, cn > 0 ? cn : 1);
+    IIM_ALLOC(P.coarse_lu64, double, 2 * cn * cn + 1);
+    IIM_ALLOC(P.coarse_lu32, float, 2 * cn * cn + 1);
   }
   mg_coarse_factor(P, P.stream);
   cudaStreamSynchronize(P.stream);
@@ -519,6 +524,21 @@ iim_status iim_problem_bytes(iim_problem* H, size_t* bytes) {
   return IIM_OK;
 }
 
+iim_status iim_problem_fit_stats(iim_problem* H, int64_t* nfit, int64_t* rows_sum, int* monomials) {
+  if (!H) return IIM_ERR_INVALID_ARG;
+  Problem& P = H->P;
+  const int K = read_count(P, 0);
+  const int nf = P.desc.bc == IIM_BC_INTERFACE ? 2 * K : K;
+  std::vector<int32_t> R(nf > 0 ? nf : 1);
+  if (nf > 0) cudaMemcpy(R.data(), P.fit_R, sizeof(int32_t) * nf, cudaMemcpyDeviceToHost);
+  int64_t s = 0;
+  for (int k = 0; k < nf; ++k) s += R[k] + 1;           // X_c plus the control point
+  if (nfit) *nfit = nf;
+  if (rows_sum) *rows_sum = s;
+  if (monomials) *monomials = P.M;
+  return cuda_check("fit stats");
+}
+
 iim_status iim_control_points(iim_problem* H, double* xc, double* nrm) {
   if (!H) return IIM_ERR_INVALID_ARG;
   Problem& P = H->P;
@@ -568,6 +588,20 @@ iim_status iim_apply_noalloc(iim_problem* H, const double* u, double* w, int inc
   return cuda_check("apply_noalloc");
 }
 
+iim_status iim_boundary_values(iim_problem* H, const double* u, double* out) {
+  if (!H || !u || !out) return IIM_ERR_INVALID_ARG;
+  iim_status st = boundary_values(H->P, u, out, H->P.stream);
+  if (st != IIM_OK) return st;
+  return cuda_check("boundary values");
+}
+
+iim_status iim_gradient(iim_problem* H, const double* u, double* grad) {
+  if (!H || !u || !grad) return IIM_ERR_INVALID_ARG;
+  iim_status st = gradient(H->P, u, grad, H->P.stream);
+  if (st != IIM_OK) return st;
+  return cuda_check("gradient");
+}
+
 iim_status iim_rhs(iim_problem* H, double* b) {
   if (!H || !b) return IIM_ERR_INVALID_ARG;
   cudaMemcpyAsync(b, H->P.b, sizeof(double) * H->P.g.N, cudaMemcpyDeviceToDevice, H->P.stream);
@@ -615,6 +649,7 @@ iim_status iim_solve(iim_problem* H, double* x, iim_solve_info* info) {
   if (!H || !x) return IIM_ERR_INVALID_ARG;
   Problem& P = H->P;
   cudaMemcpyAsync(P.x, x, sizeof(double) * P.g.N, cudaMemcpyDeviceToDevice, P.stream);
+  if (P.aug) cudaMemsetAsync(P.x + P.g.N, 0, sizeof(double), P.stream);   // alpha starts at 0
   cudaEventRecord(P.ev0, P.stream);
   const int64_t l0 = iim_launch_count();
   iim_status st = solve_enqueue(P, P.stream);
@@ -640,7 +675,7 @@ iim_status iim_solve_host(iim_problem* H, const double* f, const double* g, cons
   cudaMemcpyAsync(fst, f, sizeof(double) * P.g.N, cudaMemcpyHostToDevice, P.stream);
   copy_data(P, g, j0, j1, box, cudaMemcpyHostToDevice);
   compute_rhs(P, fst, P.stream);
-  cudaMemsetAsync(P.x, 0, sizeof(double) * P.g.N, P.stream);
+  cudaMemsetAsync(P.x, 0, sizeof(double) * (P.g.N + P.aug), P.stream);
   cudaEventRecord(P.ev0, P.stream);
   const int64_t l0 = iim_launch_count();
   iim_status st = solve_enqueue(P, P.stream);
@@ -689,6 +724,7 @@ iim_status iim_batch_solve(iim_problem** probs, double** xs, int count, iim_solv
     cudaEventRecord(evs[i], P.stream);
     cudaStreamWaitEvent(s, evs[i], 0);
     cudaMemcpyAsync(P.x, xs[i], sizeof(double) * P.g.N, cudaMemcpyDeviceToDevice, s);
+    if (P.aug) cudaMemsetAsync(P.x + P.g.N, 0, sizeof(double), s);
     cudaEventRecord(P.ev0, s);
     cudaMemsetAsync(P.d_status + 1, 0, sizeof(int), s);
     if (P.opt.use_graph) {
@@ -704,6 +740,7 @@ iim_status iim_batch_solve(iim_problem** probs, double** xs, int count, iim_solv
     Problem& P = probs[i]->P;
     if (!P.opt.use_graph) {
       cudaMemcpy(P.x, xs[i], sizeof(double) * P.g.N, cudaMemcpyDeviceToDevice);
+      if (P.aug) cudaMemset(P.x + P.g.N, 0, sizeof(double));
       cudaMemsetAsync(P.d_status + 1, 0, sizeof(int), P.stream);
       krylov_enqueue_solve(P, P.x, false);
       cudaMemcpyAsync(xs[i], P.x, sizeof(double) * P.g.N, cudaMemcpyDeviceToDevice, P.stream);
@@ -730,10 +767,11 @@ iim_status iim_kernel_time(iim_problem* H, int which, int reps, double* us) {
       case 5: krylov_orth_pass(P, j, 1, s); break;
       case 6: mg_precondition(P, P.V, nullptr, P.tmp, s); break;
       case 7: ho_apply(P, P.x, P.tmp, false, s); break;
+      case 8: setup_fits(P); break;
       default: break;
     }
   };
-  if (which < 0 || which > 7) return IIM_ERR_INVALID_ARG;
+  if (which < 0 || which > 8) return IIM_ERR_INVALID_ARG;
   for (int r = 0; r < 3; ++r) launch();
   cudaEventRecord(P.ev0, s);
   for (int r = 0; r < reps; ++r) launch();

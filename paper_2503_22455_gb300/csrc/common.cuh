@@ -27,6 +27,7 @@ struct Geom {
   int dim;
   double sign;                         // phi = sign * g
   double p[8];
+  double cs, sn;                       // ellipse: cos and sin of the rotation angle p[4]
 };
 
 // g(x) < 0 inside the body; the paper's Omega+ = {phi >= 0}, phi = sign * g
@@ -39,7 +40,7 @@ __host__ __device__ inline double geom_g(const Geom& G, const double* x) {
       return sqrt(a * a + b * b + c * c) - p[3];
     }
     case IIM_GEOM_ELLIPSE: {
-      double cs = cos(p[4]), sn = sin(p[4]);
+      const double cs = G.cs, sn = G.sn;
       double dx = x[0] - p[0], dy = x[1] - p[1];
       double y0 = cs * dx + sn * dy, y1 = -sn * dx + cs * dy;
       return (y0 / p[2]) * (y0 / p[2]) + (y1 / p[3]) * (y1 / p[3]) - 1.0;
@@ -71,7 +72,7 @@ __host__ __device__ inline void geom_grad_g(const Geom& G, const double* x, doub
       gr[0] = a / r; gr[1] = b / r; gr[2] = c / r; return;
     }
     case IIM_GEOM_ELLIPSE: {
-      double cs = cos(p[4]), sn = sin(p[4]);
+      const double cs = G.cs, sn = G.sn;
       double dx = x[0] - p[0], dy = x[1] - p[1];
       double y0 = cs * dx + sn * dy, y1 = -sn * dx + cs * dy;
       double g0 = 2 * y0 / (p[2] * p[2]), g1 = 2 * y1 / (p[3] * p[3]);
@@ -113,7 +114,7 @@ __host__ __device__ inline double geom_curvature(const Geom& G, const double* x)
       geom_grad_g(G, x, gr);
       double gn = hypot(gr[0], gr[1]);
       double t0 = -gr[1] / gn, t1 = gr[0] / gn;
-      double cs = cos(p[4]), sn = sin(p[4]);
+      const double cs = G.cs, sn = G.sn;
       double l0 = 2 / (p[2] * p[2]), l1 = 2 / (p[3] * p[3]);
       // H = R diag(l0,l1) R^T, R = [[cs,-sn],[sn,cs]]
       double u0 = cs * t0 + sn * t1, u1 = -sn * t0 + cs * t1;

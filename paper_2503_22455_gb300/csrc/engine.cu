@@ -192,32 +192,33 @@ static void build_mg_program(Engine& E, const unsigned char* present) {
     if (present[kList3dN + d]) d3 = d + 1;
   }
   const int nu1 = E.opt.nu1, nu2 = E.opt.nu2;
-  // buffer sequence of one fine level (same at every depth): A starts as u
-  struct Sel { int in, out; };
+  // kernels of one fine level (the same at every depth) and their buffers: A starts as u
+  struct Sel { int mode, in, out; };
   std::vector<Sel> down, up;
   int A = 0, B = 1;
-  down.push_back({-1, A});                        // mode 0 writes A
-  for (int it = 1; it < nu1 - 1; ++it) { down.push_back({A, B}); std::swap(A, B); }
-  down.push_back({A, B});                         // mode 1
-  std::swap(A, B);
-  up.push_back({A, B});                           // mode 2
-  std::swap(A, B);
-  for (int it = 1; it < nu2 - 1; ++it) { up.push_back({A, B}); std::swap(A, B); }
-  up.push_back({A, B});                           // mode 3: the level's result is in B
-  const int res = B;
-  auto add2 = [&](int d, int mode, Sel s) {
+  if (nu1 == 2 && nu2 == 2) {
+    down.push_back({5, -1, A});                   // both pre-smoothing sweeps + restriction
+    up.push_back({6, A, B});                      // correction + both post-smoothing sweeps
+  } else {
+    down.push_back({0, -1, A});
+    for (int it = 1; it < nu1 - 1; ++it) { down.push_back({4, A, B}); std::swap(A, B); }
+    down.push_back({1, A, B});
+    std::swap(A, B);
+    up.push_back({2, A, B});
+    std::swap(A, B);
+    for (int it = 1; it < nu2 - 1; ++it) { up.push_back({4, A, B}); std::swap(A, B); }
+    up.push_back({3, A, B});
+  }
+  const int res = B;                              // the level's result
+  auto add2 = [&](int d, const Sel& s) {
     for (int sh = 0; sh < kEngShapes; ++sh) {
       if (!present[kListMg2d + d * kEngShapes + sh]) continue;
-      EngMgStep st{0, mode, d, sh, s.in < 0 ? 0 : s.in, s.out, res, 0};
+      EngMgStep st{0, s.mode, d, sh, s.in < 0 ? 0 : s.in, s.out, res, 0};
       E.mg_steps.push_back(st);
     }
   };
-  for (int d = 0; d < d2; ++d) {
-    for (size_t k = 0; k < down.size(); ++k) {
-      const int mode = k == 0 ? 0 : (k + 1 == down.size() ? 1 : 4);
-      add2(d, mode, down[k]);
-    }
-  }
+  for (int d = 0; d < d2; ++d)
+    for (const Sel& st : down) add2(d, st);
   auto add3 = [&](int kind3, int d, int colour) {
     EngMgStep st{2 + kind3, 0, d, 0, 0, 0, 0, colour};
     E.mg_steps.push_back(st);
@@ -230,12 +231,8 @@ static void build_mg_program(Engine& E, const unsigned char* present) {
     add3(3, d, 0);
   }
   if (present[kListTail]) E.mg_steps.push_back(EngMgStep{1, 0, 0, 0, 0, 0, 0, 0});
-  for (int d = d2 - 1; d >= 0; --d) {
-    for (size_t k = 0; k < up.size(); ++k) {
-      const int mode = k == 0 ? 2 : (k + 1 == up.size() ? 3 : 4);
-      add2(d, mode, up[k]);
-    }
-  }
+  for (int d = d2 - 1; d >= 0; --d)
+    for (const Sel& st : up) add2(d, st);
   for (int d = d3 - 1; d >= 0; --d) {
     add3(4, d, 0);
     for (int it = 0; it < nu2; ++it)
@@ -408,6 +405,10 @@ iim_status iim_engine_admit(iim_engine* H, iim_problem* p, const double* x0_dev,
   Problem& P = p->P;
   if (P.opt.mg_precision == IIM_MG_FP64 || P.opt.nu1 != E.opt.nu1 || P.opt.nu2 != E.opt.nu2) {
     set_error("engine: the problem's multigrid options differ from the engine's");
+    return IIM_ERR_INVALID_ARG;
+  }
+  if (P.aug) {
+    set_error("engine: pure Neumann problems (augmented system) are solved by iim_solve only");
     return IIM_ERR_INVALID_ARG;
   }
   if ((int)mg_tail_start(P) > kEngMaxDepth) {

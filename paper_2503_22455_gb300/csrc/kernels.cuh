@@ -151,6 +151,8 @@ struct Problem {
   // multigrid
   std::vector<Level> lv;
   int coarse_nu = 0;              // unknowns on the coarsest level
+  int coarse_n = 0;               // size of the coarse dense system: coarse_nu (+1 when augmented)
+  int aug = 0;                    // pure Neumann: the augmented system of Sec. 2.3 (one more unknown)
   int32_t* coarse_map = nullptr;  // [coarse_nu] node of each coarse unknown
   double* coarse_lu64 = nullptr;  // [nu][nu] LU factors (row major), FP64
   float* coarse_lu32 = nullptr;
@@ -189,6 +191,9 @@ void ho_ghost(Problem& P, const double* u, bool with_data, cudaStream_t s);
 void ho_correct(Problem& P, const double* u, double* w, bool with_data, cudaStream_t s);
 iim_status ho_apply_noalloc(Problem& P, const double* u, double* w, bool with_data, cudaStream_t s);
 void compute_rhs(Problem& P, const double* f, cudaStream_t s);
+iim_status boundary_values(Problem& P, const double* u, double* out, cudaStream_t s);
+iim_status gradient(Problem& P, const double* u, double* grad, cudaStream_t s);
+void eng_operator_params(Problem& P, StencilCoef* C, GhostParams* GP, CorrectParams* CP);
 
 // multigrid.cu
 void mg_precondition(Problem& P, const double* v, const double* vscale, double* z, cudaStream_t s);

@@ -352,7 +352,7 @@ __global__ void k_set_handles(SolverScalars* S, cudaGraphConditionalHandle hw, c
 
 // ---------------------------------------------------------------------------- host side
 iim_status krylov_alloc(Problem& P) {
-  P.Npad = ((P.g.N + 63) / 64) * 64;
+  P.Npad = ((P.g.N + P.aug + 63) / 64) * 64;   // augmented: entry N holds the shift alpha
   const int m = P.opt.restart;
   P.V = (double*)dev_alloc(P, sizeof(double) * (size_t)(m + 1) * P.Npad);
   P.Z = (double*)dev_alloc(P, sizeof(double) * (size_t)m * P.Npad);
@@ -405,12 +405,48 @@ void krylov_orth_pass(Problem& P, int j, int which, cudaStream_t s) {
   }
 }
 
+// Augmented system (pure Neumann, Sec. 2.3): w = L u + alpha 1 on the unknowns, w_N = 1^T u.
+// The sum is deterministic: block partials in a fixed grid, then one thread in block order.
+__global__ void __launch_bounds__(256) k_aug_apply(const double* __restrict__ u, double* __restrict__ w,
+                                                   const uint8_t* __restrict__ phase, int64_t N, double* partial) {
+  const double alpha = u[N];
+  double acc[1] = {0.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    if (phase[i]) {
+      w[i] += alpha;
+      acc[0] += u[i];
+    }
+  block_reduce_store<1>(acc, partial, 1, blockIdx.x);
+}
+
+__global__ void k_aug_finish(double* __restrict__ w, int64_t N, const double* __restrict__ partial, int nb) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += partial[b];
+  w[N] = s;
+}
+
+// z_N = v_N (scaled like the rest of v): the preconditioner is the identity on alpha
+__global__ void k_aug_pass(const double* __restrict__ v, const double* __restrict__ vscale, double* __restrict__ z,
+                           int64_t N) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) z[N] = v[N] * (vscale ? *vscale : 1.0);
+}
+
+// the operator of the Krylov iteration
+static void krylov_apply(Problem& P, const double* u, double* w, cudaStream_t s) {
+  ho_apply(P, u, w, false, s);
+  if (!P.aug) return;
+  IIM_LAUNCH(k_aug_apply, P.red_blocks, kRedThreads, 0, s, u, w, P.phase, P.g.N, P.partial);
+  IIM_LAUNCH(k_aug_finish, 1, 32, 0, s, w, P.g.N, P.partial, P.red_blocks);
+}
+
 static void enqueue_iteration(Problem& P, int j, cudaStream_t s) {
   double* vj = P.V + (size_t)j * P.Npad;
   double* zj = P.Z + (size_t)j * P.Npad;
   double* w = P.V + (size_t)(j + 1) * P.Npad;
   mg_precondition(P, vj, &P.sc->inv_norm[j], zj, s);
-  ho_apply(P, zj, w, false, s);
+  if (P.aug) IIM_LAUNCH(k_aug_pass, 1, 32, 0, s, vj, &P.sc->inv_norm[j], zj, P.g.N);
+  krylov_apply(P, zj, w, s);
   orth(P, j, s, 0);
   if (P.opt.reorth) orth(P, j, s, 1);
   IIM_LAUNCH(k_arnoldi_step, 1, 32, 0, s, P.sc, j, P.d_status);
@@ -418,17 +454,17 @@ static void enqueue_iteration(Problem& P, int j, cudaStream_t s) {
 
 static void enqueue_restart(Problem& P, cudaStream_t s) {
   IIM_LAUNCH(k_solve_y, 1, 32, 0, s, P.sc);
-  IIM_LAUNCH(k_xupdate, 4 * kNumSMs, 256, 0, s, P.x, P.Z, P.Npad, P.g.N, P.sc);
-  ho_apply(P, P.x, P.tmp, false, s);
-  IIM_LAUNCH(k_residual, P.red_blocks, kRedThreads, 0, s, P.b, P.tmp, P.V, P.g.N, P.partial, P.counter, P.sc, 0,
-             P.d_status);
+  IIM_LAUNCH(k_xupdate, 4 * kNumSMs, 256, 0, s, P.x, P.Z, P.Npad, P.g.N + P.aug, P.sc);
+  krylov_apply(P, P.x, P.tmp, s);
+  IIM_LAUNCH(k_residual, P.red_blocks, kRedThreads, 0, s, P.b, P.tmp, P.V, P.g.N + P.aug, P.partial, P.counter, P.sc,
+             0, P.d_status);
 }
 
 static void enqueue_start(Problem& P, cudaStream_t s, int graph_mode) {
   IIM_LAUNCH(k_init_scalars, 1, 1, 0, s, P.sc, P.opt.restart, P.opt.max_iter, P.opt.tol, graph_mode, P.opt.reorth);
-  ho_apply(P, P.x, P.tmp, false, s);
-  IIM_LAUNCH(k_residual, P.red_blocks, kRedThreads, 0, s, P.b, P.tmp, P.V, P.g.N, P.partial, P.counter, P.sc, 1,
-             P.d_status);
+  krylov_apply(P, P.x, P.tmp, s);
+  IIM_LAUNCH(k_residual, P.red_blocks, kRedThreads, 0, s, P.b, P.tmp, P.V, P.g.N + P.aug, P.partial, P.counter, P.sc,
+             1, P.d_status);
 }
 
 static int64_t launches_now() { return iim_launch_count(); }

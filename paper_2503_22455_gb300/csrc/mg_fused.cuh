@@ -9,6 +9,8 @@
 //   MODE 2  prolongation + correction, first post-smoothing sweep
 //   MODE 3  last post-smoothing sweep; on the finest level z = (double) u
 //   MODE 4  one plain sweep (only when nu > 2)
+//   MODE 5  MODE 0 and MODE 1 in one kernel (nu1 = 2): halo 4, four half sweeps
+//   MODE 6  MODE 2 and MODE 3 in one kernel (nu2 = 2)
 // Coarse tail: every level with at most 1024 nodes (one per thread) and the dense
 // coarse solve run in a single CTA with the whole sub-hierarchy in shared memory.
 #pragma once
@@ -69,14 +71,17 @@ __device__ inline T tab2(const LevelK<T>& L, int r, int k) { return L.tab[(size_
 
 template <typename T, int TX, int TY, int MODE>
 __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx, const int by) {
-  constexpr int SX = TX + 2 * kH, SY = TY + 2 * kH, S = SX * SY;
+  constexpr int KH = MODE >= 5 ? 4 : kH;      // the fused modes run four half sweeps on the tile
+  constexpr bool DOWN_FIRST = MODE == 0 || MODE == 5, UP_FIRST = MODE == 2 || MODE == 6;
+  constexpr bool UP_LAST = MODE == 3 || MODE == 6, RESTRICT = MODE == 1 || MODE == 5;
+  constexpr int SX = TX + 2 * KH, SY = TY + 2 * KH, S = SX * SY;
   __shared__ T us[S];
   __shared__ T fs[S];
   __shared__ int as[S];
   const LevelK<T>& L = P.L;
   const int n = L.n;
-  const int x0 = bx * TX - kH, y0 = by * TY - kH;
-  const bool finest_in = MODE == 0 && P.v != nullptr;
+  const int x0 = bx * TX - KH, y0 = by * TY - KH;
+  const bool finest_in = DOWN_FIRST && P.v != nullptr;
   const T vs = finest_in ? (T)(P.vscale ? *P.vscale : 1.0) : (T)1;
   {
     // all loads of a thread are issued before any is used (no aux -> f/u dependence)
@@ -96,7 +101,7 @@ __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx
         ra[q] = __ldg(L.aux + g);
         if (finest_in) rf[q] = (T)__ldg(P.v + g) * (vs * (__ldg(P.phase + g) ? P.inv_bp : P.inv_bm));
         else rf[q] = L.f[g];
-        if (MODE != 0) ru[q] = P.u_in[g];
+        if (!DOWN_FIRST) ru[q] = P.u_in[g];
       }
     }
 #pragma unroll
@@ -110,13 +115,22 @@ __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx
     }
   }
   __syncthreads();
-  if (MODE == 2) {
-    // u += P e_coarse on margin 2.  The coarse u is 0 at coarse non-unknowns, so the
+  if (finest_in) {
+    // the finest level's right-hand side, stored before the residual replaces it in fs
+    for (int e = threadIdx.x; e < TX * TY; e += blockDim.x) {
+      const int tx = e % TX, ty = e / TX;
+      const int gx = bx * TX + tx, gy = by * TY + ty;
+      if (gx < n && gy < n) L.f[(int64_t)gy * n + gx] = fs[(ty + KH) * SX + tx + KH];
+    }
+  }
+  if (UP_FIRST) {
+    // u += P e_coarse on margin 2 (4 when fused with the whole post-smoothing).  The coarse u is 0 at coarse non-unknowns, so the
     // bilinear form needs no aux; the Neumann mean counts in-domain neighbours.
     const LevelK<T>& C = P.C;
     for (int e = threadIdx.x; e < S; e += blockDim.x) {
       const int sx = e % SX, sy = e / SX;
-      if (sx < kH - 2 || sx >= SX - (kH - 2) || sy < kH - 2 || sy >= SY - (kH - 2)) continue;
+      constexpr int PM = MODE == 6 ? 4 : 2;
+      if (sx < KH - PM || sx >= SX - (KH - PM) || sy < KH - PM || sy >= SY - (KH - PM)) continue;
       if (as[e] == -2) continue;
       const int gx = x0 + sx, gy = y0 + sy;
       const int I0 = gx >> 1, I1 = gy >> 1;
@@ -144,7 +158,7 @@ __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx
     __syncthreads();
   }
   auto half_sweep = [&](int colour, int margin, bool from_zero) {
-    const int lo = kH - margin;
+    const int lo = KH - margin;
     const int rw = SX - 2 * lo, rh = SY - 2 * lo, hw = (rw + 1) / 2;
     for (int t = threadIdx.x; t < rh * hw; t += blockDim.x) {
       const int ry = t / hw, k2 = t - ry * hw;
@@ -175,7 +189,13 @@ __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx
   if (MODE == 0) { half_sweep(0, 1, true); half_sweep(1, 0, false); }
   if (MODE == 1) { half_sweep(0, 2, false); half_sweep(1, 1, false); }
   if (MODE == 2 || MODE == 3 || MODE == 4) { half_sweep(0, 1, false); half_sweep(1, 0, false); }
-  if (MODE == 1) {
+  if (MODE == 5) {     // both pre-smoothing sweeps from u = 0
+    half_sweep(0, 4, true); half_sweep(1, 3, false); half_sweep(0, 2, false); half_sweep(1, 1, false);
+  }
+  if (MODE == 6) {     // both post-smoothing sweeps after the correction
+    half_sweep(0, 3, false); half_sweep(1, 2, false); half_sweep(0, 1, false); half_sweep(1, 0, false);
+  }
+  if (RESTRICT) {
     // residual on the tile, kept in registers until every thread has read its neighbours
     constexpr int TPT = (TX * TY + 255) / 256;
     T rr[TPT];
@@ -185,7 +205,7 @@ __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx
       rr[q] = 0;
       if (e0 >= TX * TY) continue;
       const int tx = e0 % TX, ty = e0 / TX;
-      const int e = (ty + kH) * SX + tx + kH;
+      const int e = (ty + KH) * SX + tx + KH;
       const int a = as[e];
       if (a == -1) {
         const T s = (us[e - 1] + us[e + 1]) + (us[e - SX] + us[e + SX]);
@@ -202,7 +222,7 @@ __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx
       const int e0 = threadIdx.x + q * 256;
       if (e0 >= TX * TY) continue;
       const int tx = e0 % TX, ty = e0 / TX;
-      fs[(ty + kH) * SX + tx + kH] = rr[q];
+      fs[(ty + KH) * SX + tx + KH] = rr[q];
     }
     __syncthreads();
     const LevelK<T>& C = P.C;
@@ -211,7 +231,7 @@ __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx
       const int gcx = bx * (TX / 2) + cx, gcy = by * (TY / 2) + cy;
       if (gcx >= C.n || gcy >= C.n) continue;
       const int64_t ci = (int64_t)gcy * C.n + gcx;
-      const int b = (kH + 2 * cy) * SX + kH + 2 * cx;
+      const int b = (KH + 2 * cy) * SX + KH + 2 * cx;
       const T acc = (fs[b] + fs[b + 1]) + (fs[b + SX] + fs[b + SX + 1]);
       C.f[ci] = C.aux[ci] == -2 ? (T)0 : store_residual(acc * (T)0.25, C.f_bf16);
     }
@@ -221,10 +241,9 @@ __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx
     const int gx = bx * TX + tx, gy = by * TY + ty;
     if (gx >= n || gy >= n) continue;
     const int64_t g = (int64_t)gy * n + gx;
-    const int se = (ty + kH) * SX + tx + kH;
-    if (MODE == 3 && P.z != nullptr) P.z[g] = (double)us[se];
+    const int se = (ty + KH) * SX + tx + KH;
+    if (UP_LAST && P.z != nullptr) P.z[g] = (double)us[se];
     else P.u_out[g] = us[se];
-    if (finest_in) L.f[g] = fs[se];
   }
 }
 
@@ -249,6 +268,7 @@ struct TailParams {
   int nu1, nu2, neumann;
   T* u_out;                          // where the first level's u goes (when z is not set)
   int nu;                            // coarse unknowns
+  int ld;                            // leading dimension of inv (nu, or nu + 1 when augmented)
   const int32_t* map;
   const T* inv;                      // dense inverse of the coarsest SW matrix (row major)
   const double* v;                   // set when the tail starts at the finest level
@@ -399,7 +419,7 @@ __device__ __forceinline__ void vcycle_tail_body(const TailParams<T>& P, const d
     const int lane = tid & 31, wid = tid >> 5, nw = nt / 32;
     for (int r = wid; r < P.nu; r += nw) {
       T s = 0;
-      for (int c = lane; c < P.nu; c += 32) s += P.inv[(size_t)r * P.nu + c] * f[P.map[c]];
+      for (int c = lane; c < P.nu; c += 32) s += P.inv[(size_t)r * P.ld + c] * f[P.map[c]];
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) u[P.map[r]] = s;
     }

@@ -197,11 +197,19 @@ __global__ void k_bridge_out(GridView g, const T* __restrict__ u, double* __rest
 // ---------------------------------------------------------------------------- coarsest level
 // dense coarse matrix (row major, nu x nu) from the level's stencil
 template <typename T>
-__global__ void k_coarse_assemble(LevelView<double> L, const int32_t* __restrict__ map, int nu,
-                                  const int32_t* __restrict__ inv, T* __restrict__ A) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_coarse_assemble(LevelView<double> L, const int32_t* __restrict__ map, int nu_in,
+                                  const int32_t* __restrict__ inv, T* __restrict__ A, int aug) {
+  // rows r < nu: the SW operator; augmented (pure Neumann): a last column and row of
+  // ones over the unknowns and a zero corner (Sec. 2.3), leading dimension nu + 1
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nu = nu_in + aug;
   if (r >= nu) return;
-  for (int c = 0; c < nu; ++c) A[(size_t)r * nu + c] = 0;
+  if (r == nu_in) {
+    for (int c = 0; c < nu_in; ++c) A[(size_t)r * nu + c] = 1;
+    A[(size_t)r * nu + nu_in] = 0;
+    return;
+  }
+  for (int c = 0; c < nu; ++c) A[(size_t)r * nu + c] = (aug && c == nu_in) ? (T)1 : (T)0;
   int64_t i = map[r];
   int a = L.aux[i];
   int m[3];
@@ -296,35 +304,43 @@ __global__ void k_coarse_lu(T* __restrict__ Ag, int nu, int32_t* __restrict__ pi
     for (int e = tid; e < nu * nu; e += nt) Ag[e] = A[e];
   __syncthreads();
   if (in_smem == 2) {
-    // inverse in shared memory: X = U^-1 L^-1 P, all columns at once, one row per step
+    // inverse in shared memory: X = U^-1 L^-1 P, all columns at once, one row per step.
+    // Column j is handled by G consecutive lanes that split the row's dot product.
     T* X = A + (size_t)nu * nu;
     for (int e = tid; e < nu * nu; e += nt) X[e] = 0;
     __syncthreads();
-    if (tid == 0) {
-      // P applied to the identity: row swaps in factorisation order
-      for (int j = 0; j < nu; ++j) {
-        int r = j;
-        for (int k = 0; k < nu; ++k) {
-          if (piv[k] == r) r = k;
-          else if (k == r) r = piv[k];
-        }
-        X[(size_t)r * nu + j] = 1;
+    for (int j = tid; j < nu; j += nt) {
+      // P applied to e_j: follow the row swaps in factorisation order
+      int r = j;
+      for (int k = 0; k < nu; ++k) {
+        if (piv[k] == r) r = k;
+        else if (k == r) r = piv[k];
       }
+      X[(size_t)r * nu + j] = 1;
     }
     __syncthreads();
+    int G = 1;
+    while (G < 32 && 2 * G * nu <= nt) G *= 2;
+    const int sub = tid % G, cols = nt / G;
     for (int r = 1; r < nu; ++r) {                  // forward, unit lower
-      for (int j = tid; j < nu; j += nt) {
-        T s = X[(size_t)r * nu + j];
-        for (int c = 0; c < r; ++c) s -= A[(size_t)r * nu + c] * X[(size_t)c * nu + j];
-        X[(size_t)r * nu + j] = s;
+      for (int j0 = 0; j0 < nu; j0 += cols) {
+        const int j = j0 + tid / G;
+        T s = 0;
+        if (j < nu)
+          for (int c = sub; c < r; c += G) s += A[(size_t)r * nu + c] * X[(size_t)c * nu + j];
+        for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, G);
+        if (j < nu && sub == 0) X[(size_t)r * nu + j] -= s;
       }
       __syncthreads();
     }
     for (int r = nu - 1; r >= 0; --r) {             // backward
-      for (int j = tid; j < nu; j += nt) {
-        T s = X[(size_t)r * nu + j];
-        for (int c = r + 1; c < nu; ++c) s -= A[(size_t)r * nu + c] * X[(size_t)c * nu + j];
-        X[(size_t)r * nu + j] = s / A[(size_t)r * nu + r];
+      for (int j0 = 0; j0 < nu; j0 += cols) {
+        const int j = j0 + tid / G;
+        T s = 0;
+        if (j < nu)
+          for (int c = r + 1 + sub; c < nu; c += G) s += A[(size_t)r * nu + c] * X[(size_t)c * nu + j];
+        for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, G);
+        if (j < nu && sub == 0) X[(size_t)r * nu + j] = (X[(size_t)r * nu + j] - s) / A[(size_t)r * nu + r];
       }
       __syncthreads();
     }
@@ -431,9 +447,10 @@ TailParams<T> make_tail_params(Problem& P, size_t l0, T* u_out, size_t smem_limi
   tp.nu2 = P.opt.nu2;
   tp.neumann = P.desc.bc == IIM_BC_NEUMANN;
   tp.nu = P.coarse_nu;
+  tp.ld = P.coarse_n;
   tp.map = P.coarse_map;
   const T* inv = (const T*)(sizeof(T) == 8 ? (void*)P.coarse_lu64 : (void*)P.coarse_lu32);
-  tp.inv = inv + (size_t)P.coarse_nu * P.coarse_nu;
+  tp.inv = inv + (size_t)P.coarse_n * P.coarse_n;
   tp.v = nullptr;
   tp.vscale = nullptr;
   tp.phase = P.phase;
@@ -480,6 +497,8 @@ static void launch_fine2d(Problem& P, size_t l, int mode, const double* v, const
     case 1: IIM_LAUNCH((k_mg2d<T, TX, TY, 1>), grid, 256, 0, s, fp); break;
     case 2: IIM_LAUNCH((k_mg2d<T, TX, TY, 2>), grid, 256, 0, s, fp); break;
     case 3: IIM_LAUNCH((k_mg2d<T, TX, TY, 3>), grid, 256, 0, s, fp); break;
+    case 5: IIM_LAUNCH((k_mg2d<T, TX, TY, 5>), grid, 256, 0, s, fp); break;
+    case 6: IIM_LAUNCH((k_mg2d<T, TX, TY, 6>), grid, 256, 0, s, fp); break;
     default: IIM_LAUNCH((k_mg2d<T, TX, TY, 4>), grid, 256, 0, s, fp); break;
   }
 }
@@ -501,6 +520,14 @@ static T* vcycle2d(Problem& P, size_t l, size_t lt, const double* v, const doubl
   if (l == lt) {
     launch_tail<T>(P, l, l == 0 ? v : nullptr, l == 0 ? vscale : nullptr, l == 0 ? z : nullptr, s, A);
     return A;
+  }
+  if (P.opt.nu1 == 2 && P.opt.nu2 == 2) {
+    // two fused kernels per level: both pre-smoothing sweeps + restriction, then the
+    // correction + both post-smoothing sweeps
+    fine2d<T>(P, l, 5, l == 0 ? v : nullptr, vscale, nullptr, nullptr, A, nullptr, s);
+    const T* uc = vcycle2d<T>(P, l + 1, lt, nullptr, nullptr, nullptr, s);
+    fine2d<T>(P, l, 6, nullptr, nullptr, l == 0 ? z : nullptr, A, B, uc, s);
+    return B;
   }
   fine2d<T>(P, l, 0, l == 0 ? v : nullptr, vscale, nullptr, nullptr, A, nullptr, s);
   for (int it = 1; it < P.opt.nu1 - 1; ++it) {
@@ -589,7 +616,7 @@ void mg_precondition(Problem& P, const double* v, const double* vscale, double* 
 // coarse matrix, LU and inverse; coarse_lu{64,32} hold [A (nu*nu) | inverse (nu*nu)]
 void mg_coarse_factor(Problem& P, cudaStream_t s) {
   Level& C = P.lv.back();
-  const int nu = P.coarse_nu;
+  const int nu = P.coarse_nu, cn = P.coarse_n;
   if (nu <= 0) return;
   const int Tn = 256;
   IIM_LAUNCH(k_unknown_flag, ceil_div(C.g.N, Tn), Tn, 0, s, C.g, C.aux, C.flag);
@@ -598,21 +625,23 @@ void mg_coarse_factor(Problem& P, cudaStream_t s) {
   IIM_LAUNCH(k_coarse_map, ceil_div(C.g.N, Tn), Tn, 0, s, C.g, C.aux, C.idx, P.coarse_map, inv);
   LevelView<double> V = view<double>(C);
   if (P.opt.mg_precision == IIM_MG_FP64) {
-    IIM_LAUNCH(k_coarse_assemble<double>, ceil_div(nu, 128), 128, 0, s, V, P.coarse_map, nu, inv, P.coarse_lu64);
-    size_t sm = sizeof(double) * (size_t)nu * nu;
+    IIM_LAUNCH(k_coarse_assemble<double>, ceil_div(cn, 128), 128, 0, s, V, P.coarse_map, nu, inv, P.coarse_lu64,
+               P.aug);
+    size_t sm = sizeof(double) * (size_t)cn * cn;
     int in_smem = sm <= 200 * 1024;
     if (2 * sm <= 200 * 1024) { in_smem = 2; sm *= 2; }
     if (in_smem) cudaFuncSetAttribute(k_coarse_lu<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    IIM_LAUNCH(k_coarse_lu<double>, 1, 1024, in_smem ? sm : 0, s, P.coarse_lu64, nu, P.coarse_piv,
-               P.coarse_lu64 + (size_t)nu * nu, P.d_status, in_smem);
+    IIM_LAUNCH(k_coarse_lu<double>, 1, 1024, in_smem ? sm : 0, s, P.coarse_lu64, cn, P.coarse_piv,
+               P.coarse_lu64 + (size_t)cn * cn, P.d_status, in_smem);
   } else {
-    IIM_LAUNCH(k_coarse_assemble<float>, ceil_div(nu, 128), 128, 0, s, V, P.coarse_map, nu, inv, P.coarse_lu32);
-    size_t sm = sizeof(float) * (size_t)nu * nu;
+    IIM_LAUNCH(k_coarse_assemble<float>, ceil_div(cn, 128), 128, 0, s, V, P.coarse_map, nu, inv, P.coarse_lu32,
+               P.aug);
+    size_t sm = sizeof(float) * (size_t)cn * cn;
     int in_smem = sm <= 200 * 1024;
     if (2 * sm <= 200 * 1024) { in_smem = 2; sm *= 2; }
     if (in_smem) cudaFuncSetAttribute(k_coarse_lu<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    IIM_LAUNCH(k_coarse_lu<float>, 1, 1024, in_smem ? sm : 0, s, P.coarse_lu32, nu, P.coarse_piv,
-               P.coarse_lu32 + (size_t)nu * nu, P.d_status, in_smem);
+    IIM_LAUNCH(k_coarse_lu<float>, 1, 1024, in_smem ? sm : 0, s, P.coarse_lu32, cn, P.coarse_piv,
+               P.coarse_lu32 + (size_t)cn * cn, P.d_status, in_smem);
   }
 }
 
@@ -626,7 +655,7 @@ __device__ __forceinline__ const double* eng_vj(const SlotDev& s) { return s.V +
 __device__ __forceinline__ double* eng_zj(const SlotDev& s) { return s.Z + (size_t)s.j * s.Npad; }
 
 template <int TX, int TY, int MODE>
-__global__ void __launch_bounds__(256) k_eng_mg2d(EngArgs A, int list, int d, int in_sel, int out_sel, int res_sel) {
+__global__ void __launch_bounds__(256, 4) k_eng_mg2d(EngArgs A, int list, int d, int in_sel, int out_sel, int res_sel) {
   eng_for_items(A, list, [&](int si, int item) {
     const SlotDev& s = A.slots[si];
     if (s.role != kRoleIter) return;
@@ -635,17 +664,19 @@ __global__ void __launch_bounds__(256) k_eng_mg2d(EngArgs A, int list, int d, in
     fp.C = s.lev[d + 1 < s.nlev ? d + 1 : d];
     float* b0 = s.lev[d].u;
     float* b1 = s.u2[d];
-    fp.u_in = MODE == 0 ? nullptr : (in_sel ? b1 : b0);
+    constexpr bool DOWN_FIRST = MODE == 0 || MODE == 5, UP_FIRST = MODE == 2 || MODE == 6;
+    constexpr bool UP_LAST = MODE == 3 || MODE == 6;
+    fp.u_in = DOWN_FIRST ? nullptr : (in_sel ? b1 : b0);
     fp.u_out = out_sel ? b1 : b0;
     fp.uc = nullptr;
-    if (MODE == 2) fp.uc = (d + 1 < s.nfine && res_sel) ? s.u2[d + 1] : s.lev[d + 1].u;
+    if (UP_FIRST) fp.uc = (d + 1 < s.nfine && res_sel) ? s.u2[d + 1] : s.lev[d + 1].u;
     fp.neumann = s.neumann;
-    fp.v = (MODE == 0 && d == 0) ? eng_vj(s) : nullptr;
+    fp.v = (DOWN_FIRST && d == 0) ? eng_vj(s) : nullptr;
     fp.vscale = &s.sc->inv_norm[s.j];
     fp.phase = s.phase;
     fp.inv_bp = s.inv_bp;
     fp.inv_bm = s.inv_bm;
-    fp.z = (MODE == 3 && d == 0) ? eng_zj(s) : nullptr;
+    fp.z = (UP_LAST && d == 0) ? eng_zj(s) : nullptr;
     const int gx = (s.lev[d].n + TX - 1) / TX;
     mg2d_tile<float, TX, TY, MODE>(fp, item % gx, item / gx);
   });
@@ -716,6 +747,8 @@ static void launch_eng_mg2d(const EngArgs& A, const EngMgStep& st, cudaStream_t 
     case 1: IIM_ENG_MG2D(1); break;
     case 2: IIM_ENG_MG2D(2); break;
     case 3: IIM_ENG_MG2D(3); break;
+    case 5: IIM_ENG_MG2D(5); break;
+    case 6: IIM_ENG_MG2D(6); break;
     default: IIM_ENG_MG2D(4); break;
   }
 #undef IIM_ENG_MG2D

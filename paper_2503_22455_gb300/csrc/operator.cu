@@ -504,4 +504,176 @@ void eng_operator_params(Problem& P, StencilCoef* C, GhostParams* GP, CorrectPar
     for (int mm = 0; mm < 8; ++mm) Q.box_w[k][mm] = P.box_w[k][mm];
 }
 
+
+// ---------------------------------------------------------------------------- boundary quantities, gradient
+// Sec. 2.4: the boundary quantity the data do not prescribe, from row w of each fit:
+// Dirichlet -> n . grad u(x_c) (derivative row, n out of Omega+), Neumann -> u(x_c)
+// (Eq. 6, stored as coefficients over X_c plus 1/D_c times qbar).  Eight lanes per
+// control point.
+__global__ void __launch_bounds__(64) k_boundary_values(GhostParams P, const double* __restrict__ u,
+                                                        double* __restrict__ out) {
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = gid / kGhostLanes, q = gid % kGhostLanes;
+  const int K = *P.K;
+  const bool live = c < K;
+  double acc = 0.0;
+  if (live) {
+    const int R = P.fit_R[c];
+    const int32_t* nodes = P.fit_nodes + (size_t)c * P.rcap;
+    const double* row = P.fit_coef + ((size_t)c * (P.w + 1) + P.w) * P.rcap;
+    for (int a = q; a < R; a += kGhostLanes) acc = fma(row[a], u[nodes[a]], acc);
+  }
+  acc = quad_sum(acc);
+  if (live && q == 0) out[c] = acc + P.fit_cdat[(size_t)c * (P.w + 1) + P.w] * P.g[c];
+}
+
+// centred first-derivative stencil b_{-w..w} of order 2w (odd, b_0 = 0): the unique
+// stencil exact for polynomials of degree <= 2w (2/3, -1/12 for w = 2; 3/4, -3/20,
+// 1/60 for w = 3)
+struct GradCoef {
+  double b[2 * kMaxW + 1];
+};
+
+static GradCoef grad_coef(int w) {
+  GradCoef B;
+  const double h2[2] = {2.0 / 3.0, -1.0 / 12.0};
+  const double h3[3] = {3.0 / 4.0, -3.0 / 20.0, 1.0 / 60.0};
+  for (int k = 0; k < 2 * kMaxW + 1; ++k) B.b[k] = 0.0;
+  for (int j = 1; j <= w; ++j) {
+    const double v = w == 2 ? h2[j - 1] : h3[j - 1];
+    B.b[w + j] = v;
+    B.b[w - j] = -v;
+  }
+  return B;
+}
+
+// grad u by the centred first-derivative stencil b of the scheme's order: neighbours
+// out of phase (or outside the box) contribute nothing here; their ghost values are
+// added by k_grad_correct.  out is [dim][N]; zero at nodes that are not unknowns.
+template <int D, int W>
+__global__ void __launch_bounds__(256) k_grad_stencil(GridView g, GradCoef B, int interface_,
+                                                      const double* __restrict__ u,
+                                                      const uint8_t* __restrict__ phase, double* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.N) return;
+  const int n = g.n;
+  const uint8_t ph = phase[i];
+  if (!interface_ && !ph) {
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax) out[(size_t)ax * g.N + i] = 0.0;
+    return;
+  }
+  int m[3];
+  m[0] = (int)(i % n);
+  const int64_t r = i / n;
+  m[1] = (int)(r % n);
+  m[2] = D > 2 ? (int)(r / n) : 0;
+  const double ih = 1.0 / g.h;
+#pragma unroll
+  for (int ax = 0; ax < D; ++ax) {
+    const int64_t st = ax == 0 ? 1 : (ax == 1 ? (int64_t)n : (int64_t)n * n);
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 1; j <= W; ++j) {
+      double lv = 0.0, rv = 0.0;
+      if (m[ax] - j >= 0 && phase[i - j * st] == ph) lv = u[i - j * st];
+      if (m[ax] + j < n && phase[i + j * st] == ph) rv = u[i + j * st];
+      acc = fma(B.b[W + j], rv - lv, acc);
+    }
+    out[(size_t)ax * g.N + i] = acc * ih;
+  }
+}
+
+// ghost contributions to the gradient at the affected nodes (the walk rules of k_ho_correct)
+__global__ void __launch_bounds__(64) k_grad_correct(CorrectParams P, GradCoef B,
+                                                     const double* __restrict__ u, double* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= *P.n_aff || t >= P.n_aff_cap) return;
+  const GridView& g = P.g;
+  const int n = g.n, d = g.dim, W = P.w;
+  const int64_t i = P.aff_node[t];
+  int m[3];
+  m[0] = (int)(i % n);
+  const int64_t r = i / n;
+  m[1] = (int)(r % n);
+  m[2] = d > 2 ? (int)(r / n) : 0;
+  const uint8_t ph = P.phase[i];
+  const double ih = 1.0 / g.h;
+  for (int ax = 0; ax < d; ++ax) {
+    const int64_t st = ax == 0 ? 1 : (ax == 1 ? (int64_t)n : (int64_t)n * n);
+    double acc = 0.0;
+    for (int sd = 0; sd < 2; ++sd) {
+      const int s = sd ? 1 : -1;
+      const int fit = P.aff_fit[t * 2 * d + 2 * ax + sd];
+      const int js = P.aff_j[t * 2 * d + 2 * ax + sd];
+      if (fit == -1 || fit >= P.nfit_cap) continue;
+      if (fit >= 0) {
+        for (int j = js; j <= W; ++j) {
+          const int pos = m[ax] + j * s;
+          if (pos >= 0 && pos < n && P.phase[i + j * s * st] == ph) continue;
+          acc = fma(B.b[W + j * s], P.G[(size_t)fit * W + (j - js)], acc);
+        }
+      } else {
+        double face = 0.0;
+        if (P.with_data) {
+          int64_t off = 0, mul = 1;
+          for (int k = 0; k < d; ++k) {
+            if (k == ax) continue;
+            off += m[k] * mul;
+            mul *= n;
+          }
+          off += (int64_t)(2 * ax + sd) * mul;
+          face = P.box[off];
+        }
+        for (int j = js; j <= W; ++j) {
+          const int k = j - js;
+          double v = P.box_w[k][0] * face;
+          for (int mm = 2; mm <= P.q + 1; ++mm) {
+            const int pos = s > 0 ? n - mm : mm - 1;
+            v = fma(P.box_w[k][mm - 1], u[i + (int64_t)(pos - m[ax]) * st], v);
+          }
+          acc = fma(B.b[W + j * s], v, acc);
+        }
+      }
+    }
+    out[(size_t)ax * g.N + i] += acc * ih;
+  }
+}
+
+iim_status boundary_values(Problem& P, const double* u, double* out, cudaStream_t s) {
+  if (P.desc.bc == IIM_BC_INTERFACE) {
+    set_error("boundary values are defined for boundary problems");
+    return IIM_ERR_INVALID_ARG;
+  }
+  StencilCoef C;
+  GhostParams GP;
+  CorrectParams CP;
+  eng_operator_params(P, &C, &GP, &CP);
+  if (P.K_cap > 0)
+    IIM_LAUNCH(k_boundary_values, ceil_div((int64_t)P.K_cap * kGhostLanes, 64), 64, 0, s, GP, u, out);
+  return IIM_OK;
+}
+
+iim_status gradient(Problem& P, const double* u, double* grad, cudaStream_t s) {
+  const GridView& g = P.g;
+  const GradCoef b_dev = grad_coef(P.w);
+  const int iface = P.desc.bc == IIM_BC_INTERFACE;
+  const int grid = ceil_div(g.N, 256);
+  if (g.dim == 2) {
+    if (P.w == 2) IIM_LAUNCH((k_grad_stencil<2, 2>), grid, 256, 0, s, g, b_dev, iface, u, P.phase, grad);
+    else IIM_LAUNCH((k_grad_stencil<2, 3>), grid, 256, 0, s, g, b_dev, iface, u, P.phase, grad);
+  } else {
+    if (P.w == 2) IIM_LAUNCH((k_grad_stencil<3, 2>), grid, 256, 0, s, g, b_dev, iface, u, P.phase, grad);
+    else IIM_LAUNCH((k_grad_stencil<3, 3>), grid, 256, 0, s, g, b_dev, iface, u, P.phase, grad);
+  }
+  ho_ghost(P, u, true, s);                        // ghost values with the problem's data
+  StencilCoef C;
+  GhostParams GP;
+  CorrectParams CP;
+  eng_operator_params(P, &C, &GP, &CP);
+  CP.with_data = 1;
+  if (P.aff_cap > 0) IIM_LAUNCH(k_grad_correct, ceil_div(P.aff_cap, 64), 64, 0, s, CP, b_dev, u, grad);
+  return IIM_OK;
+}
+
 }  // namespace iim

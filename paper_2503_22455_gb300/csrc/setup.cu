@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(kFitThreads) k_fit(FitParams P, const int* __r
     __syncthreads();
     if (!s_ok) continue;
     // stencil rows: warp t < w -> ghost t, warp w -> normal derivative (n out of Omega+)
-    const int nt = (P.bc == IIM_BC_DIRICHLET) ? P.w : P.w + 1;
+    const int nt = P.w + 1;                // ghosts and the normal derivative (every condition)
     if (wid < nt) {
       double* y = Y + wid * M;
       double* s = S + wid * LD;
@@ -445,6 +445,9 @@ __global__ void __launch_bounds__(kFitThreads) k_fit(FitParams P, const int* __r
         coef[(size_t)k * P.rcap + al] = S[k * LD + 1 + al] - S[k * LD] * (P.beta_p * S[P.w * LD + 1 + al]) / Dc;
       }
       if (tid < P.w) cdat[tid] = S[tid * LD] / Dc;
+      // row w: the control value itself, u_c = (qbar - sum D_i u_i) / D_c (Eq. 6)
+      for (int e = tid; e < R; e += kFitThreads) coef[(size_t)P.w * P.rcap + e] = -(P.beta_p * S[P.w * LD + 1 + e]) / Dc;
+      if (tid == 0) cdat[P.w] = 1.0 / Dc;
     } else {
       for (int e = tid; e < nt * R; e += kFitThreads) {
         int k = e / R, al = e - k * R;
@@ -637,7 +640,7 @@ __global__ void __launch_bounds__(128) k_fit_warp(FitParams P, WarpFitSmem L, in
     }
     if (!ok) continue;
     // stencil rows: quarter-warp t < nt solves for target t (ghost t < w, derivative t = w)
-    const int nt = (P.bc == IIM_BC_DIRICHLET) ? P.w : P.w + 1;
+    const int nt = P.w + 1;                // ghosts and the normal derivative (every condition)
     const int t = lane >> 3, ql = lane & 7;
     double* y = Y + t * M;
     double* srow = S + t * LDW;
@@ -706,6 +709,8 @@ __global__ void __launch_bounds__(128) k_fit_warp(FitParams P, WarpFitSmem L, in
         coef[(size_t)k * P.rcap + al] = S[k * LDW + 1 + al] - S[k * LDW] * (P.beta_p * S[P.w * LDW + 1 + al]) / Dc;
       }
       if (lane < P.w) cdat[lane] = S[lane * LDW] / Dc;
+      for (int e = lane; e < R; e += 32) coef[(size_t)P.w * P.rcap + e] = -(P.beta_p * S[P.w * LDW + 1 + e]) / Dc;
+      if (lane == 0) cdat[P.w] = 1.0 / Dc;
     } else {
       for (int e = lane; e < nt * R; e += 32) {
         const int k = e / R, al = e - k * R;
@@ -916,7 +921,7 @@ __global__ void __launch_bounds__(32) k_fit_quad(FitParams P, QuadFitSmem Lq, in
   for (int k = ql; k < M; k += 8) ialpha[k] = active ? 1.0 / alpha[k] : 0.0;
   __syncwarp();
   // stencil rows of all targets together (rows over the 8 lanes)
-  const int nt = (P.bc == IIM_BC_DIRICHLET) ? P.w : P.w + 1;
+  const int nt = P.w + 1;                // ghosts and the normal derivative (every condition)
   for (int t = 0; t < nt; ++t) {
     double* y = Y + t * M;
     if (t < P.w) {
@@ -997,6 +1002,8 @@ __global__ void __launch_bounds__(32) k_fit_quad(FitParams P, QuadFitSmem Lq, in
       coef[(size_t)k * P.rcap + al] = S[k * LDQ + 1 + al] - S[k * LDQ] * (P.beta_p * S[P.w * LDQ + 1 + al]) / Dc;
     }
     if (ql < P.w) cdat[ql] = S[ql * LDQ] / Dc;
+    for (int e = ql; e < R; e += 8) coef[(size_t)P.w * P.rcap + e] = -(P.beta_p * S[P.w * LDQ + 1 + e]) / Dc;
+    if (ql == 0) cdat[P.w] = 1.0 / Dc;
   } else {
     for (int e = ql; e < nt * R; e += 8) {
       const int k = e / R, al = e - k * R;
@@ -1014,6 +1021,10 @@ struct SWParams {
   Geom G;
   int interface_, bc, box_bc;
   double beta_p, beta_m;
+  // finest level only (else null): every cut edge is a control point whose root t is known
+  const int32_t* edge_id;
+  const double* cr_t;
+  int cr_cap;
 };
 
 // side kinds
@@ -1035,8 +1046,14 @@ __device__ inline void sw_side(const SWParams& P, const uint8_t* phase, int64_t 
   int64_t lower = s > 0 ? i : nb;
   int ml[3];
   node_index(g, lower, ml);
-  double x0[3] = {node_x(g, ml[0]), node_x(g, ml[1]), g.dim > 2 ? node_x(g, ml[2]) : 0.0};
-  double t = edge_root(P.G, x0, ax, g.h, g.dim);
+  double t;
+  const int c = P.cr_t ? P.edge_id[(int64_t)ax * g.N + lower] : -1;
+  if (c >= 0 && c < P.cr_cap) {
+    t = P.cr_t[c];                     // the same root k_crossings found on this edge
+  } else {
+    double x0[3] = {node_x(g, ml[0]), node_x(g, ml[1]), g.dim > 2 ? node_x(g, ml[2]) : 0.0};
+    t = edge_root(P.G, x0, ax, g.h, g.dim);
+  }
   double dist = s > 0 ? t : 1.0 - t;
   kind = P.bc == IIM_BC_DIRICHLET ? S_DIR : S_NEU;
   psi = fmax(dist, 0.5);               // intersections closer than h/2 are shifted (Sec. 3.1)
@@ -1124,6 +1141,8 @@ static Geom make_geom(const iim_problem_desc& d) {
   G.dim = d.dim;
   G.sign = d.plus_inside ? -1.0 : 1.0;
   for (int k = 0; k < 8; ++k) G.p[k] = d.geom_params[k];
+  G.cs = std::cos(d.geom_params[4]);    // used by the ellipse only
+  G.sn = std::sin(d.geom_params[4]);
   return G;
 }
 
@@ -1235,7 +1254,12 @@ iim_status setup_levels(Problem& P, bool size_only) {
   for (size_t l = 0; l < P.lv.size(); ++l) {
     Level& L = P.lv[l];
     SWParams S{L.g, P.geom, P.desc.bc == IIM_BC_INTERFACE, P.desc.bc, P.desc.box_bc, P.desc.beta_plus,
-               P.desc.beta_minus};
+               P.desc.beta_minus, nullptr, nullptr, 0};
+    if (l == 0 && !size_only && P.cr_t) {
+      S.edge_id = P.edge_id;
+      S.cr_t = P.cr_t;
+      S.cr_cap = P.K_cap;
+    }
     if (l > 0) IIM_LAUNCH(k_phase, ceil_div(L.g.N, T), T, 0, P.stream, P.geom, L.g, L.phase);
     IIM_LAUNCH(k_sw_classify, ceil_div(L.g.N, T), T, 0, P.stream, S, L.phase, L.aux, L.flag, P.d_status);
     scan_exclusive(L.flag, L.idx, L.g.N, P.d_counts + 2 + (int)l, P.scan_scratch, P.stream);
