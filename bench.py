@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--no-roofline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="host-driven FGMRES loop (for kernel-level profiling)")
     ap.add_argument("--batch", type=int, default=8, help="independent problems solved concurrently per step")
-    ap.add_argument("--solver", default="engine", choices=["engine", "pool"],
+    ap.add_argument("--solver", default="pool", choices=["engine", "pool"],
                     help="engine: the batch advances in lock step through the batched engine; pool: one solve "
                          "graph per problem on a pool of streams")
     ap.add_argument("--workload", default="star1024", choices=["star1024", "batch512", "serve", "ellipsoid256"],
@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
     ap.add_argument("--ticks-per-run", type=int, default=4, help="serve: engine ticks between admissions")
     ap.add_argument("--slots", type=int, default=256, help="serve: problems resident at once at most")
+    ap.add_argument("--serve-mode", type=int, default=1, choices=[0, 1],
+                    help="serve: 0 batched engine, 1 each request's solve graph on its own stream")
     ap.add_argument("--engines", type=int, default=2,
                     help="batched engines, each on its own stream with a share of the problems")
     return ap.parse_args()
@@ -276,6 +278,7 @@ def run_batch(args):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     iters, ticks, launches = [], [], 0
     split.clear()
+    torch.cuda.nvtx.range_push("timed")
     for k in range(K):
         flush.zero_()
         ev[k][0].record(main)
@@ -288,6 +291,7 @@ def run_batch(args):
                 raise RuntimeError(f"batch step {k}: {inf.as_dict()}")
             iters.append(inf.iters)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     clk = clocks.stop()
     total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world)
     value = whole_job_rate(count * K, world, total_ms)
@@ -349,10 +353,12 @@ def run_serve(args):
         view.set_data(f, g, None, None, box)
 
     # warm-up: a few requests through a separate server (library, kernels, allocator)
-    warm = iim.Server(opts, budget_bytes=budget, max_slots=args.slots, ticks_per_run=args.ticks_per_run)
+    warm = iim.Server(opts, budget_bytes=budget, max_slots=args.slots, ticks_per_run=args.ticks_per_run,
+                      mode=args.serve_mode)
     iim.serve(warm, [(0.0, iim.desc_from_spec(sp), sp) for _, sp in trace[:8]], set_data, realtime=False)
     warm.close()
-    S = iim.Server(opts, budget_bytes=budget, max_slots=args.slots, ticks_per_run=args.ticks_per_run)
+    S = iim.Server(opts, budget_bytes=budget, max_slots=args.slots, ticks_per_run=args.ticks_per_run,
+                   mode=args.serve_mode)
     clocks = Clocks(local)
     clocks.start()
     arrivals = [(t, iim.desc_from_spec(sp), sp) for t, sp in trace]
@@ -369,7 +375,8 @@ def run_serve(args):
         "dtype": "f64", "mg_dtype": "f32", "data": "synthetic",
         "config": {"workload": f"serve_poisson_{count}", "rate_per_s": args.rate, "requests": count,
                    "mix": "75% 2D stars n 128..1024, 25% 3D ellipsoids n 64..192; Dirichlet / Neumann; (4,5)/(6,7) 2D",
-                   "budget_bytes": budget, "slots": args.slots, "ticks_per_run": args.ticks_per_run, "tol": 1e-10},
+                   "budget_bytes": budget, "slots": args.slots, "ticks_per_run": args.ticks_per_run, "tol": 1e-10,
+                   "solver": "batched engine" if args.serve_mode == 0 else "per-request solve graphs on streams"},
         "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
         "mean_latency_s": float(lat.mean()), "wall_s": wall, "completed": len(ok), "failed": len(err),
         "offered_rate": count / trace[-1][0], "peak_bytes": stats["peak_bytes"], "engine_runs": stats["runs"],
@@ -663,9 +670,20 @@ def e2e_run(probs, torch, inputs, Wm, K, world, main):
             "d2h_bytes_per_step": probs[0].N * 8 * len(probs)}
 
 
-# DRAM bytes per launch from the ncu capture summarised in profiles/ (None once the
-# kernel changed after the capture)
-NCU_TRAFFIC = {}
+def ncu_traffic():
+    """DRAM bytes (read + write) per launch of each profiled kernel, from the ncu captures
+    summarised in profiles/ (lines "traffic_bytes_per_launch: <kernel> <bytes>")."""
+    out = {}
+    d = os.path.join(ROOT, "profiles")
+    for name in sorted(os.listdir(d)) if os.path.isdir(d) else []:
+        try:
+            for line in open(os.path.join(d, name)):
+                if line.startswith("traffic_bytes_per_launch:"):
+                    parts = line.split()
+                    out[parts[1]] = float(parts[2])
+        except (OSError, ValueError, IndexError):
+            continue
+    return out
 
 
 def roofline(P, iim, torch, stream, applies_per_solve):
@@ -707,7 +725,7 @@ def roofline(P, iim, torch, stream, applies_per_solve):
                 "flop_per_launch": r["flop"], "us_per_solve": r["us_per_solve"]}
 
     return {"kernel": top["kernel"], "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s (FP64)",
-            "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(top["kernel"]), "us_per_launch": top["us"],
+            "frac": achieved / peak, "traffic": ncu_traffic().get(top["kernel"]), "us_per_launch": top["us"],
             "flop_per_launch": top["flop"],
             "peak_note": "derived FP64 peak: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock (measured 0.598 TFMA/s "
                          "at 1.995 GHz agrees); the measured copy and bf16 peaks do not apply to FP64 work",

@@ -292,6 +292,13 @@ iim_status iim_server_create(const iim_options* opt, size_t hbm_budget, int max_
 /* Frees every request still held (running solves are cancelled). */
 void iim_server_destroy(iim_server* s);
 
+/* How admitted requests are solved (before the first submission): 0 = in the
+ * batched engine, advanced together one FGMRES step per tick; 1 = each request's
+ * own solve graph (captured by the creation thread) on its own stream, up to
+ * max_slots at once, overlapping on the device.  Results are the same either way
+ * and independent of the other requests. */
+iim_status iim_server_set_mode(iim_server* s, int mode);
+
 /* Queue a request; *id identifies it.  IIM_ERR_BUDGET if it alone exceeds the budget. */
 iim_status iim_server_submit(iim_server* s, const iim_problem_desc* desc, int64_t* id);
 

@@ -95,6 +95,7 @@ SIGNATURES = {
     "iim_server_create": (ctypes.c_int, [ctypes.POINTER(Options), ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "iim_server_destroy": (None, [ctypes.c_void_p]),
+    "iim_server_set_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "iim_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Desc), ctypes.POINTER(ctypes.c_int64)]),
     "iim_server_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
@@ -453,13 +454,15 @@ class Server:
     """Request loop over an engine (see iim.h): submit, step, set data, take."""
 
     def __init__(self, options: Options | None = None, budget_bytes: int = 1 << 34, max_slots: int = 64,
-                 ticks_per_run: int = 4, cap: int = 4096, create_threads: int = 8):
+                 ticks_per_run: int = 4, cap: int = 4096, create_threads: int = 8, mode: int = 0):
         lib = load()
         self.options = options or default_options()
         h = ctypes.c_void_p()
         _check(lib.iim_server_create(ctypes.byref(self.options), ctypes.c_size_t(int(budget_bytes)), int(max_slots),
                                      int(ticks_per_run), int(create_threads), ctypes.byref(h)), "iim_server_create")
         self.h = h
+        _check(lib.iim_server_set_mode(self.h, int(mode)), "iim_server_set_mode")
+        self.mode = mode
         self.cap = cap
         self._need = (ctypes.c_int64 * cap)()
         self._fin = (ctypes.c_int64 * cap)()

@@ -645,6 +645,26 @@ static iim_status finish_info(Problem& P, iim_solve_info* info) {
   return st;
 }
 
+}  // extern "C"
+
+namespace iim {
+// asynchronous solve of the problem's own data from x = 0 on its stream (request loop)
+iim_status solve_async(Problem& P) {
+  cudaMemsetAsync(P.x, 0, sizeof(double) * (P.g.N + P.aug), P.stream);
+  cudaEventRecord(P.ev0, P.stream);
+  iim_status st = solve_enqueue(P, P.stream);
+  cudaEventRecord(P.ev1, P.stream);
+  return st;
+}
+iim_status solve_finish(Problem& P, iim_solve_info* info) {
+  cudaStreamSynchronize(P.stream);
+  if (cuda_check("solve") != IIM_OK) return IIM_ERR_CUDA;
+  return finish_info(P, info);
+}
+}  // namespace iim
+
+extern "C" {
+
 iim_status iim_solve(iim_problem* H, double* x, iim_solve_info* info) {
   if (!H || !x) return IIM_ERR_INVALID_ARG;
   Problem& P = H->P;

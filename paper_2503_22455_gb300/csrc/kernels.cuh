@@ -209,6 +209,8 @@ void krylov_orth_pass(Problem& P, int j, int which, cudaStream_t s);
 
 // api.cu
 void* dev_alloc(Problem& P, size_t bytes);
+iim_status solve_async(Problem& P);
+iim_status solve_finish(Problem& P, iim_solve_info* info);
 int rows_cap(int dim, int q);                  // least-squares rows reserved per fit
 void set_error(const std::string& msg);
 

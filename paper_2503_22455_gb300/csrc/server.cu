@@ -36,6 +36,12 @@ static size_t estimate_bytes(const iim_problem_desc& d, const iim_options& o) {
 
 using Clock = std::chrono::steady_clock;
 
+}  // namespace iim
+struct iim_problem {
+  iim::Problem P;
+};
+namespace iim {
+
 enum ReqState { kQueued = 0, kCreating, kNeedData, kReady, kRunning, kRetired, kFinished, kFailed };
 
 struct Request {
@@ -70,6 +76,8 @@ struct Server {
   bool run_in_flight = false;
   int resident = 0;
   int64_t runs = 0;
+  int mode = 0;                  // 0: batched engine, 1: each request's solve graph on its own stream
+  std::vector<Request*> running;  // mode 1
   double t_step = 0, t_copy = 0, t_create = 0;   // host seconds: step calls, result copies, creation (workers)
   Clock::time_point t0;
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
@@ -100,6 +108,14 @@ static void create_worker(Server* S) {
     const auto t = Clock::now();
     r->create_status = iim_problem_create(&r->desc, &S->opt, r->stream, &r->prob);
     if (r->create_status != IIM_OK) r->prob = nullptr;
+    // streams mode: capture the request's solve graph here, off the loop's thread
+    if (r->prob && S->mode == 1 && S->opt.use_graph) {
+      r->create_status = krylov_build_graph(r->prob->P, r->prob->P.x);
+      if (r->create_status != IIM_OK) {
+        iim_problem_destroy(r->prob);
+        r->prob = nullptr;
+      }
+    }
     const double dt = std::chrono::duration<double>(Clock::now() - t).count();
     std::lock_guard<std::mutex> lk(S->mu);
     S->t_create += dt;
@@ -111,9 +127,6 @@ static void create_worker(Server* S) {
 
 using namespace iim;
 
-struct iim_problem {
-  Problem P;
-};
 struct iim_server {
   Server S;
 };
@@ -210,8 +223,22 @@ iim_status iim_server_step(iim_server* H, int64_t* need_data, int cap_need, int*
   const auto t_enter = Clock::now();
   int nn = 0, nf = 0;
   std::vector<Request*> retired;
+  // 1. finished solves: in streams mode, every running request whose solve graph is done
+  if (S.mode == 1) {
+    for (size_t k = 0; k < S.running.size();) {
+      Request* r = S.running[k];
+      if (cudaEventQuery(r->prob->P.ev1) == cudaErrorNotReady) { ++k; continue; }
+      cudaGetLastError();
+      solve_finish(r->prob->P, &r->info);
+      r->state = kRetired;
+      --S.resident;
+      retired.push_back(r);
+      S.running[k] = S.running.back();
+      S.running.pop_back();
+    }
+  }
   // 1. the last run: release the slots that finished
-  if (S.run_in_flight) {
+  if (S.mode == 0 && S.run_in_flight) {
     int nd = 0;
     iim_status st = iim_engine_poll(S.engine, 0, nullptr, S.done_buf.data(), &nd, nullptr);
     if (st == IIM_OK) {
@@ -230,8 +257,27 @@ iim_status iim_server_step(iim_server* H, int64_t* need_data, int cap_need, int*
       return st;
     }
   }
+  // 2 (streams mode). launch the solves of ready requests while slots are free
+  if (S.mode == 1) {
+    for (auto& kv : S.reqs) {
+      Request* r = kv.second;
+      if (r->state != kReady || S.resident >= S.max_slots) continue;
+      iim_status st = solve_async(r->prob->P);
+      if (st != IIM_OK) {
+        r->state = kFailed;
+        r->error = st;
+        r->t_done = S.now();
+        free_problem(S, r);
+        if (finished && nf < cap_fin) finished[nf++] = r->id;
+        continue;
+      }
+      r->state = kRunning;
+      ++S.resident;
+      S.running.push_back(r);
+    }
+  }
   // 2. join the requests whose data are set, and launch the next run
-  if (!S.run_in_flight) {
+  if (S.mode == 0 && !S.run_in_flight) {
     for (auto& kv : S.reqs) {
       Request* r = kv.second;
       if (r->state != kReady) continue;
@@ -342,6 +388,12 @@ iim_status iim_server_step(iim_server* H, int64_t* need_data, int cap_need, int*
   S.t_step += std::chrono::duration<double>(Clock::now() - t_enter).count();
   if (n_need) *n_need = nn;
   if (n_fin) *n_fin = nf;
+  return IIM_OK;
+}
+
+iim_status iim_server_set_mode(iim_server* H, int mode) {
+  if (!H || mode < 0 || mode > 1 || !H->S.reqs.empty()) return IIM_ERR_INVALID_ARG;
+  H->S.mode = mode;
   return IIM_OK;
 }
 

@@ -25,8 +25,8 @@ def env():
     return need_gpu()
 
 
-def _serve(iim, specs, budget, ticks_per_run=3):
-    S = iim.Server(iim.default_options(), budget_bytes=budget, max_slots=8, ticks_per_run=ticks_per_run)
+def _serve(iim, specs, budget, ticks_per_run=3, mode=0):
+    S = iim.Server(iim.default_options(), budget_bytes=budget, max_slots=8, ticks_per_run=ticks_per_run, mode=mode)
     arrivals = [(0.0, iim.desc_from_spec(sp), sp) for sp in specs]
     out, wall = iim.serve(S, arrivals, lambda view, sp: set_gpu_data(view, sp), realtime=False)
     stats = S.stats()
@@ -34,7 +34,10 @@ def _serve(iim, specs, budget, ticks_per_run=3):
     return [out[rid] for rid in sorted(out)], stats
 
 
-def test_served_results_equal_alone_and_single_solves(env):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_served_results_equal_alone_and_single_solves(env, mode):
+    """mode 0: requests advance together in the batched engine; mode 1: each request's
+    solve graph on its own stream."""
     torch, iim = env
     specs = [sp for _, sp in _trace()]
     assert any(sp.dim == 3 for sp in specs) and any(sp.dim == 2 for sp in specs)
@@ -45,15 +48,15 @@ def test_served_results_equal_alone_and_single_solves(env):
         sizes.append(P.device_bytes())
         P.close()
     budget = int(2.5 * max(sizes))
-    mixed, stats = _serve(iim, specs, budget)
+    mixed, stats = _serve(iim, specs, budget, mode=mode)
     assert stats["peak_bytes"] <= budget
-    assert stats["runs"] > 3
+    assert stats["runs"] > 3 or mode == 1
     assert len(mixed) == len(specs)
     for (x, info, lat, st, sp) in mixed:
         assert st == 0 and info.converged and info.relres <= 1e-10, (sp.name, info.as_dict())
         assert lat > 0
     for (x, info, lat, st, sp) in mixed:
-        (alone,), _ = _serve(iim, [sp], 1 << 36)
+        (alone,), _ = _serve(iim, [sp], 1 << 36, mode=mode)
         assert np.array_equal(alone[0], x), sp.name
         assert alone[1].iters == info.iters
     # and the plain single solve of two of them
