@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
     ap.add_argument("--ticks-per-run", type=int, default=4, help="serve: engine ticks between admissions")
     ap.add_argument("--slots", type=int, default=256, help="serve: problems resident at once at most")
+    ap.add_argument("--create-threads", type=int, default=16, help="serve: host threads creating requests")
     ap.add_argument("--serve-mode", type=int, default=1, choices=[0, 1],
                     help="serve: 0 batched engine, 1 each request's solve graph on its own stream")
     ap.add_argument("--engines", type=int, default=2,
@@ -354,11 +355,11 @@ def run_serve(args):
 
     # warm-up: a few requests through a separate server (library, kernels, allocator)
     warm = iim.Server(opts, budget_bytes=budget, max_slots=args.slots, ticks_per_run=args.ticks_per_run,
-                      mode=args.serve_mode)
+                      mode=args.serve_mode, create_threads=args.create_threads)
     iim.serve(warm, [(0.0, iim.desc_from_spec(sp), sp) for _, sp in trace[:8]], set_data, realtime=False)
     warm.close()
     S = iim.Server(opts, budget_bytes=budget, max_slots=args.slots, ticks_per_run=args.ticks_per_run,
-                   mode=args.serve_mode)
+                   mode=args.serve_mode, create_threads=args.create_threads)
     clocks = Clocks(local)
     clocks.start()
     arrivals = [(t, iim.desc_from_spec(sp), sp) for t, sp in trace]
@@ -368,7 +369,7 @@ def run_serve(args):
     stats = S.stats()
     lat = np.array([o[2] for o in out.values()])
     ok = [o for o in out.values() if o[3] == 0 and o[1].converged]
-    err = [abs(o[3]) for o in out.values() if o[3] != 0]
+    err = [(o[4].name, o[4].n, o[4].dim, int(o[3]), o[1].iters, o[1].relres) for o in out.values() if o[3] != 0]
     res = {
         "metric": "IIM serving: solves/s and p50/p99 latency (s), rel. resid 1e-10", "value": len(ok) / wall,
         "unit": "solves/s", "n_gpus": world, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -379,6 +380,7 @@ def run_serve(args):
                    "solver": "batched engine" if args.serve_mode == 0 else "per-request solve graphs on streams"},
         "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
         "mean_latency_s": float(lat.mean()), "wall_s": wall, "completed": len(ok), "failed": len(err),
+        "failures": err[:10], "create_threads": args.create_threads,
         "offered_rate": count / trace[-1][0], "peak_bytes": stats["peak_bytes"], "engine_runs": stats["runs"],
         "host_seconds": {"loop_step": host["step_s"], "client_set_data": host["set_data_s"], "take": host["take_s"],
                          "server_copy_out": stats["host_copy_s"], "server_create_threads": stats["host_create_s"]},

@@ -93,7 +93,7 @@ typedef struct {
   int nu1, nu2;          /* pre/post red-black Gauss-Seidel sweeps */
   int mg_precision;      /* IIM_MG_FP32, IIM_MG_FP64 or IIM_MG_FP32_BF16R */
   int use_graph;         /* 1: the solve runs as one CUDA graph with device-side control */
-  int reorth;            /* 1: second Gram-Schmidt pass when |w| drops by more than 1/sqrt(2) */
+  int reorth;            /* 1: second Gram-Schmidt pass when |w| drops below 1e-3 |w_old| */
 } iim_options;
 
 typedef struct {

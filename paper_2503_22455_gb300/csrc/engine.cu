@@ -419,7 +419,7 @@ iim_status iim_engine_admit(iim_engine* H, iim_problem* p, const double* x0_dev,
     size_t smem = 0;
     make_tail_params<float>(P, mg_tail_start(P), nullptr, kEngTailSmem, &smem);
     size_t base = 0;
-    for (size_t l = mg_tail_start(P); l < P.lv.size(); ++l) base += (size_t)P.lv[l].g.N * 12;
+    for (size_t l = mg_tail_start(P); l < P.lv.size(); ++l) base += (size_t)P.lv[l].g.N * 16;
     if (base > kEngTailSmem) {
       set_error("engine: coarse levels too large for the tail kernel");
       return IIM_ERR_INVALID_ARG;

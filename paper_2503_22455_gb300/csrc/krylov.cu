@@ -5,8 +5,8 @@
 //   w   = L z_j                  the IIM operator              (operator.cu)
 //   h   = V^T w, |w|^2           one fused pass over v_0..v_j  (k_multidot)
 //   w  -= V h, |w|^2             one fused pass                (k_update)
-//   optional second pass when |w| dropped below |w_old|/sqrt(2)   (classical
-//   Gram-Schmidt with re-orthogonalisation)
+//   optional second pass when |w| dropped below 1e-3 |w_old|   (classical
+//   Gram-Schmidt with re-orthogonalisation on severe cancellation)
 //   Givens rotation, Arnoldi residual estimate, flags         (k_arnoldi_step)
 // v_{j+1} is kept unnormalised; 1/|v_{j+1}| is applied inside the kernels that
 // read it.  Reductions are deterministic: per-block partials in a fixed grid,
@@ -240,7 +240,10 @@ __device__ inline void update_body(double* __restrict__ V, int64_t Np, int j, in
     *counter = 0;
     S->w2 = tot[0];
     if (!second) {
-      S->reorth_needed = S->reorth && (tot[0] < 0.5 * S->w2_old);
+      // second pass only on severe cancellation, |w| < 1e-3 |w_old| (a DGKS test with a small eta:
+      // with the multigrid preconditioner |w| drops below |w_old|/sqrt(2) at every iteration,
+      // yet one pass gives the same iterates' quality and iteration counts)
+      S->reorth_needed = S->reorth && (tot[0] < 1e-6 * S->w2_old);
     } else {
       for (int k = 0; k < nv; ++k) S->hcol[k] += S->y[k];
       S->reorth_needed = 0;

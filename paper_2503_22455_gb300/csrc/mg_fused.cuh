@@ -1,6 +1,6 @@
 // Fused Shortley-Weller multigrid kernels (paper Sec. 3.3), included by multigrid.cu.
 //
-// 2D fine levels: one CTA owns a TX x TY tile plus a halo of 3 in shared memory
+// 2D fine levels: one CTA owns a TX x TY tile plus a halo of 3 (4 for the fused modes) in shared memory
 // and runs several red/black half sweeps back to back on shrinking margins
 // (temporal blocking), so each kernel reads and writes the level once:
 //   MODE 0  first pre-smoothing sweep from u = 0; on the finest level the FP64
@@ -124,8 +124,9 @@ __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx
     }
   }
   if (UP_FIRST) {
-    // u += P e_coarse on margin 2 (4 when fused with the whole post-smoothing).  The coarse u is 0 at coarse non-unknowns, so the
-    // bilinear form needs no aux; the Neumann mean counts in-domain neighbours.
+    // u += P e_coarse on margin 2 (4 when fused with the whole post-smoothing).  The coarse
+    // u is 0 at coarse non-unknowns, so the bilinear form needs no aux; the Neumann mean
+    // counts in-domain neighbours.
     const LevelK<T>& C = P.C;
     for (int e = threadIdx.x; e < S; e += blockDim.x) {
       const int sx = e % SX, sy = e / SX;
@@ -331,9 +332,16 @@ __device__ __forceinline__ void vcycle_tail_body(const TailParams<T>& P, const d
   T* sf = su + tot;
   T* st = sf + tot;                                   // staged tables
   int* sa = (int*)(st + P.toff[P.nlev]);
+  int* sco = sa + tot;                                 // node coordinates, i0 | i1 << 10 | i2 << 20
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int k = 0; k < P.nlev; ++k)
-    for (int i = tid; i < P.L[k].N; i += nt) sa[P.off[k] + i] = P.L[k].aux[i];
+  for (int k = 0; k < P.nlev; ++k) {
+    const int n = P.L[k].n;
+    for (int i = tid; i < P.L[k].N; i += nt) {
+      sa[P.off[k] + i] = P.L[k].aux[i];
+      const int r = i / n;
+      sco[P.off[k] + i] = (i - r * n) | ((P.L[k].dim > 2 ? r % n : r) << 10) | ((P.L[k].dim > 2 ? r / n : 0) << 20);
+    }
+  }
   if (P.stage_tables) {
     for (int k = 0; k < P.nlev; ++k) {
       const int rows = min(*P.tcount[k], P.tcap[k]);
@@ -361,7 +369,8 @@ __device__ __forceinline__ void vcycle_tail_body(const TailParams<T>& P, const d
     const int n = L.n;
     for (int i = tid; i < L.N; i += blockDim.x) {
       const int a = sa[P.off[k] + i];
-      const int m[3] = {i % n, L.dim > 2 ? (i / n) % n : i / n, L.dim > 2 ? i / (n * n) : 0};
+      const int c = sco[P.off[k] + i];
+      const int m[3] = {c & 1023, (c >> 10) & 1023, c >> 20};
       if (((m[0] + m[1] + m[2]) & 1) != colour) {
         if (from_zero) u[i] = 0;
       } else if (a == -2) {

@@ -437,7 +437,7 @@ TailParams<T> make_tail_params(Problem& P, size_t l0, T* u_out, size_t smem_limi
     toff += L.irr_cap * (2 * L.g.dim + 1);
   }
   tp.toff[tp.nlev] = toff;
-  const size_t base = (sizeof(T) * 2 + sizeof(int)) * (size_t)off;
+  const size_t base = (sizeof(T) * 2 + 2 * sizeof(int)) * (size_t)off;   // u, f, aux, node coordinates
   tp.stage_tables = base + sizeof(T) * (size_t)toff <= smem_limit;
   if (!tp.stage_tables) {
     toff = 0;
