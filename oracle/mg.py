@@ -35,10 +35,11 @@ def level_sizes(n: int, dim: int):
 
 
 class Multigrid:
-    def __init__(self, ls, n, bc, box_bc, beta_p, beta_m, nu1=2, nu2=2):
+    def __init__(self, ls, n, bc, box_bc, beta_p, beta_m, nu1=2, nu2=2, gamma=1):
         self.dim = ls.dim
         self.bc = bc
         self.nu1, self.nu2 = nu1, nu2
+        self.gamma = gamma                   # 1: V-cycle, 2: W-cycle
         self.sizes = level_sizes(n, ls.dim)
         self.levels = [SWLevel(ls, m, bc, box_bc, beta_p, beta_m) for m in self.sizes]
         self.beta_p, self.beta_m = beta_p, beta_m
@@ -128,18 +129,23 @@ class Multigrid:
             u[self.c_unk] = sla.lu_solve(self.c_lu, rhs)[:self.c_unk.size]
         return u
 
-    def vcycle(self, f, lev=0):
+    def vcycle(self, f, lev=0, u0=None):
+        """One cycle on level lev for L u = f, from u0 (zero if None).  gamma = 1 is the
+        V-cycle; gamma = 2 the W-cycle (Sec. 3.3 results): the coarser level is visited
+        twice, the second visit starting from the first visit's result."""
         L = self.levels[lev]
         if lev == len(self.levels) - 1:
             return self.coarse_solve(f)
-        u = np.zeros_like(f)
+        u = np.zeros_like(f) if u0 is None else u0.copy()
         for _ in range(self.nu1):
             L.gs_colour(u, f, 0)
             L.gs_colour(u, f, 1)
         r = f - L.apply(u)
         r[~L.unk_flat] = 0.0
         fc = self.restrict(r, L, self.levels[lev + 1])
-        ec = self.vcycle(fc, lev + 1)
+        ec = None
+        for _ in range(self.gamma):
+            ec = self.vcycle(fc, lev + 1, ec)
         u += self.prolong(ec, self.levels[lev + 1], L)
         for _ in range(self.nu2):
             L.gs_colour(u, f, 0)
@@ -147,7 +153,7 @@ class Multigrid:
         return u
 
     def precondition(self, v, plus_flat):
-        """z = V-cycle applied to v / beta_sigma (Sec. 3.3, interface and boundary alike)."""
+        """z = one cycle applied to v / beta_sigma (Sec. 3.3, interface and boundary alike)."""
         f = v / np.where(plus_flat, self.beta_p, self.beta_m)
         f[~self.levels[0].unk_flat] = 0.0
         return self.vcycle(f)

@@ -10,7 +10,7 @@ from .operator import IIMOperator
 
 
 class OracleProblem:
-    def __init__(self, spec, nu1=2, nu2=2, check_curvature=True):
+    def __init__(self, spec, nu1=2, nu2=2, check_curvature=True, gamma=1):
         self.spec = spec
         self.op = IIMOperator(spec, check_curvature=check_curvature)
         self.n, self.d = spec.n, spec.dim
@@ -18,12 +18,14 @@ class OracleProblem:
         self.unk_flat = self.op.unknown.ravel(order="F")
         self._mg = None
         self.nu1, self.nu2 = nu1, nu2
+        self.gamma = gamma
 
     @property
     def mg(self):
         if self._mg is None:
             s = self.spec
-            self._mg = Multigrid(self.op.ls, s.n, s.bc, s.box_bc, s.beta_plus, s.beta_minus, self.nu1, self.nu2)
+            self._mg = Multigrid(self.op.ls, s.n, s.bc, s.box_bc, s.beta_plus, s.beta_minus, self.nu1, self.nu2,
+                                 self.gamma)
         return self._mg
 
     def data(self, spec=None):
@@ -50,6 +52,15 @@ class OracleProblem:
 
     def precondition(self, v):
         return self.mg.precondition(v, self.plus_flat)
+
+    def solve_left(self, f, data, tol=None, restart=10, max_iter=1000):
+        """Left-preconditioned GMRES (the paper's 2D solver, Sec. 3.2) with its stopping rule:
+        |M^-1 r| <= tol |M^-1 b|, tol = 1e-6 / N_x by default."""
+        from .fgmres import gmres_left
+        b = self.op.rhs(f, data)
+        tol = 1e-6 / self.n if tol is None else tol
+        x, info = gmres_left(self.op.apply, self.precondition, b, tol=tol, restart=restart, max_iter=max_iter)
+        return x, info, b
 
     @property
     def singular(self):
