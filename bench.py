@@ -39,7 +39,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=3,
+                    help="steps of each other solver form (FP64 multigrid, W-cycle, left GMRES); 0: none")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-roofline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="host-driven FGMRES loop (for kernel-level profiling)")
@@ -56,6 +57,8 @@ def parse():
     ap.add_argument("--ticks-per-run", type=int, default=4, help="serve: engine ticks between admissions")
     ap.add_argument("--slots", type=int, default=256, help="serve: problems resident at once at most")
     ap.add_argument("--create-threads", type=int, default=16, help="serve: host threads creating requests")
+    ap.add_argument("--serve-deadline", type=float, default=300.0,
+                    help="serve: fail (with the requests' states) when requests are outstanding after this many s")
     ap.add_argument("--serve-mode", type=int, default=1, choices=[0, 1],
                     help="serve: 0 batched engine, 1 each request's solve graph on its own stream")
     ap.add_argument("--engines", type=int, default=2,
@@ -356,7 +359,12 @@ def run_serve(args):
     # warm-up: a few requests through a separate server (library, kernels, allocator)
     warm = iim.Server(opts, budget_bytes=budget, max_slots=args.slots, ticks_per_run=args.ticks_per_run,
                       mode=args.serve_mode, create_threads=args.create_threads)
-    iim.serve(warm, [(0.0, iim.desc_from_spec(sp), sp) for _, sp in trace[:8]], set_data, realtime=False)
+    def note(t, taken, outstanding, st):
+        print(f"serve: {t:.0f} s, {taken} taken, {outstanding} outstanding, states {st['states']}",
+              file=sys.stderr, flush=True)
+
+    iim.serve(warm, [(0.0, iim.desc_from_spec(sp), sp) for _, sp in trace[:8]], set_data, realtime=False,
+              deadline_s=args.serve_deadline, progress=note)
     warm.close()
     S = iim.Server(opts, budget_bytes=budget, max_slots=args.slots, ticks_per_run=args.ticks_per_run,
                    mode=args.serve_mode, create_threads=args.create_threads)
@@ -364,7 +372,8 @@ def run_serve(args):
     clocks.start()
     arrivals = [(t, iim.desc_from_spec(sp), sp) for t, sp in trace]
     host = {}
-    out, wall = iim.serve(S, arrivals, set_data, realtime=True, timings=host)
+    out, wall = iim.serve(S, arrivals, set_data, realtime=True, timings=host, deadline_s=args.serve_deadline,
+                          progress=note)
     clk = clocks.stop()
     stats = S.stats()
     lat = np.array([o[2] for o in out.values()])
@@ -565,12 +574,15 @@ def run_ours(args):
     total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world)
     value = whole_job_rate(B * K, world, total_ms)
 
-    # accuracy of the last step of problem 0 against its manufactured solution
-    spec = inputs[0][2][Wm + K - 1]
-    ph = probs[0].phase().cpu().numpy().astype(bool)
-    Xn = W.node_coords(n, 2)
-    ex = W.to_flat(np.where(W.from_flat(ph, n, 2), spec.solution.u_plus(Xn), spec.solution.u_minus(Xn)))
-    err_exact = float(np.max(np.abs(xs[0].cpu().numpy() - ex)))
+    def err_of(P, x, s):
+        """max error of problem 0's solution at step s against its manufactured solution"""
+        spec = inputs[0][2][s]
+        ph = P.phase().cpu().numpy().astype(bool)
+        Xn = W.node_coords(n, 2)
+        ex = W.to_flat(np.where(W.from_flat(ph, n, 2), spec.solution.u_plus(Xn), spec.solution.u_minus(Xn)))
+        return float(np.max(np.abs(x.cpu().numpy() - ex)))
+
+    err_exact = err_of(probs[0], xs[0], Wm + K - 1)
 
     # latency of one solve (batch of one, the same problem)
     lat = []
@@ -583,9 +595,13 @@ def run_ours(args):
         torch.cuda.synchronize()
         lat.append(a.elapsed_time(b))
 
-    fp64_form = None
+    forms = {}
     if args.fp64_steps > 0:
-        fp64_form = fp64_run(args, iim, torch, specs0, streams, inputs, step, flush, Wm, main)
+        for key, kw in (("fp64_form", {"mg_precision": iim.MG_FP64}),
+                        ("w_cycle_form", {"cycle": iim.CYCLE_W}),
+                        ("left_gmres_form", {"krylov": iim.KRYLOV_GMRES_LEFT})):
+            forms[key] = form_run(args, iim, torch, specs0, streams, step, flush, Wm, main, err_of, kw)
+        forms["left_gmres_form"]["tol_on"] = "preconditioned residual |M r| / |M b|"
     e2e = None
     if not args.no_e2e:
         e2e = e2e_run(probs, torch, inputs, Wm, K, world, main)
@@ -609,7 +625,7 @@ def run_ours(args):
                    if engine is not None else "per-problem solve graphs on a stream pool"},
         "latency_ms_single_solve": statistics.median(lat),
         "iters_mean": statistics.mean(iters), "err_vs_exact": err_exact,
-        "fp64_form": fp64_form,
+        **forms,
         "e2e": e2e,
         "gpu_launches": launches,
         "roofline": roof,
@@ -626,14 +642,15 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def fp64_run(args, iim, torch, specs0, streams, inputs, step, flush, Wm, main):
-    """The all-FP64 form (FP64 multigrid), same batch and inputs."""
+def form_run(args, iim, torch, specs0, streams, step, flush, Wm, main, err_of, kw):
+    """Another form of the solver (FP64 multigrid, W-cycle or left GMRES), same batch and
+    inputs, through per-problem solve graphs (the engine runs the default form only)."""
     import statistics as st
-    opts = iim.default_options(tol=1e-10, mg_precision=iim.MG_FP64)
+    opts = iim.default_options(tol=1e-10, **kw)
     probs = [iim.Problem(iim.desc_from_spec(sp), opts, s) for sp, s in zip(specs0, streams)]
     xs = [torch.zeros(P.N, dtype=torch.float64, device="cuda") for P in probs]
-    step(0, probs, xs, use_engine=False)            # the engine runs the FP32 multigrid only
-    t, it = [], []
+    step(0, probs, xs, use_engine=False)
+    t, it, conv = [], [], True
     for k in range(args.fp64_steps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -643,9 +660,12 @@ def fp64_run(args, iim, torch, specs0, streams, inputs, step, flush, Wm, main):
         torch.cuda.synchronize()
         t.append(a.elapsed_time(b))
         it += [inf.iters for inf in infos]
+        conv = conv and all(inf.converged for inf in infos)
+    err = err_of(probs[0], xs[0], Wm + args.fp64_steps - 1)
     for P in probs:
         P.close()
-    return {"value": len(probs) * 1e3 / st.mean(t), "unit": "solves/s", "iters": st.mean(it)}
+    return {"value": len(probs) * 1e3 / st.mean(t), "unit": "solves/s", "iters": st.mean(it), "err_vs_exact": err,
+            "all_converged": conv}
 
 
 def e2e_run(probs, torch, inputs, Wm, K, world, main):

@@ -65,6 +65,14 @@ enum { IIM_BOX_NONE = 0, IIM_BOX_DIRICHLET = 1 };
 /* Multigrid precision: FP32, FP64, or FP32 with every restricted residual (the
  * right-hand side of the coarser level) rounded to BF16 where it is stored. */
 enum { IIM_MG_FP32 = 0, IIM_MG_FP64 = 1, IIM_MG_FP32_BF16R = 2 };
+/* Multigrid cycle (Sec. 3.3 results): the V-cycle visits the next coarser level once
+ * per visit of a level, the W-cycle twice, the second visit starting from the first
+ * one's result with the same right-hand side. */
+enum { IIM_CYCLE_V = 1, IIM_CYCLE_W = 2 };
+/* Krylov method: right-preconditioned flexible GMRES(m) (Sec. 4.1), or left-
+ * preconditioned GMRES(m) (Sec. 3.2), which minimises and tests the preconditioned
+ * residual |M (b - A x)| <= tol |M b| and stores no preconditioned basis. */
+enum { IIM_KRYLOV_FGMRES = 0, IIM_KRYLOV_GMRES_LEFT = 1 };
 
 /* Problem statement (paper Sec. 2.1-2.2).
  * geom_params by kind (phi = -g if plus_inside else g, g < 0 inside the body):
@@ -94,6 +102,10 @@ typedef struct {
   int mg_precision;      /* IIM_MG_FP32, IIM_MG_FP64 or IIM_MG_FP32_BF16R */
   int use_graph;         /* 1: the solve runs as one CUDA graph with device-side control */
   int reorth;            /* 1: second Gram-Schmidt pass when |w| drops below 1e-3 |w_old| */
+  int cycle;             /* IIM_CYCLE_V or IIM_CYCLE_W (single-problem solves only) */
+  int krylov;            /* IIM_KRYLOV_FGMRES or IIM_KRYLOV_GMRES_LEFT (single-problem solves only);
+                            with GMRES_LEFT, tol and the reported relres are those of the
+                            preconditioned residual */
 } iim_options;
 
 typedef struct {
@@ -108,7 +120,8 @@ typedef struct {
 
 typedef struct iim_problem iim_problem;
 
-/* Fill *opt with the defaults: tol 1e-10, restart 10, max_iter 500, V(2,2), FP32 MG, graph on, reorth on. */
+/* Fill *opt with the defaults: tol 1e-10, restart 10, max_iter 500, V(2,2), FP32 MG, graph on,
+ * reorth on, FGMRES. */
 void iim_default_options(iim_options* opt);
 
 /* Create a problem: validate, allocate the workspace and run the whole set-up
@@ -305,9 +318,9 @@ iim_status iim_server_submit(iim_server* s, const iim_problem_desc* desc, int64_
 /* One turn of the loop: (1) when the last run has finished, release the slots
  * that finished; (2) put ready requests into free slots and launch the next run;
  * (3) copy the finished solutions to the host; (4) create queued requests that
- * fit the budget.  need_data[0 .. *n_need) = ids created in this turn, waiting
- * for data; finished[0 .. *n_fin) = ids finished (or failed) in this turn.
- * Arrays may be NULL with capacity 0 (ids beyond a capacity are not reported). */
+ * fit the budget.  need_data[0 .. *n_need) = ids now waiting for data;
+ * finished[0 .. *n_fin) = ids finished (or failed).  Every id is reported once:
+ * ids beyond an array's capacity (or with a NULL array) are reported by a later step. */
 iim_status iim_server_step(iim_server* s, int64_t* need_data, int cap_need, int* n_need, int64_t* finished,
                            int cap_fin, int* n_fin);
 
@@ -324,11 +337,14 @@ iim_status iim_server_data_ready(iim_server* s, int64_t id);
 iim_status iim_server_take(iim_server* s, int64_t id, double* x_host, iim_solve_info* info, double* latency_s);
 
 /* Device bytes held (or reserved) by requests now and at most so far, queued
- * requests, requests in the engine, engine runs launched, and host seconds
+ * requests, requests in the engine, engine runs launched, host seconds
  * (double[3], may be NULL): in iim_server_step, in copying solutions to the host,
- * and in creating requests (summed over the creation threads). */
+ * and in creating requests (summed over the creation threads), and the number of
+ * requests not yet taken in each state (int[8], may be NULL): queued, being
+ * created, waiting for data, ready, running, retired, finished, failed.
+ * Any pointer may be NULL. */
 iim_status iim_server_stats(iim_server* s, size_t* bytes_in_use, size_t* peak_bytes, int* queued, int* resident,
-                            int64_t* runs, double* host_seconds);
+                            int64_t* runs, double* host_seconds, int* states);
 
 /* Boundary quantity the data do not prescribe, at every control point (K values,
  * the order of iim_control_points), from the same least-squares fits (Sec. 2.4):

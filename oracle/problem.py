@@ -10,7 +10,7 @@ from .operator import IIMOperator
 
 
 class OracleProblem:
-    def __init__(self, spec, nu1=2, nu2=2, check_curvature=True, gamma=1):
+    def __init__(self, spec, nu1=2, nu2=2, check_curvature=True, cycle=1):
         self.spec = spec
         self.op = IIMOperator(spec, check_curvature=check_curvature)
         self.n, self.d = spec.n, spec.dim
@@ -18,14 +18,14 @@ class OracleProblem:
         self.unk_flat = self.op.unknown.ravel(order="F")
         self._mg = None
         self.nu1, self.nu2 = nu1, nu2
-        self.gamma = gamma
+        self.cycle = cycle          # coarse visits per level: 1 V-cycle, 2 W-cycle
 
     @property
     def mg(self):
         if self._mg is None:
             s = self.spec
             self._mg = Multigrid(self.op.ls, s.n, s.bc, s.box_bc, s.beta_plus, s.beta_minus, self.nu1, self.nu2,
-                                 self.gamma)
+                                 self.cycle)
         return self._mg
 
     def data(self, spec=None):
@@ -53,29 +53,19 @@ class OracleProblem:
     def precondition(self, v):
         return self.mg.precondition(v, self.plus_flat)
 
-    def solve_left(self, f, data, tol=None, restart=10, max_iter=1000):
-        """Left-preconditioned GMRES (the paper's 2D solver, Sec. 3.2) with its stopping rule:
-        |M^-1 r| <= tol |M^-1 b|, tol = 1e-6 / N_x by default."""
-        from .fgmres import gmres_left
-        b = self.op.rhs(f, data)
-        tol = 1e-6 / self.n if tol is None else tol
-        x, info = gmres_left(self.op.apply, self.precondition, b, tol=tol, restart=restart, max_iter=max_iter)
-        return x, info, b
-
     @property
     def singular(self):
         """Pure Neumann problem (no outer box): L 1 = 0, solution defined up to a constant."""
         return self.spec.bc == W.NEUMANN and self.spec.box_bc == W.BOX_NONE
 
-    def solve(self, f, data, tol=1e-13, restart=10, max_iter=1000, gamma=0.0):
-        """Solve L u = b.  Singular (pure Neumann) problems solve the augmented system of
-        Sec. 2.3, [L 1; 1^T 0][u; alpha] = [b; gamma] with 1 over the unknowns, by the same
-        FGMRES; the preconditioner is the V-cycle on u and the identity on alpha.
-        info["alpha"] is the shift that makes b + alpha 1 compatible."""
+    def system(self, f, data, gamma=0.0):
+        """(apply, precondition, right-hand side, N) of the Krylov iteration.  Singular (pure
+        Neumann) problems take the augmented system of Sec. 2.3, [L 1; 1^T 0][u; alpha] =
+        [b; gamma] with 1 over the unknowns, preconditioned by the cycle on u and the
+        identity on alpha; N is then the index of alpha, else None."""
         b = self.op.rhs(f, data)
         if not self.singular:
-            x, info = fgmres(self.op.apply, self.precondition, b, tol=tol, restart=restart, max_iter=max_iter)
-            return x, info, b
+            return self.op.apply, self.precondition, b, None
         unk = self.unk_flat.astype(float)
         N = b.size
 
@@ -91,6 +81,28 @@ class OracleProblem:
             out[N] = v[N]
             return out
 
-        xa, info = fgmres(apply_aug, precond_aug, np.append(b, gamma), tol=tol, restart=restart, max_iter=max_iter)
-        info["alpha"] = xa[N]
-        return xa[:N], info, b
+        return apply_aug, precond_aug, np.append(b, gamma), N
+
+    @staticmethod
+    def _split(x, info, rhs, N):
+        if N is None:
+            return x, info, rhs
+        info["alpha"] = x[N]
+        return x[:N], info, rhs[:N]
+
+    def solve(self, f, data, tol=1e-13, restart=10, max_iter=1000, gamma=0.0):
+        """Solve L u = b by right-preconditioned FGMRES(m) (Sec. 4.1); singular problems
+        through the augmented system (info["alpha"]: the shift that makes b + alpha 1
+        compatible)."""
+        A, M, rhs, N = self.system(f, data, gamma)
+        x, info = fgmres(A, M, rhs, tol=tol, restart=restart, max_iter=max_iter)
+        return self._split(x, info, rhs, N)
+
+    def solve_left(self, f, data, tol=None, restart=10, max_iter=1000, gamma=0.0):
+        """Left-preconditioned GMRES(m) (the 2D solver of Sec. 3.2) with its stopping rule
+        |M r| <= tol |M b|, tol = 1e-6 / n by default; singular problems as in solve."""
+        from .fgmres import gmres_left
+        tol = 1e-6 / self.n if tol is None else tol
+        A, M, rhs, N = self.system(f, data, gamma)
+        x, info = gmres_left(A, M, rhs, tol=tol, restart=restart, max_iter=max_iter)
+        return self._split(x, info, rhs, N)

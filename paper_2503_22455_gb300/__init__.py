@@ -20,6 +20,8 @@ STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "curvature", 3: "rank", 4: "s
 GEOM = {"circle": 0, "ellipse": 1, "star": 2, "sphere": 3, "ellipsoid": 4}
 BC = {"dirichlet": 0, "neumann": 1, "interface": 2}
 MG_FP32, MG_FP64, MG_FP32_BF16R = 0, 1, 2
+CYCLE_V, CYCLE_W = 1, 2
+KRYLOV_FGMRES, KRYLOV_GMRES_LEFT = 0, 1
 
 
 class IIMError(RuntimeError):
@@ -38,7 +40,8 @@ class Desc(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("mg_precision", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("reorth", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("reorth", ctypes.c_int), ("cycle", ctypes.c_int),
+                ("krylov", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -107,7 +110,7 @@ SIGNATURES = {
     "iim_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t),
                                         ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
-                                        ctypes.POINTER(ctypes.c_double)]),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     "iim_last_error": (ctypes.c_char_p, []),
     "iim_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -513,20 +516,29 @@ class Server:
     def stats(self):
         b, pk, q, r, runs = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
         hs = (ctypes.c_double * 3)()
+        st = (ctypes.c_int * 8)()
         _check(load().iim_server_stats(self.h, ctypes.byref(b), ctypes.byref(pk), ctypes.byref(q), ctypes.byref(r),
-                                       ctypes.byref(runs), hs))
+                                       ctypes.byref(runs), hs, st))
         return {"bytes_in_use": b.value, "peak_bytes": pk.value, "queued": q.value, "resident": r.value,
-                "runs": runs.value, "host_step_s": hs[0], "host_copy_s": hs[1], "host_create_s": hs[2]}
+                "runs": runs.value, "host_step_s": hs[0], "host_copy_s": hs[1], "host_create_s": hs[2],
+                "states": dict(zip(SERVER_STATES, list(st)))}
 
 
-def serve(server: Server, arrivals, set_data, realtime=True, idle_sleep=0.0, timings=None):
+SERVER_STATES = ("queued", "creating", "need_data", "ready", "running", "retired", "finished", "failed")
+
+
+def serve(server: Server, arrivals, set_data, realtime=True, idle_sleep=0.0, timings=None, deadline_s=None,
+          progress=None, progress_every_s=5.0):
     """Drive a server through a stream of requests.
 
     arrivals: list of (arrival time in seconds from now, Desc, user object), sorted by time;
     set_data(problem_view, user) sets the data of a created request.  Returns
     {request id: (x, info, latency, status, user)} and the wall time.  With realtime=False
     every request is submitted at once.  timings (a dict) receives the caller-side host
-    seconds spent in step, set_data and take.
+    seconds spent in step, set_data and take.  With deadline_s, a TimeoutError naming the
+    requests' states is raised when requests are still outstanding after that many
+    seconds; progress(elapsed_s, taken, outstanding, server stats) is called every
+    progress_every_s seconds.
     """
     import time
     t0 = time.perf_counter()
@@ -535,8 +547,15 @@ def serve(server: Server, arrivals, set_data, realtime=True, idle_sleep=0.0, tim
     users, out = {}, {}
     outstanding = 0
     t_step = t_data = t_take = 0.0
+    next_note = progress_every_s
     while k < len(pending) or outstanding:
         now = time.perf_counter() - t0
+        if progress is not None and now >= next_note:
+            progress(now, len(out), outstanding, server.stats())
+            next_note = now + progress_every_s
+        if deadline_s is not None and now > deadline_s:
+            raise TimeoutError(f"serve: {outstanding} requests outstanding after {now:.0f} s "
+                               f"({len(out)} taken, {len(pending) - k} not submitted): {server.stats()}")
         while k < len(pending) and (not realtime or pending[k][0] <= now):
             _, desc, user = pending[k]
             rid = server.submit(desc)

@@ -164,6 +164,9 @@ static iim_status validate(const iim_problem_desc* d, const iim_options* o) {
   if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 + o->nu2 < 1) return IIM_ERR_INVALID_ARG;
   if (o->mg_precision != IIM_MG_FP32 && o->mg_precision != IIM_MG_FP64 && o->mg_precision != IIM_MG_FP32_BF16R)
     return IIM_ERR_INVALID_ARG;
+  if ((o->cycle != IIM_CYCLE_V && o->cycle != IIM_CYCLE_W) ||
+      (o->krylov != IIM_KRYLOV_FGMRES && o->krylov != IIM_KRYLOV_GMRES_LEFT))
+    return IIM_ERR_INVALID_ARG;
   return IIM_OK;
 }
 
@@ -196,6 +199,8 @@ void iim_default_options(iim_options* o) {
   o->mg_precision = IIM_MG_FP32;
   o->use_graph = 1;
   o->reorth = 1;
+  o->cycle = IIM_CYCLE_V;
+  o->krylov = IIM_KRYLOV_FGMRES;
 }
 
 const char* iim_last_error(void) { return g_err.c_str(); }

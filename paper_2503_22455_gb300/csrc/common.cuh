@@ -6,7 +6,10 @@
 #include <stdint.h>
 
 #include <cstdio>
+#include <mutex>
+#include <set>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/iim.h"
@@ -212,6 +215,27 @@ __device__ inline float store_residual(float v, int bf16) {
 __device__ inline double store_residual(double v, int) { return v; }
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Raise a kernel's dynamic shared memory limit to the most the device allows (beside the
+// kernel's static shared memory), once per device and kernel.  The limit is a
+// process-wide attribute of the function; setting it to each problem's own size would
+// race with another thread launching the same kernel for a larger problem.
+inline cudaError_t smem_optin(const void* func) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count({dev, func})) return cudaSuccess;
+  int mx = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, func);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess) done.insert({dev, func});
+  return e;
+}
 
 // launch accounting (every kernel launch of the library goes through IIM_LAUNCH)
 void note_launch();

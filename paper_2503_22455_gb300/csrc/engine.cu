@@ -411,6 +411,10 @@ iim_status iim_engine_admit(iim_engine* H, iim_problem* p, const double* x0_dev,
     set_error("engine: pure Neumann problems (augmented system) are solved by iim_solve only");
     return IIM_ERR_INVALID_ARG;
   }
+  if (P.opt.cycle != IIM_CYCLE_V || P.opt.krylov != IIM_KRYLOV_FGMRES) {
+    set_error("engine: W-cycles and left-preconditioned GMRES are solved by iim_solve only");
+    return IIM_ERR_INVALID_ARG;
+  }
   if ((int)mg_tail_start(P) > kEngMaxDepth) {
     set_error("engine: too many fine multigrid levels");
     return IIM_ERR_INVALID_ARG;

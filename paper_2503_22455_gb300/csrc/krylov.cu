@@ -14,6 +14,10 @@
 // the true residual |b - A x| / |b| at every restart (x += Z y).
 // The whole solve is one CUDA graph: WHILE(not done) { IF(active) iteration 0;
 // ...; IF(active) iteration m-1; restart }, with the conditions set by kernels.
+//
+// Left-preconditioned GMRES(m) (Sec. 3.2) shares the Arnoldi kernels: its basis is
+// built from w = M(L v_j), x += V y, and the residual it tests and restarts from is
+// the preconditioned one, M (b - L x), relative to |M b|.
 #include <algorithm>
 
 #include "engine.cuh"
@@ -83,15 +87,24 @@ __device__ inline void set_cond(SolverScalars* S, cudaGraphConditionalHandle h, 
   if (S->graph_mode) cudaGraphSetConditional(h, v ? 1u : 0u);
 }
 
-// restart / start: V0 = b - Ax (Ax in ax), |V0|^2, |b|^2
+// restart / start: V0 = b - Ax (Ax in ax), |V0|^2, |b|^2.  With b == nullptr V0 already
+// holds the residual (left preconditioning: M (b - A x)) and is only measured.
+// first: 0 restart, 1 start, 2 only store |V0| as the norm of b (left preconditioning:
+// V0 = M b), 3 start with that norm already stored.
 __device__ inline void residual_body(const double* __restrict__ b, const double* __restrict__ ax,
                                      double* __restrict__ v0, int64_t N, double* partial, unsigned int* counter,
                                      SolverScalars* S, int first, int* status, int vb, int nvb) {
   double acc[2] = {0.0, 0.0};
   for (int64_t i = (int64_t)vb * blockDim.x + threadIdx.x; i < N; i += (int64_t)nvb * blockDim.x) {
-    double bi = b[i];
-    double r = bi - ax[i];
-    v0[i] = r;
+    double bi, r;
+    if (b) {
+      bi = b[i];
+      r = bi - ax[i];
+      v0[i] = r;
+    } else {
+      r = v0[i];
+      bi = r;
+    }
     acc[0] = fma(r, r, acc[0]);
     acc[1] = fma(bi, bi, acc[1]);
   }
@@ -101,9 +114,13 @@ __device__ inline void residual_body(const double* __restrict__ b, const double*
   sum_partials(partial, nvb, 4, 2, tot);
   if (threadIdx.x == 0) {
     *counter = 0;
+    if (first == 2) {
+      S->bnorm = sqrt(tot[1]);
+      return;
+    }
     double rn = sqrt(tot[0]);
     if (first) {
-      S->bnorm = sqrt(tot[1]);
+      if (first == 1) S->bnorm = sqrt(tot[1]);
       S->iters = 0;
       S->restarts = 0;
       S->done = 0;
@@ -315,12 +332,14 @@ __global__ void k_solve_y(SolverScalars* S) {
   solve_y_body(S);
 }
 
-// x += sum_{i<k} y_i Z_i
+// x += sum_{i<k} y_i Z_i (right preconditioning), or x += sum_{i<k} y_i V_i / |V_i| with
+// Z = V (left preconditioning: the basis is stored unnormalised)
 __device__ inline void xupdate_body(double* __restrict__ x, const double* __restrict__ Z, int64_t Np, int64_t N,
-                                    const SolverScalars* S, int vb, int nvb) {
+                                    const SolverScalars* S, int vb, int nvb, bool unnormalised = false) {
   __shared__ double y[kMaxRestart];
   __shared__ int k;
-  if (threadIdx.x < kMaxRestart) y[threadIdx.x] = S->y[threadIdx.x];
+  if (threadIdx.x < kMaxRestart)
+    y[threadIdx.x] = unnormalised ? S->y[threadIdx.x] * S->inv_norm[threadIdx.x] : S->y[threadIdx.x];
   if (threadIdx.x == 0) k = S->k;
   __syncthreads();
   for (int64_t i = (int64_t)vb * blockDim.x + threadIdx.x; i < N; i += (int64_t)nvb * blockDim.x) {
@@ -331,8 +350,15 @@ __device__ inline void xupdate_body(double* __restrict__ x, const double* __rest
 }
 
 __global__ void __launch_bounds__(256) k_xupdate(double* __restrict__ x, const double* __restrict__ Z, int64_t Np,
-                                                 int64_t N, const SolverScalars* S) {
-  xupdate_body(x, Z, Np, N, S, blockIdx.x, gridDim.x);
+                                                 int64_t N, const SolverScalars* S, int unnormalised) {
+  xupdate_body(x, Z, Np, N, S, blockIdx.x, gridDim.x, unnormalised != 0);
+}
+
+// r = b - ax
+__global__ void __launch_bounds__(256) k_sub(const double* __restrict__ b, const double* __restrict__ ax,
+                                             double* __restrict__ r, int64_t N) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    r[i] = b[i] - ax[i];
 }
 
 __global__ void k_init_scalars(SolverScalars* S, int m, int max_iter, double tol, int graph_mode, int reorth) {
@@ -357,8 +383,10 @@ __global__ void k_set_handles(SolverScalars* S, cudaGraphConditionalHandle hw, c
 iim_status krylov_alloc(Problem& P) {
   P.Npad = ((P.g.N + P.aug + 63) / 64) * 64;   // augmented: entry N holds the shift alpha
   const int m = P.opt.restart;
+  // right preconditioning keeps the m preconditioned vectors; left needs one scratch vector
+  const int mz = P.opt.krylov == IIM_KRYLOV_GMRES_LEFT ? 1 : m;
   P.V = (double*)dev_alloc(P, sizeof(double) * (size_t)(m + 1) * P.Npad);
-  P.Z = (double*)dev_alloc(P, sizeof(double) * (size_t)m * P.Npad);
+  P.Z = (double*)dev_alloc(P, sizeof(double) * (size_t)mz * P.Npad);
   P.x = (double*)dev_alloc(P, sizeof(double) * P.Npad);
   P.tmp = (double*)dev_alloc(P, sizeof(double) * P.Npad);
   P.sc = (SolverScalars*)dev_alloc(P, sizeof(SolverScalars));
@@ -370,7 +398,7 @@ iim_status krylov_alloc(Problem& P) {
   P.counter = (unsigned int*)dev_alloc(P, sizeof(unsigned int) * 4);
   if (!P.V || !P.Z || !P.x || !P.tmp || !P.sc || !P.partial || !P.counter) return IIM_ERR_BUDGET;
   cudaMemsetAsync(P.V, 0, sizeof(double) * (size_t)(m + 1) * P.Npad, P.stream);
-  cudaMemsetAsync(P.Z, 0, sizeof(double) * (size_t)m * P.Npad, P.stream);
+  cudaMemsetAsync(P.Z, 0, sizeof(double) * (size_t)mz * P.Npad, P.stream);
   cudaMemsetAsync(P.x, 0, sizeof(double) * P.Npad, P.stream);
   cudaMemsetAsync(P.tmp, 0, sizeof(double) * P.Npad, P.stream);
   cudaMemsetAsync(P.counter, 0, sizeof(unsigned int) * 4, P.stream);
@@ -443,21 +471,49 @@ static void krylov_apply(Problem& P, const double* u, double* w, cudaStream_t s)
   IIM_LAUNCH(k_aug_finish, 1, 32, 0, s, w, P.g.N, P.partial, P.red_blocks);
 }
 
+// the preconditioner of the Krylov iteration: z = M(v * vscale) (identity on alpha)
+static void krylov_precondition(Problem& P, const double* v, const double* vscale, double* z, cudaStream_t s) {
+  mg_precondition(P, v, vscale, z, s);
+  if (P.aug) IIM_LAUNCH(k_aug_pass, 1, 32, 0, s, v, vscale, z, P.g.N);
+}
+
+static bool left_prec(const Problem& P) { return P.opt.krylov == IIM_KRYLOV_GMRES_LEFT; }
+
 static void enqueue_iteration(Problem& P, int j, cudaStream_t s) {
   double* vj = P.V + (size_t)j * P.Npad;
-  double* zj = P.Z + (size_t)j * P.Npad;
   double* w = P.V + (size_t)(j + 1) * P.Npad;
-  mg_precondition(P, vj, &P.sc->inv_norm[j], zj, s);
-  if (P.aug) IIM_LAUNCH(k_aug_pass, 1, 32, 0, s, vj, &P.sc->inv_norm[j], zj, P.g.N);
-  krylov_apply(P, zj, w, s);
+  if (left_prec(P)) {
+    krylov_apply(P, vj, P.tmp, s);                                  // L v_j (v_j unnormalised)
+    krylov_precondition(P, P.tmp, &P.sc->inv_norm[j], w, s);       // w = M L v_j / |v_j|
+  } else {
+    double* zj = P.Z + (size_t)j * P.Npad;
+    krylov_precondition(P, vj, &P.sc->inv_norm[j], zj, s);
+    krylov_apply(P, zj, w, s);
+  }
   orth(P, j, s, 0);
   if (P.opt.reorth) orth(P, j, s, 1);
   IIM_LAUNCH(k_arnoldi_step, 1, 32, 0, s, P.sc, j, P.d_status);
 }
 
+// left preconditioning: V0 = M (b - L x), measured (first: 0 restart, 3 start)
+static void enqueue_left_residual(Problem& P, cudaStream_t s, int first) {
+  const int64_t n = P.g.N + P.aug;
+  double* r = P.Z;   // scratch
+  krylov_apply(P, P.x, P.tmp, s);
+  IIM_LAUNCH(k_sub, 4 * kNumSMs, 256, 0, s, P.b, P.tmp, r, n);
+  krylov_precondition(P, r, nullptr, P.V, s);
+  IIM_LAUNCH(k_residual, P.red_blocks, kRedThreads, 0, s, nullptr, nullptr, P.V, n, P.partial, P.counter, P.sc,
+             first, P.d_status);
+}
+
 static void enqueue_restart(Problem& P, cudaStream_t s) {
   IIM_LAUNCH(k_solve_y, 1, 32, 0, s, P.sc);
-  IIM_LAUNCH(k_xupdate, 4 * kNumSMs, 256, 0, s, P.x, P.Z, P.Npad, P.g.N + P.aug, P.sc);
+  if (left_prec(P)) {
+    IIM_LAUNCH(k_xupdate, 4 * kNumSMs, 256, 0, s, P.x, P.V, P.Npad, P.g.N + P.aug, P.sc, 1);
+    enqueue_left_residual(P, s, 0);
+    return;
+  }
+  IIM_LAUNCH(k_xupdate, 4 * kNumSMs, 256, 0, s, P.x, P.Z, P.Npad, P.g.N + P.aug, P.sc, 0);
   krylov_apply(P, P.x, P.tmp, s);
   IIM_LAUNCH(k_residual, P.red_blocks, kRedThreads, 0, s, P.b, P.tmp, P.V, P.g.N + P.aug, P.partial, P.counter, P.sc,
              0, P.d_status);
@@ -465,6 +521,14 @@ static void enqueue_restart(Problem& P, cudaStream_t s) {
 
 static void enqueue_start(Problem& P, cudaStream_t s, int graph_mode) {
   IIM_LAUNCH(k_init_scalars, 1, 1, 0, s, P.sc, P.opt.restart, P.opt.max_iter, P.opt.tol, graph_mode, P.opt.reorth);
+  if (left_prec(P)) {
+    // |M b| first (the reference of the stopping test), then the preconditioned residual
+    krylov_precondition(P, P.b, nullptr, P.V, s);
+    IIM_LAUNCH(k_residual, P.red_blocks, kRedThreads, 0, s, nullptr, nullptr, P.V, P.g.N + P.aug, P.partial,
+               P.counter, P.sc, 2, P.d_status);
+    enqueue_left_residual(P, s, 3);
+    return;
+  }
   krylov_apply(P, P.x, P.tmp, s);
   IIM_LAUNCH(k_residual, P.red_blocks, kRedThreads, 0, s, P.b, P.tmp, P.V, P.g.N + P.aug, P.partial, P.counter, P.sc,
              1, P.d_status);

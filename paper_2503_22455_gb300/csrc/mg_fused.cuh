@@ -11,6 +11,8 @@
 //   MODE 4  one plain sweep (only when nu > 2)
 //   MODE 5  MODE 0 and MODE 1 in one kernel (nu1 = 2): halo 4, four half sweeps
 //   MODE 6  MODE 2 and MODE 3 in one kernel (nu2 = 2)
+//   MODE 7  MODE 5 from a given u (a W-cycle's second visit of a level): halo 5, since
+//           the first half sweep now reads its neighbours
 // Coarse tail: every level with at most 1024 nodes (one per thread) and the dense
 // coarse solve run in a single CTA with the whole sub-hierarchy in shared memory.
 #pragma once
@@ -71,9 +73,11 @@ __device__ inline T tab2(const LevelK<T>& L, int r, int k) { return L.tab[(size_
 
 template <typename T, int TX, int TY, int MODE>
 __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx, const int by) {
-  constexpr int KH = MODE >= 5 ? 4 : kH;      // the fused modes run four half sweeps on the tile
+  // the fused modes run four half sweeps on the tile; from a given u the first one needs
+  // one more ring of neighbours
+  constexpr int KH = MODE == 7 ? 5 : MODE >= 5 ? 4 : kH;
   constexpr bool DOWN_FIRST = MODE == 0 || MODE == 5, UP_FIRST = MODE == 2 || MODE == 6;
-  constexpr bool UP_LAST = MODE == 3 || MODE == 6, RESTRICT = MODE == 1 || MODE == 5;
+  constexpr bool UP_LAST = MODE == 3 || MODE == 6, RESTRICT = MODE == 1 || MODE == 5 || MODE == 7;
   constexpr int SX = TX + 2 * KH, SY = TY + 2 * KH, S = SX * SY;
   __shared__ T us[S];
   __shared__ T fs[S];
@@ -196,6 +200,9 @@ __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx
   if (MODE == 6) {     // both post-smoothing sweeps after the correction
     half_sweep(0, 3, false); half_sweep(1, 2, false); half_sweep(0, 1, false); half_sweep(1, 0, false);
   }
+  if (MODE == 7) {     // both pre-smoothing sweeps from u_in
+    half_sweep(0, 4, false); half_sweep(1, 3, false); half_sweep(0, 2, false); half_sweep(1, 1, false);
+  }
   if (RESTRICT) {
     // residual on the tile, kept in registers until every thread has read its neighbours
     constexpr int TPT = (TX * TY + 255) / 256;
@@ -267,6 +274,9 @@ struct TailParams {
   int tcap[kTailMaxLevels];
   int stage_tables;                  // 1: tables copied to shared memory
   int nu1, nu2, neumann;
+  int gamma;                         // visits of the next coarser level per visit (1: V, 2: W)
+  int top_visits;                    // consecutive visits of the first level (gamma when the
+                                     // tail is entered from a finer level, else 1)
   T* u_out;                          // where the first level's u goes (when z is not set)
   int nu;                            // coarse unknowns
   int ld;                            // leading dimension of inv (nu, or nu + 1 when augmented)
@@ -386,9 +396,11 @@ __device__ __forceinline__ void vcycle_tail_body(const TailParams<T>& P, const d
     }
     __syncthreads();
   };
-  for (int k = 0; k < P.nlev - 1; ++k) {
+  // pre-smoothing of level k (the first sweep from u = 0 when zero) and the restriction
+  // of its residual to level k + 1
+  auto down = [&](int k, bool zero) {
     for (int it = 0; it < P.nu1; ++it) {
-      sweep(k, 0, it == 0);
+      sweep(k, 0, zero && it == 0);
       sweep(k, 1, false);
     }
     const LevelK<T>& L = P.L[k];
@@ -417,8 +429,9 @@ __device__ __forceinline__ void vcycle_tail_body(const TailParams<T>& P, const d
       sf[P.off[k + 1] + I] = store_residual(acc, C.f_bf16);
     }
     __syncthreads();
-  }
-  {
+  };
+  // the dense solve on the coarsest level (it does not depend on a starting u)
+  auto coarse = [&]() {
     const int k = P.nlev - 1;
     const LevelK<T>& L = P.L[k];
     T* u = su + P.off[k];
@@ -433,8 +446,9 @@ __device__ __forceinline__ void vcycle_tail_body(const TailParams<T>& P, const d
       if (lane == 0) u[P.map[r]] = s;
     }
     __syncthreads();
-  }
-  for (int k = P.nlev - 2; k >= 0; --k) {
+  };
+  // level k += prolongated correction of level k + 1, then post-smoothing
+  auto up = [&](int k) {
     const LevelK<T>& L = P.L[k];
     const LevelK<T>& C = P.L[k + 1];
     T* u = su + P.off[k];
@@ -474,6 +488,51 @@ __device__ __forceinline__ void vcycle_tail_body(const TailParams<T>& P, const d
     for (int it = 0; it < P.nu2; ++it) {
       sweep(k, 0, false);
       sweep(k, 1, false);
+    }
+  };
+  // Visit schedule (Sec. 3.3 results): each visit of level k below the first runs gamma
+  // visits of level k + 1, the second from the first one's result with the same f; the
+  // first level is visited top_visits times in a row.  Repeated coarsest visits within a
+  // visit of the level above return the same u (the dense solve ignores the start), so
+  // one is run.
+  if (P.nlev == 1) {
+    coarse();
+  } else {
+    int cnt[kTailMaxLevels];   // visits of level k + 1 completed in the current visit of level k
+    int k = 0, top_done = 0;
+    bool zero = true, descending = true;
+    for (;;) {
+      if (descending) {
+        if (k == P.nlev - 1) {
+          coarse();
+          --k;
+          cnt[k] = P.gamma;
+          descending = false;
+          continue;
+        }
+        down(k, zero);
+        cnt[k] = 0;
+        ++k;
+        zero = true;
+        continue;
+      }
+      if (cnt[k] < P.gamma) {       // another visit of level k + 1 from its current u
+        ++k;
+        zero = false;
+        descending = true;
+        continue;
+      }
+      up(k);
+      if (k == 0) {
+        if (++top_done < P.top_visits) {
+          zero = false;
+          descending = true;
+          continue;
+        }
+        break;
+      }
+      --k;
+      ++cnt[k];
     }
   }
   const LevelK<T>& L = P.L[0];

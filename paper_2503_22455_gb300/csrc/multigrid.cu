@@ -445,6 +445,8 @@ TailParams<T> make_tail_params(Problem& P, size_t l0, T* u_out, size_t smem_limi
   }
   tp.nu1 = P.opt.nu1;
   tp.nu2 = P.opt.nu2;
+  tp.gamma = P.opt.cycle;
+  tp.top_visits = 1;
   tp.neumann = P.desc.bc == IIM_BC_NEUMANN;
   tp.nu = P.coarse_nu;
   tp.ld = P.coarse_n;
@@ -462,15 +464,18 @@ TailParams<T> make_tail_params(Problem& P, size_t l0, T* u_out, size_t smem_limi
 }
 template TailParams<float> make_tail_params<float>(Problem&, size_t, float*, size_t, size_t*);
 
+// The tail entered from a finer level runs all gamma visits of its first level (they
+// follow one another with the same right-hand side); from the finest level, one.
 template <typename T>
 static void launch_tail(Problem& P, size_t l0, const double* v, const double* vscale, double* z, cudaStream_t s,
                         T* u_out = nullptr) {
   size_t smem = 0;
   TailParams<T> tp = make_tail_params<T>(P, l0, u_out, 200 * 1024, &smem);
+  tp.top_visits = l0 == 0 ? 1 : P.opt.cycle;
   tp.v = v;
   tp.vscale = vscale;
   tp.z = z;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_vcycle_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 48 * 1024) smem_optin((const void*)k_vcycle_tail<T>);
   IIM_LAUNCH(k_vcycle_tail<T>, 1, kTailThreads, smem, s, tp);
 }
 
@@ -499,6 +504,7 @@ static void launch_fine2d(Problem& P, size_t l, int mode, const double* v, const
     case 3: IIM_LAUNCH((k_mg2d<T, TX, TY, 3>), grid, 256, 0, s, fp); break;
     case 5: IIM_LAUNCH((k_mg2d<T, TX, TY, 5>), grid, 256, 0, s, fp); break;
     case 6: IIM_LAUNCH((k_mg2d<T, TX, TY, 6>), grid, 256, 0, s, fp); break;
+    case 7: IIM_LAUNCH((k_mg2d<T, TX, TY, 7>), grid, 256, 0, s, fp); break;
     default: IIM_LAUNCH((k_mg2d<T, TX, TY, 4>), grid, 256, 0, s, fp); break;
   }
 }
@@ -511,32 +517,43 @@ static void fine2d(Problem& P, size_t l, int mode, const double* v, const double
 }
 
 // 2D: fused kernels per fine level (MODE 0, [4...], 1 down; 2, [4...], 3 up), ping-ponging
-// between the level's two u buffers.  Returns the buffer that holds the level's result.
+// between the level's two u buffers.  u0 is the level's starting u (the previous visit's
+// result in a W-cycle; nullptr: zero).  Returns the buffer that holds the level's result.
 template <typename T>
 static T* vcycle2d(Problem& P, size_t l, size_t lt, const double* v, const double* vscale, double* z,
-                   cudaStream_t s) {
+                   cudaStream_t s, const T* u0 = nullptr) {
   T* A = (T*)P.lv[l].u;
   T* B = (T*)P.lv[l].u2;
   if (l == lt) {
     launch_tail<T>(P, l, l == 0 ? v : nullptr, l == 0 ? vscale : nullptr, l == 0 ? z : nullptr, s, A);
     return A;
   }
+  // gamma visits of the next level (one launch of the tail runs all of its own)
+  auto coarser = [&]() -> const T* {
+    if (l + 1 == lt) return vcycle2d<T>(P, l + 1, lt, nullptr, nullptr, nullptr, s);
+    const T* uc = nullptr;
+    for (int g = 0; g < P.opt.cycle; ++g) uc = vcycle2d<T>(P, l + 1, lt, nullptr, nullptr, nullptr, s, uc);
+    return uc;
+  };
   if (P.opt.nu1 == 2 && P.opt.nu2 == 2) {
     // two fused kernels per level: both pre-smoothing sweeps + restriction, then the
-    // correction + both post-smoothing sweeps
-    fine2d<T>(P, l, 5, l == 0 ? v : nullptr, vscale, nullptr, nullptr, A, nullptr, s);
-    const T* uc = vcycle2d<T>(P, l + 1, lt, nullptr, nullptr, nullptr, s);
+    // correction + both post-smoothing sweeps.  The result is in B, so a later visit
+    // reads B and writes A.
+    if (u0) fine2d<T>(P, l, 7, nullptr, nullptr, nullptr, u0, A, nullptr, s);
+    else fine2d<T>(P, l, 5, l == 0 ? v : nullptr, vscale, nullptr, nullptr, A, nullptr, s);
+    const T* uc = coarser();
     fine2d<T>(P, l, 6, nullptr, nullptr, l == 0 ? z : nullptr, A, B, uc, s);
     return B;
   }
-  fine2d<T>(P, l, 0, l == 0 ? v : nullptr, vscale, nullptr, nullptr, A, nullptr, s);
+  if (u0) fine2d<T>(P, l, 4, nullptr, nullptr, nullptr, u0, A, nullptr, s);
+  else fine2d<T>(P, l, 0, l == 0 ? v : nullptr, vscale, nullptr, nullptr, A, nullptr, s);
   for (int it = 1; it < P.opt.nu1 - 1; ++it) {
     fine2d<T>(P, l, 4, nullptr, nullptr, nullptr, A, B, nullptr, s);
     std::swap(A, B);
   }
   fine2d<T>(P, l, 1, nullptr, nullptr, nullptr, A, B, nullptr, s);
   std::swap(A, B);
-  const T* uc = vcycle2d<T>(P, l + 1, lt, nullptr, nullptr, nullptr, s);
+  const T* uc = coarser();
   fine2d<T>(P, l, 2, nullptr, nullptr, nullptr, A, B, uc, s);
   std::swap(A, B);
   for (int it = 1; it < P.opt.nu2 - 1; ++it) {
@@ -547,9 +564,10 @@ static T* vcycle2d(Problem& P, size_t l, size_t lt, const double* v, const doubl
   return B;
 }
 
-// generic path (3D fine levels): one kernel per half sweep, transfers separate
+// generic path (3D fine levels): one kernel per half sweep, transfers separate; u is
+// updated in place and starts from zero unless this is a later visit of a W-cycle
 template <typename T>
-static void vcycle(Problem& P, size_t l, size_t lt, cudaStream_t s) {
+static void vcycle(Problem& P, size_t l, size_t lt, cudaStream_t s, bool from_zero = true) {
   const int Tn = 256;
   Level& L = P.lv[l];
   T* u = (T*)L.u;
@@ -561,13 +579,15 @@ static void vcycle(Problem& P, size_t l, size_t lt, cudaStream_t s) {
   LevelView<T> V = view<T>(L);
   LevelK<T> K = levk<T>(L);
   const int64_t ncol = (L.g.N / L.g.n) * ((L.g.n + 1) / 2);
-  IIM_LAUNCH(k_zero<T>, ceil_div(L.g.N, Tn), Tn, 0, s, u, L.g.N);
+  if (from_zero) IIM_LAUNCH(k_zero<T>, ceil_div(L.g.N, Tn), Tn, 0, s, u, L.g.N);
   for (int it = 0; it < P.opt.nu1; ++it)
     for (int c = 0; c < 2; ++c) IIM_LAUNCH(k_smooth<T>, ceil_div(ncol, Tn), Tn, 0, s, V, K.ih2, K.dreg, u, f, c);
   Level& C = P.lv[l + 1];
   IIM_LAUNCH(k_resid_restrict<T>, ceil_div(C.g.N, Tn), Tn, 0, s, V, K.ih2, K.dreg, u, f, C.g, C.aux, (T*)C.f,
              C.f_bf16);
-  vcycle<T>(P, l + 1, lt, s);
+  if (l + 1 == lt) vcycle<T>(P, l + 1, lt, s);
+  else
+    for (int g = 0; g < P.opt.cycle; ++g) vcycle<T>(P, l + 1, lt, s, g == 0);
   IIM_LAUNCH(k_prolong<T>, ceil_div(L.g.N, Tn), Tn, 0, s, L.g, L.aux, u, C.g, C.aux, (const T*)C.u,
              P.desc.bc == IIM_BC_NEUMANN);
   for (int it = 0; it < P.opt.nu2; ++it)
@@ -630,7 +650,7 @@ void mg_coarse_factor(Problem& P, cudaStream_t s) {
     size_t sm = sizeof(double) * (size_t)cn * cn;
     int in_smem = sm <= 200 * 1024;
     if (2 * sm <= 200 * 1024) { in_smem = 2; sm *= 2; }
-    if (in_smem) cudaFuncSetAttribute(k_coarse_lu<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (in_smem) smem_optin((const void*)k_coarse_lu<double>);
     IIM_LAUNCH(k_coarse_lu<double>, 1, 1024, in_smem ? sm : 0, s, P.coarse_lu64, cn, P.coarse_piv,
                P.coarse_lu64 + (size_t)cn * cn, P.d_status, in_smem);
   } else {
@@ -639,7 +659,7 @@ void mg_coarse_factor(Problem& P, cudaStream_t s) {
     size_t sm = sizeof(float) * (size_t)cn * cn;
     int in_smem = sm <= 200 * 1024;
     if (2 * sm <= 200 * 1024) { in_smem = 2; sm *= 2; }
-    if (in_smem) cudaFuncSetAttribute(k_coarse_lu<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (in_smem) smem_optin((const void*)k_coarse_lu<float>);
     IIM_LAUNCH(k_coarse_lu<float>, 1, 1024, in_smem ? sm : 0, s, P.coarse_lu32, cn, P.coarse_piv,
                P.coarse_lu32 + (size_t)cn * cn, P.d_status, in_smem);
   }
@@ -765,11 +785,7 @@ void eng_launch_mg(const EngArgs& A, const EngMgStep& st, size_t tail_smem, cuda
     return;
   }
   if (st.kind == 1) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_eng_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      attr = true;
-    }
+    smem_optin((const void*)k_eng_tail);
     IIM_LAUNCH(k_eng_tail, eng_grid((const void*)k_eng_tail, kTailThreads, tail_smem), kTailThreads, tail_smem, s, A);
     return;
   }

@@ -24,7 +24,7 @@ namespace iim {
 // admission; the exact size, known once the problem exists, is what is charged.
 static size_t estimate_bytes(const iim_problem_desc& d, const iim_options& o) {
   const double N = (double)d.n * d.n * (d.dim == 3 ? d.n : 1);
-  const double vec = 8.0 * (2 * o.restart + 3);               // V, Z, x, tmp
+  const double vec = 8.0 * (o.restart + 1 + (o.krylov == IIM_KRYLOV_GMRES_LEFT ? 1 : o.restart) + 2);   // V, Z, x, tmp
   const double grid = 1.0 + 8.0 * d.dim + 8.0 + 8.0;          // phase, edge flags/ids, affected flags/ids, b
   const double mg = (d.dim == 2 ? 4.0 / 3.0 : 8.0 / 7.0) * (1.0 + 12.0 + 12.0);   // phase, aux/flag/idx, u/u2/f
   const double K = d.dim == 2 ? 3.0 * d.n : 1.5 * (double)d.n * d.n;
@@ -78,6 +78,8 @@ struct Server {
   int64_t runs = 0;
   int mode = 0;                  // 0: batched engine, 1: each request's solve graph on its own stream
   std::vector<Request*> running;  // mode 1
+  // ids to report to the caller (kept until a step has room for them)
+  std::deque<int64_t> note_need, note_fin;
   double t_step = 0, t_copy = 0, t_create = 0;   // host seconds: step calls, result copies, creation (workers)
   Clock::time_point t0;
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
@@ -268,7 +270,7 @@ iim_status iim_server_step(iim_server* H, int64_t* need_data, int cap_need, int*
         r->error = st;
         r->t_done = S.now();
         free_problem(S, r);
-        if (finished && nf < cap_fin) finished[nf++] = r->id;
+        S.note_fin.push_back(r->id);
         continue;
       }
       r->state = kRunning;
@@ -289,7 +291,7 @@ iim_status iim_server_step(iim_server* H, int64_t* need_data, int cap_need, int*
         r->error = st;
         r->t_done = S.now();
         free_problem(S, r);
-        if (finished && nf < cap_fin) finished[nf++] = r->id;
+        S.note_fin.push_back(r->id);
         continue;
       }
       r->slot = slot;
@@ -316,7 +318,7 @@ iim_status iim_server_step(iim_server* H, int64_t* need_data, int cap_need, int*
     r->state = r->info.status == IIM_OK ? kFinished : kFailed;
     r->error = (iim_status)r->info.status;
     free_problem(S, r);
-    if (finished && nf < cap_fin) finished[nf++] = r->id;
+    S.note_fin.push_back(r->id);
   }
   // 4. requests the workers have created: check the exact size against the budget
   std::vector<Request*> got;
@@ -334,7 +336,7 @@ iim_status iim_server_step(iim_server* H, int64_t* need_data, int cap_need, int*
       r->t_done = S.now();
       S.free_streams.push_back(r->stream);
       r->stream = nullptr;
-      if (finished && nf < cap_fin) finished[nf++] = r->id;
+      S.note_fin.push_back(r->id);
       continue;
     }
     r->bytes = r->prob->P.bytes;
@@ -349,7 +351,7 @@ iim_status iim_server_step(iim_server* H, int64_t* need_data, int cap_need, int*
         r->state = kFailed;
         r->error = IIM_ERR_BUDGET;
         r->t_done = S.now();
-        if (finished && nf < cap_fin) finished[nf++] = r->id;
+        S.note_fin.push_back(r->id);
       } else {
         r->state = kQueued;
         S.queue.push_front(r);
@@ -359,7 +361,7 @@ iim_status iim_server_step(iim_server* H, int64_t* need_data, int cap_need, int*
     S.in_use += r->bytes;
     S.peak = S.in_use > S.peak ? S.in_use : S.peak;
     r->state = kNeedData;
-    if (need_data && nn < cap_need) need_data[nn++] = r->id;
+    S.note_need.push_back(r->id);
   }
   // 5. admission by budget, in submission order: reserve and hand to the workers
   while (!S.queue.empty()) {
@@ -385,6 +387,15 @@ iim_status iim_server_step(iim_server* H, int64_t* need_data, int cap_need, int*
     S.cv.notify_one();
   }
   S.peak = S.in_use > S.peak ? S.in_use : S.peak;
+  // report as many as the caller's arrays hold; the rest wait for the next step
+  while (!S.note_need.empty() && need_data && nn < cap_need) {
+    need_data[nn++] = S.note_need.front();
+    S.note_need.pop_front();
+  }
+  while (!S.note_fin.empty() && finished && nf < cap_fin) {
+    finished[nf++] = S.note_fin.front();
+    S.note_fin.pop_front();
+  }
   S.t_step += std::chrono::duration<double>(Clock::now() - t_enter).count();
   if (n_need) *n_need = nn;
   if (n_fin) *n_fin = nf;
@@ -436,7 +447,7 @@ iim_status iim_server_take(iim_server* H, int64_t id, double* x_host, iim_solve_
 }
 
 iim_status iim_server_stats(iim_server* H, size_t* bytes_in_use, size_t* peak_bytes, int* queued, int* resident,
-                            int64_t* runs, double* host_seconds) {
+                            int64_t* runs, double* host_seconds, int* states) {
   if (!H) return IIM_ERR_INVALID_ARG;
   Server& S = H->S;
   if (host_seconds) {
@@ -447,6 +458,10 @@ iim_status iim_server_stats(iim_server* H, size_t* bytes_in_use, size_t* peak_by
   }
   if (bytes_in_use) *bytes_in_use = S.in_use;
   if (peak_bytes) *peak_bytes = S.peak;
+  if (states) {
+    for (int k = 0; k < 8; ++k) states[k] = 0;
+    for (auto& kv : S.reqs) ++states[kv.second->state];
+  }
   if (queued) *queued = (int)S.queue.size();
   if (resident) *resident = S.resident;
   if (runs) *runs = S.runs;

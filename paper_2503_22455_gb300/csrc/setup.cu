@@ -730,13 +730,21 @@ __global__ void __launch_bounds__(128) k_fit_warp(FitParams P, WarpFitSmem L, in
 // region size is tried here; fits that need a larger region, have too few or too
 // many rows, or fail the rank test are flagged and redone by k_fit (one CTA each),
 // which applies the same rules.
-constexpr int kQuadRows = 56;          // rows of X_c a quarter-warp holds (typical: 23 for q = 4, 44 for q = 6)
+constexpr int kQuadRows = 48;          // rows of X_c a quarter-warp holds (q = 6: 38..46 rows; q = 4: about 23)
 
+// Shared memory of one fit (doubles): V [M][LDQ], then the target rows S [4][LDQ] (which
+// hold the node offsets [kQuadRows][2] before V is filled, and R^-T c_t in their first M
+// entries before the reflectors are applied), alpha, 1/alpha, beta [M] each, and the node
+// indices (ints).  LDQ is odd, so the eight lanes of a fit, each on its own column, hit
+// distinct banks; the size is 8 mod 16 doubles, so the two fits of a half warp start 16
+// banks apart.  M = 28: 13.5 KB per fit, four warps per SM.
 struct QuadFitSmem {
   int M;
   __host__ __device__ int LDQ() const { return kQuadRows + 1; }
   __host__ __device__ size_t doubles() const {
-    return (size_t)M * LDQ() + 4 * LDQ() + 4 * M + 3 * M + 2 * kQuadRows + kQuadRows / 2 + 1;
+    const int s_rel = 4 * LDQ() > 2 * kQuadRows ? 4 * LDQ() : 2 * kQuadRows;
+    const size_t raw = (size_t)M * LDQ() + s_rel + 3 * M + kQuadRows / 2;
+    return raw + ((8 - (int)(raw % 16)) + 16) % 16;
   }
 };
 
@@ -757,13 +765,12 @@ __global__ void __launch_bounds__(32) k_fit_quad(FitParams P, QuadFitSmem Lq, in
   const int LDQ = Lq.LDQ(), n = g.n;
   double* base = smq + (size_t)(wib * 4 + qf) * Lq.doubles();
   double* V = base;                      // [M][LDQ]
-  double* S = V + (size_t)M * LDQ;       // [4][LDQ]
-  double* Y = S + 4 * LDQ;               // [4][M]
-  double* alpha = Y + 4 * M;             // [M]
+  double* S = V + (size_t)M * LDQ;       // [4][LDQ] (after the QR)
+  double* rel = S;                       // [kQuadRows][2] (until V is filled)
+  double* alpha = S + (4 * LDQ > 2 * kQuadRows ? 4 * LDQ : 2 * kQuadRows);   // [M]
   double* ialpha = alpha + M;            // [M]
   double* beta = ialpha + M;             // [M]
-  double* rel = beta + M;                // [kQuadRows][2]
-  int* nodes = (int*)(rel + 2 * kQuadRows);
+  int* nodes = (int*)(beta + M);         // [kQuadRows]
   bool active = f < nfit_here;
   const int c = P.interface_ ? (f >> 1) : f;
   const bool sig_plus = P.interface_ ? ((f & 1) == 0) : true;
@@ -780,6 +787,7 @@ __global__ void __launch_bounds__(32) k_fit_quad(FitParams P, QuadFitSmem Lq, in
   }
   const double ns0 = sig_plus ? -nrm[0] : nrm[0], ns1 = sig_plus ? -nrm[1] : nrm[1];
   const double an = P.q + 1.0, at = P.q / 2 + 1.0;
+  const double an2 = an * an, at2 = at * at;
   const int rad = (int)ceil(an) + 1;
   int wlo0 = 0, wlo1 = 0, we0 = 1, we1 = 1;
   if (active) {
@@ -826,7 +834,8 @@ __global__ void __launch_bounds__(32) k_fit_quad(FitParams P, QuadFitSmem Lq, in
     r1 = (node_x(g, i1) - xc[1]) * ih;
     const double d2 = r0 * r0 + r1 * r1, t = r0 * ns0 + r1 * ns1;
     const double tau2 = fmax(d2 - t * t, 0.0);
-    return t >= 0.0 && tau2 / (at * at) + t * t / (an * an) <= 1.0;
+    // tau^2 / at^2 + t^2 / an^2 <= 1 multiplied through by at^2 an^2 (small exact integers)
+    return t >= 0.0 && tau2 * an2 + (t * t) * at2 <= at2 * an2;
   };
   // one pass over the window: selection bits per lane (chunks of at most 64 positions)
   const int chunk = (total + 7) / 8;
@@ -863,50 +872,67 @@ __global__ void __launch_bounds__(32) k_fit_quad(FitParams P, QuadFitSmem Lq, in
   }
   __syncwarp();
   const int m = active ? R + 1 : 0;
-  for (int e = ql; e < m * M; e += 8) {
-    const int col = e / m, row = e - col * m;
-    V[(size_t)col * LDQ + row] = row == 0 ? (col == 0 ? 1.0 : 0.0) : monomial(P.monos + 3 * col, rel + 2 * (row - 1), 2);
+  {
+    // Vandermonde rows over the lanes: row 0 is x_c itself (xi = 0), row 1 + o the o-th
+    // node.  Powers of each coordinate once per row, then one product per monomial, in
+    // the graded order of the exponent table (degree, then decreasing x exponent).
+    constexpr int Q = M == 28 ? 6 : 4;
+    static_assert((Q + 1) * (Q + 2) / 2 == M, "2D monomial count");
+    for (int row = ql; row < m; row += 8) {
+      const double x0 = row == 0 ? 0.0 : rel[2 * (row - 1)], x1 = row == 0 ? 0.0 : rel[2 * (row - 1) + 1];
+      double px[Q + 1], py[Q + 1];
+      px[0] = 1.0;
+      py[0] = 1.0;
+#pragma unroll
+      for (int e = 1; e <= Q; ++e) {
+        px[e] = px[e - 1] * x0;
+        py[e] = py[e - 1] * x1;
+      }
+      int col = 0;
+#pragma unroll
+      for (int deg = 0; deg <= Q; ++deg)
+#pragma unroll
+        for (int a = deg; a >= 0; --a) V[(size_t)(col++) * LDQ + row] = px[a] * py[deg - a];
+    }
   }
   __syncwarp();
-  // Householder QR, rows over the 8 lanes.  The trailing columns go four at a time
-  // (four independent products and reductions in flight); each product and update is
-  // the same sequence of operations as one column at a time.
+  // Householder QR.  The column's norm goes over the rows (8 lanes, tree sum); every lane
+  // of the quarter forms the reflector's scalars, then each lane applies it to its own
+  // trailing columns (k + 1 + ql, k + 9 + ql, ...): a product and an update over the rows
+  // with no reduction across lanes.
   for (int k = 0; k < M; ++k) {
     double* vk = V + (size_t)k * LDQ;
     double s = 0;
     for (int r = k + ql; r < m; r += 8) s = fma(vk[r], vk[r], s);
     q8_sum(s);
+    const double x0 = m > 0 ? vk[k] : 0.0;
+    const double nr = sqrt(s);
+    const double a = x0 >= 0 ? -nr : nr;
+    const double vtv = 2.0 * (s - x0 * a);
+    const double bk = vtv > 0 ? 2.0 / vtv : 0.0;
+    __syncwarp();                       // vk[k] read by every lane before it changes
     if (ql == 0 && m > 0) {
-      const double x0 = vk[k];
-      const double nr = sqrt(s);
-      const double a = x0 >= 0 ? -nr : nr;
-      const double vtv = 2.0 * (s - x0 * a);
       vk[k] = x0 - a;
       alpha[k] = a;
-      beta[k] = vtv > 0 ? 2.0 / vtv : 0.0;
+      beta[k] = bk;
     }
     __syncwarp();
-    const double bk = m > 0 ? beta[k] : 0.0;
-    for (int c0 = k + 1; c0 < M; c0 += 4) {
-      double d[4] = {0.0, 0.0, 0.0, 0.0};
-      for (int r = k + ql; r < m; r += 8) {
-        const double v = vk[r];
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-          if (c0 + t < M) d[t] = fma(v, V[(size_t)(c0 + t) * LDQ + r], d[t]);
+    for (int j = k + 1 + ql; j < M; j += 8) {
+      double* vj = V + (size_t)j * LDQ;
+      double d0 = 0.0, d1 = 0.0;
+      int r = k;
+      for (; r + 1 < m; r += 2) {
+        d0 = fma(vk[r], vj[r], d0);
+        d1 = fma(vk[r + 1], vj[r + 1], d1);
       }
-#pragma unroll
-      for (int t = 0; t < 4; ++t)
-        if (c0 + t < M) {
-          q8_sum(d[t]);
-          d[t] *= bk;
-        }
-      for (int r = k + ql; r < m; r += 8) {
-        const double v = vk[r];
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-          if (c0 + t < M) V[(size_t)(c0 + t) * LDQ + r] = fma(-d[t], v, V[(size_t)(c0 + t) * LDQ + r]);
+      if (r < m) d0 = fma(vk[r], vj[r], d0);
+      const double sc = (d0 + d1) * bk;
+      r = k;
+      for (; r + 1 < m; r += 2) {
+        vj[r] = fma(-sc, vk[r], vj[r]);
+        vj[r + 1] = fma(-sc, vk[r + 1], vj[r + 1]);
       }
+      if (r < m) vj[r] = fma(-sc, vk[r], vj[r]);
     }
     __syncwarp();
   }
@@ -923,7 +949,7 @@ __global__ void __launch_bounds__(32) k_fit_quad(FitParams P, QuadFitSmem Lq, in
   // stencil rows of all targets together (rows over the 8 lanes)
   const int nt = P.w + 1;                // ghosts and the normal derivative (every condition)
   for (int t = 0; t < nt; ++t) {
-    double* y = Y + t * M;
+    double* y = S + t * LDQ;
     if (t < P.w) {
       int mlo0 = (int)(lo % n), mlo1 = (int)(lo / n);
       int gm0 = mlo0, gm1 = mlo1;
@@ -939,23 +965,23 @@ __global__ void __launch_bounds__(32) k_fit_quad(FitParams P, QuadFitSmem Lq, in
     }
   }
   __syncwarp();
-  for (int i = 0; i < M; ++i) {                    // y_t = R^-T c_t
+  for (int i = 0; i < M; ++i) {                    // y_t = R^-T c_t, in place in S_t
     double part[4] = {0.0, 0.0, 0.0, 0.0};
     for (int l = ql; l < i; l += 8) {
       const double rv = V[(size_t)i * LDQ + l];
 #pragma unroll
       for (int t = 0; t < 4; ++t)
-        if (t < nt) part[t] = fma(rv, Y[t * M + l], part[t]);
+        if (t < nt) part[t] = fma(rv, S[t * LDQ + l], part[t]);
     }
 #pragma unroll
     for (int t = 0; t < 4; ++t)
       if (t < nt) q8_sum(part[t]);
     if (ql == 0)
-      for (int t = 0; t < nt; ++t) Y[t * M + i] = (Y[t * M + i] - part[t]) * ialpha[i];
+      for (int t = 0; t < nt; ++t) S[t * LDQ + i] = (S[t * LDQ + i] - part[t]) * ialpha[i];
     __syncwarp();
   }
-  for (int t = 0; t < nt; ++t)
-    for (int r = ql; r < m; r += 8) S[t * LDQ + r] = r < M ? Y[t * M + r] : 0.0;
+  for (int t = 0; t < nt; ++t)                      // [y_t; 0]
+    for (int r = M + ql; r < m; r += 8) S[t * LDQ + r] = 0.0;
   __syncwarp();
   for (int k = M - 1; k >= 0; --k) {                // s_t = Q [y_t; 0]
     const double* vk = V + (size_t)k * LDQ;
@@ -1215,7 +1241,7 @@ iim_status setup_fits(Problem& P) {
   int wpb = (int)((200 * 1024) / per_warp);
   wpb = wpb > 4 ? 4 : (wpb < 1 ? 1 : wpb);
   const size_t smw = per_warp * wpb;
-  cudaError_t e = cudaFuncSetAttribute(k_fit_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw);
+  cudaError_t e = smem_optin((const void*)k_fit_warp);
   if (e != cudaSuccess) {
     set_error(std::string("least-squares kernel shared memory: ") + cudaGetErrorString(e));
     return IIM_ERR_CUDA;
@@ -1226,7 +1252,7 @@ iim_status setup_fits(Problem& P) {
     Q.M = P.M;
     const size_t smq = sizeof(double) * Q.doubles() * 4;       // one warp, four fits
     const void* kq = P.M == 15 ? (const void*)k_fit_quad<15> : (const void*)k_fit_quad<28>;
-    e = cudaFuncSetAttribute(kq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
+    e = smem_optin(kq);
     if (e != cudaSuccess) {
       set_error(std::string("least-squares kernel shared memory: ") + cudaGetErrorString(e));
       return IIM_ERR_CUDA;
@@ -1239,7 +1265,7 @@ iim_status setup_fits(Problem& P) {
   // CTA per fit for the flagged ones (more rows than a warp holds, or a grown region)
   size_t smem = fit_smem_bytes(P);
   if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = smem_optin((const void*)k_fit);
     if (e != cudaSuccess) {
       set_error(std::string("least-squares kernel shared memory: ") + cudaGetErrorString(e));
       return IIM_ERR_CUDA;

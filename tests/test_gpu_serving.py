@@ -57,7 +57,8 @@ def test_served_results_equal_alone_and_single_solves(env, mode):
         assert lat > 0
     for (x, info, lat, st, sp) in mixed:
         (alone,), _ = _serve(iim, [sp], 1 << 36, mode=mode)
-        assert np.array_equal(alone[0], x), sp.name
+        assert np.array_equal(alone[0], x), (sp.name, sp.n, sp.dim, "alone", alone[1].as_dict(), "mixed", info.as_dict(),
+                                             float(np.max(np.abs(alone[0] - x))))
         assert alone[1].iters == info.iters
     # and the plain single solve of two of them
     for (x, info, lat, st, sp) in mixed[:2]:
@@ -76,3 +77,19 @@ def test_request_larger_than_budget_is_refused(env):
         S.submit(iim.desc_from_spec(sp))
     assert e.value.status == 7
     S.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_every_request_reported_with_one_id_per_step(env, mode):
+    """Arrays of capacity 1: ids that do not fit are reported by later steps, each once,
+    and the final state counts are all zero once every request is taken."""
+    torch, iim = env
+    specs = [sp for _, sp in _trace()][:6]
+    S = iim.Server(iim.default_options(), budget_bytes=1 << 36, max_slots=8, ticks_per_run=3, mode=mode, cap=1)
+    arrivals = [(0.0, iim.desc_from_spec(sp), sp) for sp in specs]
+    out, wall = iim.serve(S, arrivals, lambda view, sp: set_gpu_data(view, sp), realtime=False, deadline_s=120)
+    st = S.stats()
+    S.close()
+    assert len(out) == len(specs)
+    assert all(o[3] == 0 for o in out.values())
+    assert sum(st["states"].values()) == 0

@@ -122,3 +122,18 @@ def test_left_gmres_minimises_the_preconditioned_residual():
     assert np.max(np.abs(xl[unk] - x_ref)) < 1e-8 * np.max(np.abs(x_ref))
     y_right = np.linalg.lstsq(A @ Q, b[unk], rcond=None)[0]
     assert np.max(np.abs(Q @ y_right - x_ref)) > 1e-4 * np.max(np.abs(x_ref))
+
+
+def test_left_gmres_pure_neumann_augmented_matches_fgmres():
+    """The augmented system of Sec. 2.3 is nonsingular: left GMRES and FGMRES converge to
+    the same (u, alpha)."""
+    spec = W.ProblemSpec(n=40, geometry=W.Geometry(W.ELLIPSE, (0.01, -0.02, 0.6, 0.45, 0.3), True),
+                         bc=W.NEUMANN, order=4, solution=W.sin_cos_2d(2.0, 0.3, 1.5, 0.7))
+    P = OracleProblem(spec)
+    assert P.singular
+    f, data = P.data()
+    xr, ir, _ = P.solve(f, data, tol=1e-13)
+    xl, il, _ = P.solve_left(f, data, tol=1e-13)
+    assert ir["converged"] and il["converged"]
+    assert np.max(np.abs(xl - xr)) < 1e-9 * np.max(np.abs(xr))
+    assert abs(il["alpha"] - ir["alpha"]) < 1e-9 * max(abs(ir["alpha"]), 1e-300) + 1e-12
