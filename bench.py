@@ -738,6 +738,7 @@ def roofline(P, iim, torch, stream, applies_per_solve):
                                "us_per_solve": us.value * applies_per_solve}
     if not out:
         return None
+    hbm = hbm_kernels(P, iim, torch, pk)
     top = max(out.values(), key=lambda r: r["us_per_solve"])
     achieved = top["flop"] / (top["us"] * 1e-6) / 1e12
 
@@ -751,7 +752,41 @@ def roofline(P, iim, torch, stream, applies_per_solve):
             "flop_per_launch": top["flop"],
             "peak_note": "derived FP64 peak: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock (measured 0.598 TFMA/s "
                          "at 1.995 GHz agrees); the measured copy and bf16 peaks do not apply to FP64 work",
-            "kernels": [entry(r) for r in out.values()]}
+            "kernels": [entry(r) for r in out.values()], "hbm_kernels": hbm}
+
+
+def hbm_kernels(P, iim, torch, pk):
+    """Achieved HBM bandwidth of the memory-bound kernels of one iteration: the first level's
+    fused multigrid kernels, the stencil and the orthogonalisation passes, each timed alone
+    after an L2 flush (inputs from HBM) and back to back (inputs in L2), against the measured
+    copy bandwidth.  Algorithmic bytes per node: multigrid down 8 (v) + 4 (aux) + 4 (f) +
+    4 (u) + 1 (coarse f), plus 1 (phase) when beta differs between the phases; up 4 (u) +
+    4 (aux) + 4 (f) + 1 (coarse u) + 8 (z); stencil 8 (u) + 8 (w) + 1 (phase); multi-dot and
+    update over j + 1 = restart/2 + 1 vectors: 8 (j + 2) and 8 (j + 3)."""
+    peak = pk.get("hbm_gbs")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    N, j = P.N, P.options.restart // 2
+    beta2 = 1 if P.desc.beta_plus != P.desc.beta_minus else 0
+    cases = [("mg_down0", f"k_mg2d<float,64,16,5> first level", 21 + beta2),
+             ("mg_up0", f"k_mg2d<float,64,16,6> first level", 21),
+             ("stencil", "k_ho_stencil", 17),
+             ("multidot", f"k_multidot<{j + 1}>", 8 * (j + 2)),
+             ("update", f"k_update<{j + 1}>", 8 * (j + 3))]
+    res = []
+    for which, name, bpn in cases:
+        try:
+            cold = iim.kernel_time(P, which, reps=10, flush=flush)
+            warm = iim.kernel_time(P, which, reps=50)
+        except iim.IIMError:
+            continue
+        b = bpn * N
+        r = {"kernel": name, "bytes_per_launch": b, "us_hbm": cold, "gbs_hbm": b / cold / 1e3,
+             "us_l2": warm, "gbs_l2": b / warm / 1e3}
+        if peak:
+            r["frac_hbm"] = r["gbs_hbm"] / peak
+        res.append(r)
+    del flush
+    return res
 
 
 def cpu_baseline(n, gpu_iters):

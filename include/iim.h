@@ -59,7 +59,8 @@ typedef enum {
   IIM_ERR_CAPACITY = 11      /* re-setup needs more workspace than allocated */
 } iim_status;
 
-enum { IIM_GEOM_CIRCLE = 0, IIM_GEOM_ELLIPSE = 1, IIM_GEOM_STAR = 2, IIM_GEOM_SPHERE = 3, IIM_GEOM_ELLIPSOID = 4 };
+enum { IIM_GEOM_CIRCLE = 0, IIM_GEOM_ELLIPSE = 1, IIM_GEOM_STAR = 2, IIM_GEOM_SPHERE = 3, IIM_GEOM_ELLIPSOID = 4,
+       IIM_GEOM_PERTURBED_SPHERE = 5 };
 enum { IIM_BC_DIRICHLET = 0, IIM_BC_NEUMANN = 1, IIM_BC_INTERFACE = 2 };
 enum { IIM_BOX_NONE = 0, IIM_BOX_DIRICHLET = 1 };
 /* Multigrid precision: FP32, FP64, or FP32 with every restricted residual (the
@@ -81,6 +82,11 @@ enum { IIM_KRYLOV_FGMRES = 0, IIM_KRYLOV_GMRES_LEFT = 1 };
  *   STAR      cx cy r0 amp m phase    g = |x - c| - (r0 + amp sin(m theta + phase))
  *   SPHERE    cx cy cz R
  *   ELLIPSOID cx cy cz a0 a1 a2       axis aligned
+ *   PERTURBED_SPHERE cx cy cz rho0 rho1
+ *                                     g = r - rho0 - rho1 Y(e), r = |x - c|, e = (x - c)/r,
+ *                                     Y = (3 sqrt(3)/2) (e_x^2 - e_y^2) e_z (a degree-3 spherical
+ *                                     harmonic scaled to max |Y| = 1; the radially perturbed
+ *                                     sphere of the paper's 3D verification, Sec. 4.2)
  */
 typedef struct {
   int dim;               /* 2 or 3 */
@@ -367,9 +373,17 @@ iim_status iim_gradient(iim_problem* p, const double* u_dev, double* grad_dev);
  * which: 0 high-order stencil, 1 ghost values, 2 corrections (Eq. 12 operator
  * kernels); 3 one red half sweep on the finest level; 4 FGMRES multi-dot and
  * 5 update over restart/2 + 1 vectors; 6 a whole V-cycle; 7 the whole operator;
- * 8 the least-squares fits of the set-up (Sec. 2.1-2.2).
+ * 8 the least-squares fits of the set-up (Sec. 2.1-2.2); 9 / 10 the first level's fused
+ * down / up multigrid kernel (2D, V(2,2); IIM_ERR_INVALID_ARG otherwise); 11 the coarse
+ * single-CTA tail of the V-cycle.
  * Overwrites the problem's work vectors: call it between solves.  Synchronises. */
 iim_status iim_kernel_time(iim_problem* p, int which, int reps, double* us);
+
+/* The same, each timed launch alone and preceded by an overwrite of flush_dev
+ * (flush_bytes of caller-owned device memory, larger than L2), so that the launch reads
+ * its inputs from HBM.  flush_dev = NULL or flush_bytes = 0: as iim_kernel_time. */
+iim_status iim_kernel_time_flushed(iim_problem* p, int which, int reps, void* flush_dev, size_t flush_bytes,
+                                   double* us);
 
 /* Least-squares fits of the current set-up: their number, the sum of their rows
  * (|X_c| + 1 each) and the monomial count M (for work estimates).  Synchronises. */

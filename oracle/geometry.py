@@ -14,7 +14,7 @@ import math
 
 import numpy as np
 
-from workloads import CIRCLE, ELLIPSE, STAR, SPHERE, ELLIPSOID
+from workloads import CIRCLE, ELLIPSE, STAR, SPHERE, ELLIPSOID, PERTURBED_SPHERE, PERTURB_SCALE
 
 
 class LevelSet:
@@ -46,6 +46,15 @@ class LevelSet:
             rho = np.hypot(dx, dy)
             th = np.arctan2(dy, dx)
             return rho - (p[2] + p[3] * np.sin(p[4] * th + p[5]))
+        if self.kind == PERTURBED_SPHERE:
+            # g = r - rho0 - rho1 c Q(d) / r^3 with d = x - centre, r = |d|, Q = (dx^2 - dy^2) dz:
+            # Q / r^3 is the harmonic (e_x^2 - e_y^2) e_z of the direction e = d / r
+            # at the centre itself (r = 0) the direction is undefined: the harmonic term is 0
+            d = X - np.array(p[:3])
+            r = np.sqrt(np.sum(d * d, axis=-1))
+            Q = (d[..., 0] ** 2 - d[..., 1] ** 2) * d[..., 2]
+            Y = np.divide(Q, r ** 3, out=np.zeros_like(r), where=r > 0)
+            return r - p[3] - p[4] * PERTURB_SCALE * Y
         raise ValueError("unknown geometry kind")
 
     def phi(self, X):
@@ -74,6 +83,14 @@ class LevelSet:
             er = np.stack([dx / rho, dy / rho], axis=-1)
             et = np.stack([-dy / rho, dx / rho], axis=-1)
             return er - (rp / rho)[..., None] * et
+        if self.kind == PERTURBED_SPHERE:
+            d = X - np.array(p[:3])
+            r = np.sqrt(np.sum(d * d, axis=-1))[..., None]
+            Q = ((d[..., 0] ** 2 - d[..., 1] ** 2) * d[..., 2])[..., None]
+            gQ = np.stack([2 * d[..., 0] * d[..., 2], -2 * d[..., 1] * d[..., 2],
+                           d[..., 0] ** 2 - d[..., 1] ** 2], axis=-1)
+            # grad (Q r^-3) = grad Q r^-3 - 3 Q d r^-5
+            return d / r - p[4] * PERTURB_SCALE * (gQ / r ** 3 - 3 * Q * d / r ** 5)
         raise ValueError
 
     def normal(self, X):
@@ -96,25 +113,52 @@ class LevelSet:
             r2 = -p[3] * p[4] ** 2 * np.sin(p[4] * th + p[5])
             # curvature of the polar curve r(theta)
             return np.abs(r * r + 2 * r1 * r1 - r * r2) / (r * r + r1 * r1) ** 1.5
-        # quadrics: shape operator P H P / |grad g| on the tangent space
+        # shape operator P H P / |grad g| on the tangent space (H: Hessian of g)
         if self.kind == ELLIPSE:
             c, s = math.cos(p[4]), math.sin(p[4])
             R = np.array([[c, -s], [s, c]])
-            H = R @ np.diag([2 / p[2] ** 2, 2 / p[3] ** 2]) @ R.T
+            H = np.broadcast_to(R @ np.diag([2 / p[2] ** 2, 2 / p[3] ** 2]) @ R.T, X.shape[:-1] + (2, 2))
+        elif self.kind == ELLIPSOID:
+            H = np.broadcast_to(np.diag(2 / np.array(p[3:6]) ** 2), X.shape[:-1] + (3, 3))
         else:
-            H = np.diag(2 / np.array(p[3:6]) ** 2)
+            H = self.hess_g(X)
         G = self.grad_g(X)
         gn = np.linalg.norm(G, axis=-1)
         n = G / gn[..., None]
         out = np.zeros(X.shape[:-1])
         flat_n = n.reshape(-1, self.dim)
         flat_g = gn.reshape(-1)
+        flat_H = np.reshape(H, (-1, self.dim, self.dim))
         res = out.reshape(-1)
         for k in range(flat_n.shape[0]):
             P = np.eye(self.dim) - np.outer(flat_n[k], flat_n[k])
-            S = P @ H @ P / flat_g[k]
+            S = P @ flat_H[k] @ P / flat_g[k]
             res[k] = np.max(np.abs(np.linalg.eigvalsh(S)))
         return res.reshape(X.shape[:-1])
+
+    def hess_g(self, X):
+        """Hessian of g for PERTURBED_SPHERE:
+        (I - e e^T) / r - rho1 c [Hess Q r^-3 - 3 r^-5 (grad Q d^T + d grad Q^T)
+                                  + Q (-3 r^-5 I + 15 r^-7 d d^T)]."""
+        p = self.p
+        if self.kind != PERTURBED_SPHERE:
+            raise ValueError("hess_g: perturbed sphere only")
+        d = X - np.array(p[:3])
+        r = np.sqrt(np.sum(d * d, axis=-1))[..., None, None]
+        dd = d[..., :, None] * d[..., None, :]
+        I = np.eye(3)
+        Q = ((d[..., 0] ** 2 - d[..., 1] ** 2) * d[..., 2])[..., None, None]
+        gQ = np.stack([2 * d[..., 0] * d[..., 2], -2 * d[..., 1] * d[..., 2],
+                       d[..., 0] ** 2 - d[..., 1] ** 2], axis=-1)
+        HQ = np.zeros(X.shape[:-1] + (3, 3))
+        HQ[..., 0, 0] = 2 * d[..., 2]
+        HQ[..., 1, 1] = -2 * d[..., 2]
+        HQ[..., 0, 2] = HQ[..., 2, 0] = 2 * d[..., 0]
+        HQ[..., 1, 2] = HQ[..., 2, 1] = -2 * d[..., 1]
+        cross = gQ[..., :, None] * d[..., None, :] + d[..., :, None] * gQ[..., None, :]
+        Hr = (I - dd / r ** 2) / r
+        Hp = HQ / r ** 3 - 3 * cross / r ** 5 + Q * (-3 * I / r ** 5 + 15 * dd / r ** 7)
+        return Hr - p[4] * PERTURB_SCALE * Hp
 
     def _ellipse_local(self, X):
         p = self.p

@@ -17,7 +17,7 @@ IIM_OK = 0
 IIM_ERR_TIMEOUT = 8
 STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "curvature", 3: "rank", 4: "singular", 5: "not converged",
                 6: "breakdown", 7: "budget", 8: "timeout", 9: "cuda", 10: "geometry", 11: "capacity"}
-GEOM = {"circle": 0, "ellipse": 1, "star": 2, "sphere": 3, "ellipsoid": 4}
+GEOM = {"circle": 0, "ellipse": 1, "star": 2, "sphere": 3, "ellipsoid": 4, "perturbed_sphere": 5}
 BC = {"dirichlet": 0, "neumann": 1, "interface": 2}
 MG_FP32, MG_FP64, MG_FP32_BF16R = 0, 1, 2
 CYCLE_V, CYCLE_W = 1, 2
@@ -81,6 +81,8 @@ SIGNATURES = {
     "iim_batch_solve": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
                                        ctypes.POINTER(SolveInfo)]),
     "iim_kernel_time": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "iim_kernel_time_flushed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                               ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)]),
     "iim_launch_count": (ctypes.c_int64, []),
     "iim_engine_create": (ctypes.c_int, [ctypes.POINTER(Options), ctypes.c_int, ctypes.c_void_p,
                                          ctypes.POINTER(ctypes.c_void_p)]),
@@ -354,7 +356,7 @@ def batch_solve(problems, xs, check=True):
 
 
 KERNELS = {"stencil": 0, "ghost": 1, "correct": 2, "smooth_fine": 3, "multidot": 4, "update": 5, "vcycle": 6,
-           "operator": 7, "fits": 8}
+           "operator": 7, "fits": 8, "mg_down0": 9, "mg_up0": 10, "mg_tail": 11}
 
 
 def fit_stats(problem):
@@ -364,10 +366,18 @@ def fit_stats(problem):
     return nf.value, rs.value, m.value
 
 
-def kernel_time(problem, which, reps=50) -> float:
-    """Average device microseconds per launch of one internal kernel (see iim_kernel_time)."""
+def kernel_time(problem, which, reps=50, flush=None) -> float:
+    """Average device microseconds per launch of one internal kernel (see iim_kernel_time);
+    with ``flush`` (a device tensor larger than L2) each launch follows an overwrite of it."""
     us = ctypes.c_double()
-    _check(load().iim_kernel_time(problem.h, KERNELS.get(which, which), int(reps), ctypes.byref(us)), "kernel_time")
+    if flush is None:
+        _check(load().iim_kernel_time(problem.h, KERNELS.get(which, which), int(reps), ctypes.byref(us)),
+               "kernel_time")
+    else:
+        _check(load().iim_kernel_time_flushed(problem.h, KERNELS.get(which, which), int(reps),
+                                              ctypes.c_void_p(flush.data_ptr()),
+                                              ctypes.c_size_t(flush.numel() * flush.element_size()),
+                                              ctypes.byref(us)), "kernel_time")
     return us.value
 
 

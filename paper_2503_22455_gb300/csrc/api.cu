@@ -152,7 +152,8 @@ static iim_status validate(const iim_problem_desc* d, const iim_options* o) {
   }
   if (d->n < 16 || d->n > (d->dim == 2 ? 32768 : 1024)) return IIM_ERR_INVALID_ARG;
   bool k2 = d->geom_kind == IIM_GEOM_CIRCLE || d->geom_kind == IIM_GEOM_ELLIPSE || d->geom_kind == IIM_GEOM_STAR;
-  bool k3 = d->geom_kind == IIM_GEOM_SPHERE || d->geom_kind == IIM_GEOM_ELLIPSOID;
+  bool k3 = d->geom_kind == IIM_GEOM_SPHERE || d->geom_kind == IIM_GEOM_ELLIPSOID ||
+            d->geom_kind == IIM_GEOM_PERTURBED_SPHERE;
   if ((d->dim == 2 && !k2) || (d->dim == 3 && !k3)) return IIM_ERR_INVALID_ARG;
   if (d->bc < 0 || d->bc > 2 || d->box_bc < 0 || d->box_bc > 1) return IIM_ERR_INVALID_ARG;
   if (d->bc == IIM_BC_INTERFACE && d->box_bc != IIM_BOX_DIRICHLET) {
@@ -777,7 +778,7 @@ iim_status iim_batch_solve(iim_problem** probs, double** xs, int count, iim_solv
   return worst;
 }
 
-iim_status iim_kernel_time(iim_problem* H, int which, int reps, double* us) {
+iim_status iim_kernel_time_flushed(iim_problem* H, int which, int reps, void* flush, size_t flush_bytes, double* us) {
   if (!H || !us || reps < 1) return IIM_ERR_INVALID_ARG;
   Problem& P = H->P;
   cudaStream_t s = P.stream;
@@ -793,11 +794,34 @@ iim_status iim_kernel_time(iim_problem* H, int which, int reps, double* us) {
       case 6: mg_precondition(P, P.V, nullptr, P.tmp, s); break;
       case 7: ho_apply(P, P.x, P.tmp, false, s); break;
       case 8: setup_fits(P); break;
+      case 9: mg_one_kernel(P, 0, P.V, P.tmp, s); break;
+      case 10: mg_one_kernel(P, 1, P.V, P.tmp, s); break;
+      case 11: mg_one_kernel(P, 2, P.V, P.tmp, s); break;
       default: break;
     }
   };
-  if (which < 0 || which > 8) return IIM_ERR_INVALID_ARG;
+  if (which < 0 || which > 11) return IIM_ERR_INVALID_ARG;
+  if (which >= 9 && which <= 10 && !mg_has_fused_first(P)) {
+    set_error("kernel_time: the problem has no fused first-level multigrid kernels");
+    return IIM_ERR_INVALID_ARG;
+  }
   for (int r = 0; r < 3; ++r) launch();
+  if (flush && flush_bytes > 0) {
+    // each launch alone after overwriting a buffer larger than L2: its inputs come from HBM
+    double tot = 0;
+    for (int r = 0; r < reps; ++r) {
+      cudaMemsetAsync(flush, r & 0xff, flush_bytes, s);
+      cudaEventRecord(P.ev0, s);
+      launch();
+      cudaEventRecord(P.ev1, s);
+      cudaEventSynchronize(P.ev1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, P.ev0, P.ev1);
+      tot += ms;
+    }
+    *us = 1e3 * tot / reps;
+    return cuda_check("kernel time");
+  }
   cudaEventRecord(P.ev0, s);
   for (int r = 0; r < reps; ++r) launch();
   cudaEventRecord(P.ev1, s);
@@ -806,6 +830,10 @@ iim_status iim_kernel_time(iim_problem* H, int which, int reps, double* us) {
   cudaEventElapsedTime(&ms, P.ev0, P.ev1);
   *us = 1e3 * ms / reps;
   return cuda_check("kernel time");
+}
+
+iim_status iim_kernel_time(iim_problem* H, int which, int reps, double* us) {
+  return iim_kernel_time_flushed(H, which, reps, nullptr, 0, us);
 }
 
 }  // extern "C"

@@ -33,6 +33,11 @@ struct Geom {
   double cs, sn;                       // ellipse: cos and sin of the rotation angle p[4]
 };
 
+// Perturbed sphere: g = r - rho0 - rho1 c Q(d) / r^3 (-rho0 at the centre), d = x - centre, r = |d|,
+// Q = (dx^2 - dy^2) dz, so that Q / r^3 is the degree-3 harmonic (e_x^2 - e_y^2) e_z of the
+// direction e = d / r and c = 3 sqrt(3) / 2 scales its maximum on the sphere to 1.
+constexpr double kPerturbScale = 2.598076211353316;
+
 // g(x) < 0 inside the body; the paper's Omega+ = {phi >= 0}, phi = sign * g
 __host__ __device__ inline double geom_g(const Geom& G, const double* x) {
   const double* p = G.p;
@@ -56,6 +61,12 @@ __host__ __device__ inline double geom_g(const Geom& G, const double* x) {
       double dx = x[0] - p[0], dy = x[1] - p[1];
       double rho = hypot(dx, dy), th = atan2(dy, dx);
       return rho - (p[2] + p[3] * sin(p[4] * th + p[5]));
+    }
+    case IIM_GEOM_PERTURBED_SPHERE: {
+      double a = x[0] - p[0], b = x[1] - p[1], c = x[2] - p[2];
+      double r = sqrt(a * a + b * b + c * c);
+      if (r == 0.0) return -p[3];          // the centre: direction undefined, harmonic term 0
+      return r - p[3] - p[4] * kPerturbScale * ((a * a - b * b) * c) / (r * r * r);
     }
   }
   return 0.0;
@@ -95,7 +106,61 @@ __host__ __device__ inline void geom_grad_g(const Geom& G, const double* x, doub
       gr[1] = dy / rho - rp / rho * (dx / rho);
       return;
     }
+    case IIM_GEOM_PERTURBED_SPHERE: {
+      // grad g = d / r - rho1 c (grad Q r^-3 - 3 Q d r^-5)
+      double d[3] = {x[0] - p[0], x[1] - p[1], x[2] - p[2]};
+      double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2], r = sqrt(r2);
+      double Q = (d[0] * d[0] - d[1] * d[1]) * d[2];
+      double gQ[3] = {2 * d[0] * d[2], -2 * d[1] * d[2], d[0] * d[0] - d[1] * d[1]};
+      double ir3 = 1.0 / (r2 * r), ir5 = ir3 / r2, k = p[4] * kPerturbScale;
+      for (int i = 0; i < 3; ++i) gr[i] = d[i] / r - k * (gQ[i] * ir3 - 3 * Q * d[i] * ir5);
+      return;
+    }
   }
+}
+
+// Hessian of g (row major 3 x 3) for the perturbed sphere:
+// (I - e e^T) / r - rho1 c [Hess Q r^-3 - 3 r^-5 (grad Q d^T + d grad Q^T) + Q (-3 r^-5 I + 15 r^-7 d d^T)]
+__host__ __device__ inline void geom_hess_perturbed(const Geom& G, const double* x, double* H) {
+  const double* p = G.p;
+  double d[3] = {x[0] - p[0], x[1] - p[1], x[2] - p[2]};
+  double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2], r = sqrt(r2);
+  double Q = (d[0] * d[0] - d[1] * d[1]) * d[2];
+  double gQ[3] = {2 * d[0] * d[2], -2 * d[1] * d[2], d[0] * d[0] - d[1] * d[1]};
+  double HQ[9] = {2 * d[2], 0, 2 * d[0], 0, -2 * d[2], -2 * d[1], 2 * d[0], -2 * d[1], 0};
+  double ir3 = 1.0 / (r2 * r), ir5 = ir3 / r2, ir7 = ir5 / r2, k = p[4] * kPerturbScale;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const double del = i == j ? 1.0 : 0.0;
+      const double hr = (del - d[i] * d[j] / r2) / r;
+      const double hp = HQ[3 * i + j] * ir3 - 3 * (gQ[i] * d[j] + d[i] * gQ[j]) * ir5 +
+                        Q * (-3 * del * ir5 + 15 * d[i] * d[j] * ir7);
+      H[3 * i + j] = hr - k * hp;
+    }
+}
+
+// largest |eigenvalue| of the shape operator P H P / |grad g| on the tangent plane of a
+// 3D level surface (gr: grad g, H: Hessian of g, row major)
+__host__ __device__ inline double shape_max_curvature3(const double* gr, const double* H) {
+  double gn = sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+  double n[3] = {gr[0] / gn, gr[1] / gn, gr[2] / gn};
+  double a[3];
+  if (fabs(n[0]) < 0.9) { a[0] = 1; a[1] = 0; a[2] = 0; } else { a[0] = 0; a[1] = 1; a[2] = 0; }
+  double dt = a[0] * n[0] + a[1] * n[1] + a[2] * n[2];
+  double t1[3] = {a[0] - dt * n[0], a[1] - dt * n[1], a[2] - dt * n[2]};
+  double l = sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+  t1[0] /= l; t1[1] /= l; t1[2] /= l;
+  double t2[3] = {n[1] * t1[2] - n[2] * t1[1], n[2] * t1[0] - n[0] * t1[2], n[0] * t1[1] - n[1] * t1[0]};
+  double s11 = 0, s12 = 0, s22 = 0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      s11 += t1[i] * H[3 * i + j] * t1[j];
+      s12 += t1[i] * H[3 * i + j] * t2[j];
+      s22 += t2[i] * H[3 * i + j] * t2[j];
+    }
+  s11 /= gn; s12 /= gn; s22 /= gn;
+  double m = 0.5 * (s11 + s22), dd = sqrt(0.25 * (s11 - s22) * (s11 - s22) + s12 * s12);
+  return fmax(fabs(m + dd), fabs(m - dd));
 }
 
 // largest |principal curvature| of the level surface through x
@@ -146,6 +211,12 @@ __host__ __device__ inline double geom_curvature(const Geom& G, const double* x)
       s11 /= gn; s12 /= gn; s22 /= gn;
       double m = 0.5 * (s11 + s22), dd = sqrt(0.25 * (s11 - s22) * (s11 - s22) + s12 * s12);
       return fmax(fabs(m + dd), fabs(m - dd));
+    }
+    case IIM_GEOM_PERTURBED_SPHERE: {
+      double gr[3], H[9];
+      geom_grad_g(G, x, gr);
+      geom_hess_perturbed(G, x, H);
+      return shape_max_curvature3(gr, H);
     }
   }
   return 0.0;

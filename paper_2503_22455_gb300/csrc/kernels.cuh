@@ -197,6 +197,8 @@ void eng_operator_params(Problem& P, StencilCoef* C, GhostParams* GP, CorrectPar
 
 // multigrid.cu
 void mg_precondition(Problem& P, const double* v, const double* vscale, double* z, cudaStream_t s);
+bool mg_one_kernel(Problem& P, int which, const double* v, double* z, cudaStream_t s);
+bool mg_has_fused_first(const Problem& P);
 void mg_coarse_factor(Problem& P, cudaStream_t s);
 void mg_smooth_fine(Problem& P, int colour, cudaStream_t s);
 

@@ -82,11 +82,19 @@ __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx
   __shared__ T us[S];
   __shared__ T fs[S];
   __shared__ int as[S];
+  // The irregular rows of the tile's cells, staged once: a cell with aux a >= 0 gets a slot
+  // and as[e] = -3 - slot; past the capacity it keeps a and reads the level's table.
+  constexpr int kIrrCap = sizeof(T) == 8 ? 96 : 256;
+  __shared__ T ts[kIrrCap * 5];
+  __shared__ int s_nirr;
   const LevelK<T>& L = P.L;
   const int n = L.n;
   const int x0 = bx * TX - KH, y0 = by * TY - KH;
   const bool finest_in = DOWN_FIRST && P.v != nullptr;
   const T vs = finest_in ? (T)(P.vscale ? *P.vscale : 1.0) : (T)1;
+  const bool one_beta = P.inv_bp == P.inv_bm;       // no phase lookup for the scaling
+  if (threadIdx.x == 0) s_nirr = 0;
+  __syncthreads();
   {
     // all loads of a thread are issued before any is used (no aux -> f/u dependence)
     constexpr int NL = (S + 255) / 256;
@@ -103,7 +111,7 @@ __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx
       if (e < S && gx >= 0 && gx < n && gy >= 0 && gy < n) {
         const int64_t g = (int64_t)gy * n + gx;
         ra[q] = __ldg(L.aux + g);
-        if (finest_in) rf[q] = (T)__ldg(P.v + g) * (vs * (__ldg(P.phase + g) ? P.inv_bp : P.inv_bm));
+        if (finest_in) rf[q] = (T)__ldg(P.v + g) * (vs * (one_beta || __ldg(P.phase + g) ? P.inv_bp : P.inv_bm));
         else rf[q] = L.f[g];
         if (!DOWN_FIRST) ru[q] = P.u_in[g];
       }
@@ -115,10 +123,21 @@ __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx
       const bool unk = ra[q] != -2;
       us[e] = unk ? ru[q] : (T)0;
       fs[e] = unk ? rf[q] : (T)0;
-      as[e] = ra[q];
+      int a = ra[q];
+      if (a >= 0) {
+        const int slot = atomicAdd(&s_nirr, 1);
+        if (slot < kIrrCap) {
+#pragma unroll
+          for (int k = 0; k < 5; ++k) ts[slot * 5 + k] = tab2(L, a, k);
+          a = -3 - slot;
+        }
+      }
+      as[e] = a;
     }
   }
   __syncthreads();
+  // coefficient k of the irregular row of a cell (staged or from the level's table)
+  auto cf = [&](int a, int k) -> T { return a <= -3 ? ts[(-3 - a) * 5 + k] : tab2(L, a, k); };
   if (finest_in) {
     // the finest level's right-hand side, stored before the residual replaces it in fs
     for (int e = threadIdx.x; e < TX * TY; e += blockDim.x) {
@@ -182,9 +201,8 @@ __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx
       } else {
         T s = 0;
         if (!from_zero)
-          s = tab2(L, a, 1) * us[e - 1] + tab2(L, a, 2) * us[e + 1] + tab2(L, a, 3) * us[e - SX] +
-              tab2(L, a, 4) * us[e + SX];
-        const T dg = tab2(L, a, 0);
+          s = cf(a, 1) * us[e - 1] + cf(a, 2) * us[e + 1] + cf(a, 3) * us[e - SX] + cf(a, 4) * us[e + SX];
+        const T dg = cf(a, 0);
         nv = dg != (T)0 ? (fs[e] - s) / dg : (T)0;
       }
       us[e] = nv;
@@ -218,10 +236,9 @@ __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx
       if (a == -1) {
         const T s = (us[e - 1] + us[e + 1]) + (us[e - SX] + us[e + SX]);
         rr[q] = fs[e] - (L.dreg * us[e] + L.ih2 * s);
-      } else if (a >= 0) {
-        const T s = tab2(L, a, 1) * us[e - 1] + tab2(L, a, 2) * us[e + 1] + tab2(L, a, 3) * us[e - SX] +
-                    tab2(L, a, 4) * us[e + SX];
-        rr[q] = fs[e] - (tab2(L, a, 0) * us[e] + s);
+      } else if (a != -2) {
+        const T s = cf(a, 1) * us[e - 1] + cf(a, 2) * us[e + 1] + cf(a, 3) * us[e - SX] + cf(a, 4) * us[e + SX];
+        rr[q] = fs[e] - (cf(a, 0) * us[e] + s);
       }
     }
     __syncthreads();
@@ -256,7 +273,7 @@ __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx
 }
 
 template <typename T, int TX, int TY, int MODE>
-__global__ void __launch_bounds__(256) k_mg2d(Fine2DParams<T> P) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 7 : 1) k_mg2d(Fine2DParams<T> P) {
   mg2d_tile<T, TX, TY, MODE>(P, blockIdx.x, blockIdx.y);
 }
 

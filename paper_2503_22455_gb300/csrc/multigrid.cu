@@ -633,6 +633,33 @@ void mg_precondition(Problem& P, const double* v, const double* vscale, double* 
   else precondition_t<float>(P, v, vscale, z, s);
 }
 
+// The first level runs the fused down / up kernels (2D, V(2,2), above the tail)
+bool mg_has_fused_first(const Problem& P) {
+  return P.g.dim == 2 && tail_start(P) > 0 && P.opt.nu1 == 2 && P.opt.nu2 == 2;
+}
+
+// One kernel of the V-cycle alone (profiling): which 0 = the first level's down kernel,
+// 1 = its up kernel (both need mg_has_fused_first), 2 = the coarse tail.
+template <typename T>
+static bool mg_one_kernel_t(Problem& P, int which, const double* v, double* z, cudaStream_t s) {
+  const size_t lt = tail_start(P);
+  if (which == 2) {
+    launch_tail<T>(P, lt, lt == 0 ? v : nullptr, nullptr, lt == 0 ? z : nullptr, s);
+    return true;
+  }
+  if (!mg_has_fused_first(P)) return false;
+  T* A = (T*)P.lv[0].u;
+  T* B = (T*)P.lv[0].u2;
+  if (which == 0) fine2d<T>(P, 0, 5, v, nullptr, nullptr, nullptr, A, nullptr, s);
+  else fine2d<T>(P, 0, 6, nullptr, nullptr, z, A, B, (const T*)P.lv[1].u, s);
+  return true;
+}
+
+bool mg_one_kernel(Problem& P, int which, const double* v, double* z, cudaStream_t s) {
+  if (P.opt.mg_precision == IIM_MG_FP64) return mg_one_kernel_t<double>(P, which, v, z, s);
+  return mg_one_kernel_t<float>(P, which, v, z, s);
+}
+
 // coarse matrix, LU and inverse; coarse_lu{64,32} hold [A (nu*nu) | inverse (nu*nu)]
 void mg_coarse_factor(Problem& P, cudaStream_t s) {
   Level& C = P.lv.back();

@@ -1,0 +1,62 @@
+"""The radially perturbed sphere of the paper's 3D verification (Sec. 4.2) on the GPU.
+
+* phase bit-exact, control points and normals to 1e-12, the operator to 1e-12 relative
+  against the oracle (Dirichlet and pure Neumann, n = 40);
+* the manufactured solution of Sec. 4.2 solved at n = 48, 96, 192: the maximum error over
+  the unknowns decays with order >= 3.5 (Dirichlet) and >= 3.5 after removing the mean
+  (pure Neumann, augmented system), with FP32 multigrid and tol 1e-12.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.problem import OracleProblem
+from tests.gpu_helpers import dev, gpu_problem, need_gpu, rel_err, set_gpu_data
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    return need_gpu()
+
+
+@pytest.mark.parametrize("bc", [W.DIRICHLET, W.NEUMANN])
+def test_perturbed_sphere_geometry_and_operator_match_oracle(env, bc):
+    torch, iim = env
+    spec = W.perturbed_sphere(40, bc)
+    P = gpu_problem(iim, spec, mg_precision=iim.MG_FP64)
+    O = OracleProblem(spec)
+    assert np.array_equal(P.phase().cpu().numpy().astype(bool), O.plus_flat)
+    assert P.K == O.op.cross.count
+    xc, nc = P.control_points()
+    assert np.max(np.abs(xc.cpu().numpy() - O.op.cross.x)) < 1e-12
+    assert np.max(np.abs(nc.cpu().numpy() - O.op.cross.normal)) < 1e-12
+    u = np.random.default_rng(3).standard_normal(P.N)
+    assert rel_err(P.apply(dev(u)).cpu().numpy(), O.op.apply(u)) < 1e-12
+    v = np.random.default_rng(4).standard_normal(P.N) * O.unk_flat
+    assert rel_err(P.precondition(dev(v)).cpu().numpy(), O.precondition(v)) < 1e-12
+
+
+@pytest.mark.parametrize("bc", [W.DIRICHLET, W.NEUMANN])
+def test_perturbed_sphere_convergence(env, bc):
+    torch, iim = env
+    ns, errs = (48, 96, 192), []
+    for n in ns:
+        spec = W.perturbed_sphere(n, bc)
+        P = gpu_problem(iim, spec, tol=1e-12, max_iter=600)
+        set_gpu_data(P, spec)
+        x, info = P.solve()
+        assert info.converged, (n, info.as_dict())
+        ph = P.phase().cpu().numpy().astype(bool)
+        ex = W.to_flat(spec.solution.u_plus(W.node_coords(n, 3)))
+        e = (x.cpu().numpy() - ex)[ph]
+        if bc == W.NEUMANN:
+            e = e - e.mean()
+        errs.append(float(np.max(np.abs(e))))
+        P.close()
+    orders = [math.log(errs[k] / errs[k + 1]) / math.log(ns[k + 1] / ns[k]) for k in range(len(ns) - 1)]
+    print(f"\n[perturbed sphere bc={bc}] max errors {errs}, orders {orders}")
+    assert min(orders) >= 3.5, (errs, orders)

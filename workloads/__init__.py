@@ -18,7 +18,10 @@ from dataclasses import dataclass, field
 import numpy as np
 
 # geometry kinds (same integer codes as the C header)
-CIRCLE, ELLIPSE, STAR, SPHERE, ELLIPSOID = 0, 1, 2, 3, 4
+CIRCLE, ELLIPSE, STAR, SPHERE, ELLIPSOID, PERTURBED_SPHERE = 0, 1, 2, 3, 4, 5
+# the perturbation of PERTURBED_SPHERE: the real spherical harmonic of degree 3, order 2,
+# (e_x^2 - e_y^2) e_z for the unit direction e, scaled to a maximum of 1 on the sphere
+PERTURB_SCALE = 1.5 * math.sqrt(3.0)
 # boundary condition kinds
 DIRICHLET, NEUMANN, INTERFACE = 0, 1, 2
 # outer box condition
@@ -35,6 +38,8 @@ class Geometry:
       STAR      (cx, cy, r0, amp, m, phase)      r(theta) = r0 + amp sin(m theta + phase)
       SPHERE    (cx, cy, cz, R)
       ELLIPSOID (cx, cy, cz, a0, a1, a2)         axis-aligned
+      PERTURBED_SPHERE (cx, cy, cz, rho0, rho1)  r(e) = rho0 + rho1 Y(e), Y the degree-3
+                                                 harmonic above (max |Y| = 1)
     """
     kind: int
     params: tuple
@@ -42,7 +47,7 @@ class Geometry:
 
     @property
     def dim(self) -> int:
-        return 3 if self.kind in (SPHERE, ELLIPSOID) else 2
+        return 3 if self.kind in (SPHERE, ELLIPSOID, PERTURBED_SPHERE) else 2
 
 
 @dataclass
@@ -163,6 +168,25 @@ def sin_sin_cos_3d(a, b) -> Manufactured:
 
     lap = lambda X, xp=np: -(a[0] ** 2 + a[1] ** 2 + a[2] ** 2) * u(X, xp)
     return Manufactured(u, g, lap)
+
+
+def sin_sum_3d(k=2.0 * math.pi) -> Manufactured:
+    """u = sin(k x) + sin(k y) + sin(k z).  With k = 2 pi this is the paper's 3D verification
+    solution sin(4 pi x_i) summed, on the unit cube mapped to [-1,1]^3."""
+    u = lambda X, xp=np: xp.sin(k * X[..., 0]) + xp.sin(k * X[..., 1]) + xp.sin(k * X[..., 2])
+    g = lambda X, xp=np: xp.stack([k * xp.cos(k * X[..., 0]), k * xp.cos(k * X[..., 1]),
+                                   k * xp.cos(k * X[..., 2])], axis=-1)
+    lap = lambda X, xp=np: -(k * k) * u(X, xp)
+    return Manufactured(u, g, lap)
+
+
+def perturbed_sphere(n: int, bc: int = DIRICHLET) -> "ProblemSpec":
+    """The paper's 3D verification body (a sphere of radius 0.35 perturbed by 0.05 times a
+    spherical harmonic, in the unit cube), mapped to [-1,1]^3: rho0 = 0.7, rho1 = 0.1,
+    centred; interior problem (no outer box), Dirichlet or Neumann, (4,5)."""
+    return ProblemSpec(n=n, geometry=Geometry(PERTURBED_SPHERE, (0.0, 0.0, 0.0, 0.7, 0.1), plus_inside=True),
+                       bc=bc, order=4, box_bc=BOX_NONE, solution=sin_sum_3d(),
+                       name=f"perturbed_sphere_{'dir' if bc == DIRICHLET else 'neu'}_{n}")
 
 
 class Polynomial:
