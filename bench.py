@@ -785,6 +785,10 @@ def hbm_kernels(P, iim, torch, pk):
         if peak:
             r["frac_hbm"] = r["gbs_hbm"] / peak
         res.append(r)
+    try:
+        res.append({"kernel": "k_vcycle_tail (one CTA, latency)", "us_l2": iim.kernel_time(P, "mg_tail", reps=50)})
+    except iim.IIMError:
+        pass
     del flush
     return res
 

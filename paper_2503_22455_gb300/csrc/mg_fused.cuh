@@ -53,6 +53,28 @@ static LevelK<T> levk(const Level& L) {
 
 constexpr int kH = 3;
 
+// The point operations of the fine-level kernels, with every multiply-add fused explicitly
+// and every other product kept unfused, so that the shared-memory tile kernels (here and
+// in the batched engine) and the register-tiled ones give bit-identical results.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+// Gauss-Seidel value of a regular cell: (f - ih2 ((l + r) + (d + u))) / (-2d/h^2)
+template <typename T>
+__device__ __forceinline__ T gs_regular(T f, T s, T ih2, T inv_dreg) { return mul_rn(fma(-ih2, s, f), inv_dreg); }
+// the off-diagonal sum of an irregular cell, c1 l + c2 r + c3 d + c4 u
+template <typename T>
+__device__ __forceinline__ T irr_offdiag(T c1, T c2, T c3, T c4, T l, T r, T d, T u) {
+  return fma(c4, u, fma(c3, d, fma(c2, r, mul_rn(c1, l))));
+}
+// residual of a regular cell, f - (dreg u + ih2 s)
+template <typename T>
+__device__ __forceinline__ T res_regular(T f, T u, T s, T dreg, T ih2) { return f - fma(dreg, u, mul_rn(ih2, s)); }
+// bilinear coarse-to-fine weights 9/16, 3/16, 3/16, 1/16
+template <typename T>
+__device__ __forceinline__ T prolong_bilinear(T e0, T e1, T e2, T e3) {
+  return fma((T)0.0625, e3, fma((T)0.1875, e2, fma((T)0.1875, e1, mul_rn((T)0.5625, e0))));
+}
+
 template <typename T>
 struct Fine2DParams {
   LevelK<T> L;
@@ -111,7 +133,7 @@ __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx
       if (e < S && gx >= 0 && gx < n && gy >= 0 && gy < n) {
         const int64_t g = (int64_t)gy * n + gx;
         ra[q] = __ldg(L.aux + g);
-        if (finest_in) rf[q] = (T)__ldg(P.v + g) * (vs * (one_beta || __ldg(P.phase + g) ? P.inv_bp : P.inv_bm));
+        if (finest_in) rf[q] = mul_rn((T)__ldg(P.v + g), mul_rn(vs, one_beta || __ldg(P.phase + g) ? P.inv_bp : P.inv_bm));
         else rf[q] = L.f[g];
         if (!DOWN_FIRST) ru[q] = P.u_in[g];
       }
@@ -175,7 +197,7 @@ __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx
         acc = cnt > 0 ? ((ok[0] ? ev[0] : 0) + (ok[1] ? ev[1] : 0) + (ok[2] ? ev[2] : 0) + (ok[3] ? ev[3] : 0)) / (T)cnt
                       : (T)0;
       } else {
-        acc = (T)0.5625 * ev[0] + (T)0.1875 * ev[1] + (T)0.1875 * ev[2] + (T)0.0625 * ev[3];
+        acc = prolong_bilinear(ev[0], ev[1], ev[2], ev[3]);
       }
       us[e] += acc;
     }
@@ -197,11 +219,11 @@ __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx
       T nv;
       if (a == -1) {
         const T s = from_zero ? (T)0 : (us[e - 1] + us[e + 1]) + (us[e - SX] + us[e + SX]);
-        nv = (fs[e] - L.ih2 * s) * L.inv_dreg;
+        nv = gs_regular(fs[e], s, L.ih2, L.inv_dreg);
       } else {
         T s = 0;
         if (!from_zero)
-          s = cf(a, 1) * us[e - 1] + cf(a, 2) * us[e + 1] + cf(a, 3) * us[e - SX] + cf(a, 4) * us[e + SX];
+          s = irr_offdiag(cf(a, 1), cf(a, 2), cf(a, 3), cf(a, 4), us[e - 1], us[e + 1], us[e - SX], us[e + SX]);
         const T dg = cf(a, 0);
         nv = dg != (T)0 ? (fs[e] - s) / dg : (T)0;
       }
@@ -235,10 +257,10 @@ __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx
       const int a = as[e];
       if (a == -1) {
         const T s = (us[e - 1] + us[e + 1]) + (us[e - SX] + us[e + SX]);
-        rr[q] = fs[e] - (L.dreg * us[e] + L.ih2 * s);
+        rr[q] = res_regular(fs[e], us[e], s, L.dreg, L.ih2);
       } else if (a != -2) {
-        const T s = cf(a, 1) * us[e - 1] + cf(a, 2) * us[e + 1] + cf(a, 3) * us[e - SX] + cf(a, 4) * us[e + SX];
-        rr[q] = fs[e] - (cf(a, 0) * us[e] + s);
+        const T s = irr_offdiag(cf(a, 1), cf(a, 2), cf(a, 3), cf(a, 4), us[e - 1], us[e + 1], us[e - SX], us[e + SX]);
+        rr[q] = fs[e] - fma(cf(a, 0), us[e], s);
       }
     }
     __syncthreads();
