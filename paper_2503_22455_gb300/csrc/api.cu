@@ -66,6 +66,11 @@ static void free_all(Problem& P) {
   P.setup_graph = nullptr;
   if (P.ev0) cudaEventDestroy(P.ev0);
   if (P.ev1) cudaEventDestroy(P.ev1);
+  if (P.ev_fork) cudaEventDestroy(P.ev_fork);
+  if (P.ev_join) cudaEventDestroy(P.ev_join);
+  if (P.side) cudaStreamDestroy(P.side);
+  P.ev_fork = P.ev_join = nullptr;
+  P.side = nullptr;
   P.graph_exec = nullptr;
   P.graph = nullptr;
   P.ev0 = nullptr;
@@ -263,6 +268,12 @@ iim_status iim_problem_create(const iim_problem_desc* desc, const iim_options* o
   const int64_t N = P.g.N;
   cudaEventCreate(&P.ev0);
   cudaEventCreate(&P.ev1);
+  if (cudaStreamCreateWithFlags(&P.side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P.ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    P.side = nullptr;                  // no side stream: the operator runs its kernels in sequence
+  }
   // monomials of total degree <= q, graded order
   std::vector<int> mono;
   for (int deg = 0; deg <= P.q; ++deg) {

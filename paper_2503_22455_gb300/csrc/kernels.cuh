@@ -171,6 +171,10 @@ struct Problem {
   cudaGraphExec_t setup_exec = nullptr;
   int64_t kern_setup = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // a second stream for work that runs beside the main one (the ghost values beside the
+  // stencil), joined back by events, also inside captured graphs
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   size_t bytes = 0;               // device bytes held
   std::vector<void*> allocs;
 };

@@ -288,8 +288,19 @@ void ho_correct(Problem& P, const double* u, double* w, bool with_data, cudaStre
 }
 
 void ho_apply(Problem& P, const double* u, double* w, bool with_data, cudaStream_t s) {
-  ho_stencil(P, u, w, s);
-  ho_ghost(P, u, with_data, s);
+  if (P.side && P.ev_fork && P.ev_join) {
+    // the ghost values read only u: they are computed on the side stream beside the
+    // stencil, and the corrections wait for both
+    cudaEventRecord(P.ev_fork, s);
+    cudaStreamWaitEvent(P.side, P.ev_fork, 0);
+    ho_ghost(P, u, with_data, P.side);
+    cudaEventRecord(P.ev_join, P.side);
+    ho_stencil(P, u, w, s);
+    cudaStreamWaitEvent(s, P.ev_join, 0);
+  } else {
+    ho_stencil(P, u, w, s);
+    ho_ghost(P, u, with_data, s);
+  }
   ho_correct(P, u, w, with_data, s);
 }
 
