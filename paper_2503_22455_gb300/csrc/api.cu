@@ -439,11 +439,26 @@ iim_status iim_problem_create(const iim_problem_desc* desc, const iim_options* o
 
 static iim_status setup_enqueue(Problem& P) {
   setup_geometry(P, false);
-  iim_status st = setup_fits(P);
-  if (st != IIM_OK) return st;
+  if (!(P.side && P.ev_fork && P.ev_join)) {
+    iim_status st = setup_fits(P);
+    if (st != IIM_OK) return st;
+    setup_levels(P, false);
+    mg_coarse_factor(P, P.stream);
+    return IIM_OK;
+  }
+  // the Shortley-Weller levels and the coarse factor need the geometry but not the fits:
+  // they run on the side stream beside the fits and are joined before the set-up ends
+  cudaEventRecord(P.ev_fork, P.stream);
+  cudaStreamWaitEvent(P.side, P.ev_fork, 0);
+  const cudaStream_t main = P.stream;
+  P.stream = P.side;
   setup_levels(P, false);
   mg_coarse_factor(P, P.stream);
-  return IIM_OK;
+  P.stream = main;
+  cudaEventRecord(P.ev_join, P.side);
+  const iim_status st = setup_fits(P);
+  cudaStreamWaitEvent(P.stream, P.ev_join, 0);     // joined on every path
+  return st;
 }
 
 // The set-up is a fixed sequence of kernels with no host decision in it, so (with
