@@ -404,11 +404,10 @@ static LevelView<T> view(const Level& L) {
   return v;
 }
 
-// first level handled by the single-CTA tail: the first with at most kTailThreads
-// nodes, so that each thread of the tail owns at most one node per level
+// first level handled by the single-CTA tail: the first with at most kTailNodes nodes
 static size_t tail_start(const Problem& P) {
   size_t l = 0;
-  while (l + 1 < P.lv.size() && P.lv[l].g.N > kTailThreads) ++l;
+  while (l + 1 < P.lv.size() && P.lv[l].g.N > kTailNodes) ++l;
   return l;
 }
 size_t mg_tail_start(const Problem& P) { return tail_start(P); }
