@@ -13,7 +13,7 @@
 //   MODE 6  MODE 2 and MODE 3 in one kernel (nu2 = 2)
 //   MODE 7  MODE 5 from a given u (a W-cycle's second visit of a level): halo 5, since
 //           the first half sweep now reads its neighbours
-// Coarse tail: every level with at most 1024 nodes (a few per thread) and the dense
+// Coarse tail: every level with at most 1024 nodes (one per thread) and the dense
 // coarse solve run in a single CTA with the whole sub-hierarchy in shared memory.
 #pragma once
 
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 7 : 1) k_mg2d(Fine2DPara
 // ---------------------------------------------------------------------------- coarse tail (one CTA)
 constexpr int kTailMaxLevels = 8;
 constexpr int kTailNodes = 1024;      // levels with at most this many nodes go to the tail
-constexpr int kTailThreads = 256;     // threads of the tail's CTA (a few nodes each on its first level)
+constexpr int kTailThreads = 1024;    // threads of the tail's CTA: one node each on its first level
 
 template <typename T>
 struct TailParams {
