@@ -12,12 +12,15 @@ Layout
   fits.py      least-squares interpolants, ghost / Neumann / jump rows (Sec. 2.1-2.2)
   operator.py  the (n,k) IIM operator L_Omega and data term           (Sec. 2.3, Eq. 12)
   sw.py        Shortley-Weller operators and 1D formulas              (Sec. 3.1, Eqs. 18-21)
-  mg.py        geometric multigrid V-cycle                           (Sec. 3.3)
-  fgmres.py    right-preconditioned flexible GMRES(m)                (Sec. 4.1)
+  mg.py        geometric multigrid V- and W-cycles                   (Sec. 3.3)
+  fgmres.py    right-preconditioned flexible GMRES(m) (Sec. 4.1) and
+               left-preconditioned GMRES(m)                          (Sec. 3.2)
+  dense.py     dense assembly of the operator for brute-force checks
   problem.py   glue: build everything for one problem, solve it
 
 Parity-unpinned readings (no printed value pins them; only the invariants in
 tests/ do): the half-ellipse semi-axes of the least-squares region, the
-cell-centred restriction/prolongation weights, the outer-box closure, the
-coarsest-grid size rule.
+outer-box closure, the coarsest-grid size rule, the degree of the spherical
+harmonic of the perturbed sphere.  The cell-centred transfer weights are pinned
+by multilinear exactness (tests/test_oracle_transfers.py).
 """
