@@ -374,9 +374,17 @@ __global__ void k_init_scalars(SolverScalars* S, int m, int max_iter, double tol
   S->done = 0;
 }
 
-__global__ void k_set_handles(SolverScalars* S, cudaGraphConditionalHandle hw, cudaGraphConditionalHandle* hif, int m) {
-  S->h_while = hw;
-  for (int k = 0; k < m; ++k) S->h_if[k] = hif[k];
+// the solve graph's condition handles, passed by value (no staging buffer: building a
+// graph allocates and frees nothing, so it does not synchronise the device)
+struct GraphHandles {
+  cudaGraphConditionalHandle h_while;
+  cudaGraphConditionalHandle h_if[kMaxRestart];
+  int m;
+};
+
+__global__ void k_set_handles(SolverScalars* S, GraphHandles H) {
+  S->h_while = H.h_while;
+  for (int k = 0; k < H.m; ++k) S->h_if[k] = H.h_if[k];
 }
 
 // ---------------------------------------------------------------------------- host side
@@ -618,13 +626,13 @@ iim_status krylov_build_graph(Problem& P, double* x) {
     return IIM_ERR_CUDA;
   }
   // the handles live in the solver scalars so that kernels can set them
-  cudaGraphConditionalHandle* dh = nullptr;
-  cudaMalloc(&dh, sizeof(cudaGraphConditionalHandle) * m);
-  cudaMemcpy(dh, hif.data(), sizeof(cudaGraphConditionalHandle) * m, cudaMemcpyHostToDevice);
-  k_set_handles<<<1, 1, 0, s>>>(P.sc, hw, dh, m);
+  GraphHandles H = {};
+  H.h_while = hw;
+  H.m = m;
+  for (int j = 0; j < m; ++j) H.h_if[j] = hif[j];
+  k_set_handles<<<1, 1, 0, s>>>(P.sc, H);
   note_launch();
   cudaStreamSynchronize(s);
-  cudaFree(dh);
   e = cudaGraphInstantiate(&P.graph_exec, g, 0);
   cudaStreamDestroy(s);
   P.graph = g;
