@@ -2,7 +2,8 @@
 
 * on a two-level hierarchy the coarse solve is exact, so the W-cycle equals the V-cycle;
 * as a solver on the Shortley-Weller system, the W-cycle converges faster than the
-  V-cycle for Neumann and interface problems and its rate hardly changes with n;
+  V-cycle for Neumann and interface problems (2D and 3D) and its rate hardly changes
+  with n (2D);
 * left GMRES with the identity preconditioner is plain GMRES: after k iterations it
   equals right-preconditioned FGMRES with the identity (same minimisation problem);
   with the exact inverse as preconditioner it converges in one iteration; converged,
