@@ -63,3 +63,39 @@ def test_invalid_descriptor_is_rejected_without_touching_the_device(lib_path):
     d = iim.make_desc(2, 64, iim.GEOM["star"], (0, 0, 0.5, 0.1, 5, 0), False, iim.BC["interface"], 0, order=6)
     st = lib.iim_problem_create(ctypes.byref(d), ctypes.byref(iim.default_options()), None, ctypes.byref(h))
     assert st == 1 and "box" in lib.iim_last_error().decode()
+
+
+def _header_enums():
+    src = open(os.path.join(ROOT, "include", "iim.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    vals = {}
+    for body in re.findall(r"enum\s*\{(.*?)\}", src, flags=re.S):
+        for name, val in re.findall(r"(IIM_\w+)\s*=\s*(\d+)", body):
+            vals[name] = int(val)
+    return vals
+
+
+def test_binding_constants_match_the_header():
+    """The binding's geometry, condition, precision, cycle and Krylov codes are the header's."""
+    import paper_2503_22455_gb300 as iim
+    import workloads as W
+    e = _header_enums()
+    for key, name in (("circle", "CIRCLE"), ("ellipse", "ELLIPSE"), ("star", "STAR"), ("sphere", "SPHERE"),
+                      ("ellipsoid", "ELLIPSOID"), ("perturbed_sphere", "PERTURBED_SPHERE")):
+        assert iim.GEOM[key] == e["IIM_GEOM_" + name] == getattr(W, name), key
+    for key in ("dirichlet", "neumann", "interface"):
+        assert iim.BC[key] == e["IIM_BC_" + key.upper()] == getattr(W, key.upper())
+    assert (W.BOX_NONE, W.BOX_DIRICHLET) == (e["IIM_BOX_NONE"], e["IIM_BOX_DIRICHLET"])
+    assert (iim.MG_FP32, iim.MG_FP64, iim.MG_FP32_BF16R) == (e["IIM_MG_FP32"], e["IIM_MG_FP64"], e["IIM_MG_FP32_BF16R"])
+    assert (iim.CYCLE_V, iim.CYCLE_W) == (e["IIM_CYCLE_V"], e["IIM_CYCLE_W"])
+    assert (iim.KRYLOV_FGMRES, iim.KRYLOV_GMRES_LEFT) == (e["IIM_KRYLOV_FGMRES"], e["IIM_KRYLOV_GMRES_LEFT"])
+
+
+def test_options_struct_matches_the_header(lib_path):
+    """iim_default_options fills every field the binding's struct declares (no layout drift):
+    the defaults the header documents come back through ctypes."""
+    import paper_2503_22455_gb300 as iim
+    iim.load(lib_path)
+    o = iim.default_options()
+    assert (o.restart, o.max_iter, o.nu1, o.nu2, o.mg_precision, o.use_graph, o.reorth, o.cycle, o.krylov) == \
+        (10, 500, 2, 2, iim.MG_FP32, 1, 1, iim.CYCLE_V, iim.KRYLOV_FGMRES)
