@@ -99,3 +99,16 @@ def test_options_struct_matches_the_header(lib_path):
     o = iim.default_options()
     assert (o.restart, o.max_iter, o.nu1, o.nu2, o.mg_precision, o.use_graph, o.reorth, o.cycle, o.krylov) == \
         (10, 500, 2, 2, iim.MG_FP32, 1, 1, iim.CYCLE_V, iim.KRYLOV_FGMRES)
+
+
+@pytest.mark.parametrize("field,value", [("cycle", 0), ("cycle", 3), ("krylov", 2), ("krylov", -1),
+                                         ("restart", 17), ("mg_precision", 3)])
+def test_invalid_options_are_rejected_without_touching_the_device(lib_path, field, value):
+    import paper_2503_22455_gb300 as iim
+    lib = iim.load(lib_path)
+    d = iim.make_desc(2, 64, iim.GEOM["circle"], (0.0, 0.0, 0.5), True, iim.BC["dirichlet"], 0, order=4)
+    o = iim.default_options()
+    setattr(o, field, value)
+    h = ctypes.c_void_p()
+    st = lib.iim_problem_create(ctypes.byref(d), ctypes.byref(o), None, ctypes.byref(h))
+    assert st == 1 and not h.value, (field, value, st)
