@@ -180,21 +180,22 @@ iim_status iim_apply(iim_problem* p, const double* u_dev, double* w_dev, int inc
 
 /* The operator of iim_apply without touching the problem's own scratch.  The
  * paper has no counterpart: this is a deployment variant.  iim_apply writes the
- * ghost values of Eq. 4 into scratch that iim_problem_create allocated for that
- * problem; this call writes them into one fixed area compiled into the library
- * (2^18 doubles = 2 MiB, reserved on every GPU that loads the library until the
+ * ghost values into scratch that iim_problem_create allocated for that problem;
+ * this call writes them into one fixed area compiled into the library (2^18
+ * doubles = 2 MiB, reserved on every GPU that loads the library until the
  * process exits) and calls no cudaMalloc, cudaFree or allocating library
  * routine.  It is for callers that keep their problems' memory fixed once they
- * are set up and cannot allocate afterwards: code paths that run under a hard
- * device-memory budget with nothing left to grow into, or that run while a
- * stream is being captured, where allocation is not permitted.  The first call
- * on a device looks up the area's device address (with that device current);
- * make that first call before any stream capture begins.  Problems whose
- * ghost values exceed the area (2 x control points x w > 2^18 for interfaces,
- * control points x w otherwise) are rejected with IIM_ERR_CAPACITY.  Every call
- * shares the one area, which keeps the last call's contents: calls that overlap
- * on the device (other streams, threads or problems) race and must be ordered
- * by the caller.  Arguments and results are those of iim_apply.  Asynchronous. */
+ * are set up and cannot allocate afterwards, such as code that runs under a hard
+ * device-memory budget with nothing left to grow into.  The first call on a
+ * device looks up the area's device address (with that device current); make
+ * that first call before any stream capture begins.  Problems whose ghost
+ * values exceed the area (2 x control points x w > 2^18 for interfaces, control
+ * points x w otherwise) are rejected with IIM_ERR_CAPACITY before anything is
+ * launched.  Every call shares the one area, which keeps the last call's
+ * contents; each call writes every ghost value before reading it, so nothing
+ * needs clearing, but calls that overlap on the device (other streams, threads
+ * or problems) race and must be ordered by the caller.  Arguments and results
+ * are those of iim_apply.  Asynchronous. */
 iim_status iim_apply_noalloc(iim_problem* p, const double* u_dev, double* w_dev, int include_data);
 
 /* b of the last iim_set_data.  Asynchronous. */

@@ -14,7 +14,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libiim.so")
 
 IIM_OK = 0
-IIM_ERR_TIMEOUT = 8
+IIM_ERR_INVALID_ARG, IIM_ERR_CURVATURE, IIM_ERR_RANK, IIM_ERR_SINGULAR = 1, 2, 3, 4
+IIM_ERR_NOT_CONVERGED, IIM_ERR_BREAKDOWN, IIM_ERR_BUDGET, IIM_ERR_TIMEOUT = 5, 6, 7, 8
+IIM_ERR_CUDA, IIM_ERR_GEOMETRY, IIM_ERR_CAPACITY = 9, 10, 11
 STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "curvature", 3: "rank", 4: "singular", 5: "not converged",
                 6: "breakdown", 7: "budget", 8: "timeout", 9: "cuda", 10: "geometry", 11: "capacity"}
 GEOM = {"circle": 0, "ellipse": 1, "star": 2, "sphere": 3, "ellipsoid": 4, "perturbed_sphere": 5}

@@ -564,66 +564,104 @@ void krylov_enqueue_solve(Problem& P, double* x, bool graph_mode) {
   }
 }
 
-static cudaGraphNode_t add_conditional(cudaGraph_t g, cudaStream_t s, cudaGraphConditionalHandle h,
-                                       cudaGraphConditionalNodeType type, cudaGraph_t* body) {
+// Add a conditional node after the capture's current dependencies and make it the
+// only dependency of what follows; *body receives the node's body graph.
+static cudaError_t add_conditional(cudaGraph_t g, cudaStream_t s, cudaGraphConditionalHandle h,
+                                   cudaGraphConditionalNodeType type, cudaGraph_t* body) {
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
   cudaStreamCaptureStatus st;
-  cudaStreamGetCaptureInfo(s, &st, nullptr, nullptr, &deps, nullptr, &ndeps);
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, nullptr, &deps, nullptr, &ndeps);
+  if (e != cudaSuccess) return e;
   cudaGraphNodeParams cp = {};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = h;
   cp.conditional.type = type;
   cp.conditional.size = 1;
   cudaGraphNode_t node;
-  cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp);
-  cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+  e = cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e != cudaSuccess) return e;
   *body = cp.conditional.phGraph_out[0];
-  return node;
+  return cudaSuccess;
 }
 
 // Build the solve graph once per problem.  The solve reads and writes P.x.
+// Every graph and capture call is checked; on a failure the capture is ended, the
+// graph and the stream are destroyed and the error names the call.
 iim_status krylov_build_graph(Problem& P, double* x) {
   (void)x;
   cudaStream_t s;
-  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return IIM_ERR_CUDA;
-  cudaGraph_t g;
-  cudaGraphCreate(&g, 0);
-  cudaGraphConditionalHandle hw;
-  cudaGraphConditionalHandleCreate(&hw, g, 0, 0);
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error(std::string("solve graph: cudaStreamCreateWithFlags: ") + cudaGetErrorString(e));
+    return IIM_ERR_CUDA;
+  }
+  cudaGraph_t g = nullptr;
+  const char* failed = nullptr;
+  auto ok = [&](cudaError_t r, const char* what) {
+    if (r != cudaSuccess && !failed) {
+      failed = what;
+      e = r;
+    }
+    return failed == nullptr;
+  };
+  auto fail = [&]() -> iim_status {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+      cudaGraph_t captured = nullptr;     // the graph captured into: g or one of its bodies
+      cudaStreamEndCapture(s, &captured);
+    }
+    cudaGetLastError();
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(s);
+    set_error(std::string("solve graph: ") + failed + ": " + cudaGetErrorString(e));
+    return IIM_ERR_CUDA;
+  };
+  // capture into an existing graph: end the capture and check that the stream's work
+  // recorded without error
+  auto end_capture = [&](const char* what) {
+    cudaGraph_t captured = nullptr;
+    if (!ok(cudaStreamEndCapture(s, &captured), what)) return false;
+    return ok(cudaGetLastError(), what);
+  };
   const int m = P.opt.restart;
-  cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  cudaGraphConditionalHandle hw;
+  if (!ok(cudaGraphCreate(&g, 0), "cudaGraphCreate")) return fail();
+  if (!ok(cudaGraphConditionalHandleCreate(&hw, g, 0, 0), "cudaGraphConditionalHandleCreate")) return fail();
+  if (!ok(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed),
+          "cudaStreamBeginCaptureToGraph (start)"))
+    return fail();
   int64_t c0 = launches_now();
   enqueue_start(P, s, 1);
   P.kern_start = launches_now() - c0;
-  cudaGraph_t body;
-  add_conditional(g, s, hw, cudaGraphCondTypeWhile, &body);
-  cudaStreamEndCapture(s, &g);
+  cudaGraph_t body = nullptr;
+  if (!ok(add_conditional(g, s, hw, cudaGraphCondTypeWhile, &body), "conditional WHILE node")) return fail();
+  if (!end_capture("cudaStreamEndCapture (start)")) return fail();
   std::vector<cudaGraphConditionalHandle> hif(m);
-  for (int j = 0; j < m; ++j) cudaGraphConditionalHandleCreate(&hif[j], body, 0, 0);
-  cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  for (int j = 0; j < m; ++j)
+    if (!ok(cudaGraphConditionalHandleCreate(&hif[j], body, 0, 0), "cudaGraphConditionalHandleCreate (IF)"))
+      return fail();
+  if (!ok(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed),
+          "cudaStreamBeginCaptureToGraph (restart)"))
+    return fail();
   std::vector<cudaGraph_t> ibody(m);
-  for (int j = 0; j < m; ++j) add_conditional(body, s, hif[j], cudaGraphCondTypeIf, &ibody[j]);
+  for (int j = 0; j < m; ++j)
+    if (!ok(add_conditional(body, s, hif[j], cudaGraphCondTypeIf, &ibody[j]), "conditional IF node")) return fail();
   c0 = launches_now();
   enqueue_restart(P, s);
   P.kern_restart = launches_now() - c0;
-  cudaStreamEndCapture(s, &body);
+  if (!end_capture("cudaStreamEndCapture (restart)")) return fail();
   for (int j = 0; j < m; ++j) {
-    cudaStreamBeginCaptureToGraph(s, ibody[j], nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (!ok(cudaStreamBeginCaptureToGraph(s, ibody[j], nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed),
+            "cudaStreamBeginCaptureToGraph (iteration)"))
+      return fail();
     c0 = launches_now();
     enqueue_iteration(P, j, s);
     P.kern_iter[j] = launches_now() - c0;
-    cudaStreamEndCapture(s, &ibody[j]);
-  }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    set_error(std::string("graph capture: ") + cudaGetErrorString(e));
-    cudaStreamDestroy(s);
-    return IIM_ERR_CUDA;
-  }
-  if (e != cudaSuccess) {
-    cudaStreamDestroy(s);
-    return IIM_ERR_CUDA;
+    if (!end_capture("cudaStreamEndCapture (iteration)")) return fail();
   }
   // the handles live in the solver scalars so that kernels can set them
   GraphHandles H = {};
@@ -632,14 +670,13 @@ iim_status krylov_build_graph(Problem& P, double* x) {
   for (int j = 0; j < m; ++j) H.h_if[j] = hif[j];
   k_set_handles<<<1, 1, 0, s>>>(P.sc, H);
   note_launch();
-  cudaStreamSynchronize(s);
-  e = cudaGraphInstantiate(&P.graph_exec, g, 0);
+  if (!ok(cudaGetLastError(), "k_set_handles launch")) return fail();
+  if (!ok(cudaStreamSynchronize(s), "cudaStreamSynchronize")) return fail();
+  cudaGraphExec_t ge = nullptr;
+  if (!ok(cudaGraphInstantiate(&ge, g, 0), "cudaGraphInstantiate")) return fail();
   cudaStreamDestroy(s);
+  P.graph_exec = ge;
   P.graph = g;
-  if (e != cudaSuccess) {
-    set_error(std::string("graph instantiate: ") + cudaGetErrorString(e));
-    return IIM_ERR_CUDA;
-  }
   return IIM_OK;
 }
 

@@ -89,6 +89,10 @@ def test_binding_constants_match_the_header():
     assert (iim.MG_FP32, iim.MG_FP64, iim.MG_FP32_BF16R) == (e["IIM_MG_FP32"], e["IIM_MG_FP64"], e["IIM_MG_FP32_BF16R"])
     assert (iim.CYCLE_V, iim.CYCLE_W) == (e["IIM_CYCLE_V"], e["IIM_CYCLE_W"])
     assert (iim.KRYLOV_FGMRES, iim.KRYLOV_GMRES_LEFT) == (e["IIM_KRYLOV_FGMRES"], e["IIM_KRYLOV_GMRES_LEFT"])
+    status = {k: v for k, v in e.items() if k.startswith("IIM_ERR_") or k == "IIM_OK"}
+    assert len(status) == len(iim.STATUS_NAMES)
+    for name, val in status.items():
+        assert getattr(iim, name) == val, name
 
 
 def test_options_struct_matches_the_header(lib_path):
