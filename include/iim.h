@@ -60,11 +60,14 @@ typedef enum {
 } iim_status;
 
 enum { IIM_GEOM_CIRCLE = 0, IIM_GEOM_ELLIPSE = 1, IIM_GEOM_STAR = 2, IIM_GEOM_SPHERE = 3, IIM_GEOM_ELLIPSOID = 4,
-       IIM_GEOM_PERTURBED_SPHERE = 5 };
+       IIM_GEOM_PERTURBED_SPHERE = 5, IIM_GEOM_FOURIER = 6, IIM_GEOM_LEVELSET_GRID = 7 };
+/* most modes of an IIM_GEOM_FOURIER curve */
+enum { IIM_MAX_FOURIER_MODES = 16 };
 enum { IIM_BC_DIRICHLET = 0, IIM_BC_NEUMANN = 1, IIM_BC_INTERFACE = 2 };
 enum { IIM_BOX_NONE = 0, IIM_BOX_DIRICHLET = 1 };
 /* Multigrid precision: FP32, FP64, or FP32 with every restricted residual (the
- * right-hand side of the coarser level) rounded to BF16 where it is stored. */
+ * right-hand side of each coarser level) stored as 2-byte BF16 (rounded to nearest even)
+ * and computed with in FP32. */
 enum { IIM_MG_FP32 = 0, IIM_MG_FP64 = 1, IIM_MG_FP32_BF16R = 2 };
 /* Multigrid cycle (Sec. 3.3 results): the V-cycle visits the next coarser level once
  * per visit of a level, the W-cycle twice, the second visit starting from the first
@@ -87,6 +90,22 @@ enum { IIM_KRYLOV_FGMRES = 0, IIM_KRYLOV_GMRES_LEFT = 1 };
  *                                     Y = (3 sqrt(3)/2) (e_x^2 - e_y^2) e_z (a degree-3 spherical
  *                                     harmonic scaled to max |Y| = 1; the radially perturbed
  *                                     sphere of the paper's 3D verification, Sec. 4.2)
+ *   FOURIER   cx cy                   g = |x - c| - r(theta), r(theta) = a0 + sum_{k=1..K}
+ *                                     (a_k cos k theta + b_k sin k theta): a closed curve given in
+ *                                     parametric (polar) form, 2D.  The coefficients are in
+ *                                     geom_coef; r must stay positive.  The coefficients are fixed
+ *                                     at creation (iim_problem_setup may move the centre).
+ *   LEVELSET_GRID (no parameters)     g = the level set given at the grid's own nodes (phi_dev),
+ *                                     2D or 3D.  Between nodes g is the tensor product of the
+ *                                     degree-5 Lagrange interpolants through the 6 nodes around
+ *                                     the point along each axis (shifted inwards at the grid's
+ *                                     edge), so that control points, normals (its gradient),
+ *                                     curvatures (its Hessian) and the coarse multigrid levels
+ *                                     all come from one function, exact for polynomial level
+ *                                     sets of degree <= 5 in each variable.  This is the form
+ *                                     of the paper's problem statement (Omega+ = {phi > 0},
+ *                                     Sec. 2.1 and the level-set domain of Sec. 4.4) for shapes
+ *                                     with no closed form here.  Needs n >= 16.
  */
 typedef struct {
   int dim;               /* 2 or 3 */
@@ -98,6 +117,14 @@ typedef struct {
   int box_bc;            /* IIM_BOX_*; interface problems need IIM_BOX_DIRICHLET */
   double beta_plus, beta_minus;
   int order;             /* 4 -> (4,5) scheme, 6 -> (6,7) scheme (Sec. 2.4) */
+  /* IIM_GEOM_FOURIER: host array a0, a1, b1, ..., aK, bK (n_geom_coef = 2 K + 1, 1 <= K <=
+   * IIM_MAX_FOURIER_MODES), copied by iim_problem_create.  NULL / 0 for other kinds. */
+  const double* geom_coef;
+  int n_geom_coef;
+  /* IIM_GEOM_LEVELSET_GRID: device array of the level set at the n^dim nodes (x0 fastest),
+   * copied by iim_problem_create (borrowed for that call only; iim_problem_set_phi replaces
+   * the copy).  NULL for other kinds. */
+  const double* phi_dev;
 } iim_problem_desc;
 
 typedef struct {
@@ -147,6 +174,11 @@ iim_status iim_problem_create(const iim_problem_desc* desc, const iim_options* o
  * capture it again). */
 iim_status iim_problem_setup(iim_problem* p, const double* geom_params);
 
+/* Replace the level set of an IIM_GEOM_LEVELSET_GRID problem by phi_dev (n^dim values at
+ * the grid's nodes, copied on the problem's stream); the next iim_problem_setup builds the
+ * set-up from it.  IIM_ERR_INVALID_ARG for other geometry kinds.  Asynchronous. */
+iim_status iim_problem_set_phi(iim_problem* p, const double* phi_dev);
+
 /* Synchronise the problem's stream and return the device status word. */
 iim_status iim_status_get(iim_problem* p);
 
@@ -163,6 +195,19 @@ iim_status iim_problem_bytes(iim_problem* p, size_t* bytes);
  * of the cut grid edge): xc_dev [K][dim], normal_dev [K][dim] (out of Omega+).
  * Either pointer may be NULL.  Asynchronous. */
 iim_status iim_control_points(iim_problem* p, double* xc_dev, double* normal_dev);
+
+/* Grid edge of every control point, in the order of iim_control_points: axis_dev [K] the
+ * axis of the cut edge, lower_dev [K] the flat index of its lower node, side_dev [K] 1 when
+ * the lower node is in Omega+ (the edge leaves Omega+ in the + direction of the axis), else 0.
+ * Any pointer may be NULL.  Asynchronous. */
+iim_status iim_control_point_edges(iim_problem* p, int32_t* axis_dev, int32_t* lower_dev, uint8_t* side_dev);
+
+/* Outer-box Dirichlet sample points (B of them, iim_problem_sizes): xb_dev [B][dim], in the
+ * order iim_set_data takes box_dev: faces (-x0, +x0, -x1, +x1, -x2, +x2), within a face the
+ * other node indices in flat order (lowest remaining axis fastest).  Each point lies on its
+ * face (coordinate -1 or +1) with the other coordinates of its grid line, half a cell
+ * beyond the line's last node.  IIM_ERR_INVALID_ARG without an outer box.  Asynchronous. */
+iim_status iim_box_points(iim_problem* p, double* xb_dev);
 
 /* Phase of every node (1 = Omega+) as bytes, n^d entries.  Asynchronous. */
 iim_status iim_phase(iim_problem* p, uint8_t* phase_dev);

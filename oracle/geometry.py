@@ -14,11 +14,22 @@ import math
 
 import numpy as np
 
-from workloads import CIRCLE, ELLIPSE, STAR, SPHERE, ELLIPSOID, PERTURBED_SPHERE, PERTURB_SCALE
+from workloads import (CIRCLE, ELLIPSE, STAR, SPHERE, ELLIPSOID, PERTURBED_SPHERE, PERTURB_SCALE, FOURIER,
+                       LEVELSET_GRID)
+
+# D_k = prod_{j != k} (k - j) over the six stencil nodes 0..5 of the degree-5 interpolant
+_LAG_DEN = np.array([-120.0, 24.0, -12.0, 12.0, -24.0, 120.0])
 
 
 class LevelSet:
-    """phi(x) for an analytic body; ``g`` is negative inside the body."""
+    """phi(x) for an analytic body, a polar Fourier curve or a level set given at the grid's
+    nodes; ``g`` is negative inside the body.
+
+    FOURIER: g = |x - c| - r(theta), r = a0 + sum_k (a_k cos k theta + b_k sin k theta).
+    LEVELSET_GRID: g is the level set given at the nodes of the problem's grid and, between
+    them, the tensor product of the degree-5 Lagrange interpolants through the six nodes
+    around the point along each axis (the six nodes shifted inwards at the grid's edge).
+    """
 
     def __init__(self, geometry):
         self.geom = geometry
@@ -26,6 +37,69 @@ class LevelSet:
         self.p = tuple(float(v) for v in geometry.params)
         self.sign = -1.0 if geometry.plus_inside else 1.0   # phi = sign * g
         self.dim = geometry.dim
+        if self.kind == FOURIER:
+            c = np.asarray(geometry.coef, dtype=float)
+            self.a0, self.fa, self.fb = c[0], c[1::2], c[2::2]
+        if self.kind == LEVELSET_GRID:
+            self.values = np.asarray(geometry.values, dtype=float)
+            self.gn = self.values.shape[0]
+            self.gh = 2.0 / self.gn
+
+    # polar Fourier curve ------------------------------------------------------------
+    def _fourier(self, th):
+        """r, r', r'' of the Fourier curve at angles th."""
+        k = np.arange(1, self.fa.size + 1)
+        kt = th[..., None] * k
+        ck, sk = np.cos(kt), np.sin(kt)
+        r = self.a0 + np.sum(self.fa * ck + self.fb * sk, axis=-1)
+        r1 = np.sum(k * (self.fb * ck - self.fa * sk), axis=-1)
+        r2 = -np.sum(k * k * (self.fa * ck + self.fb * sk), axis=-1)
+        return r, r1, r2
+
+    # level set given at the nodes ----------------------------------------------------
+    def _lagrange(self, x, order):
+        """First stencil node s and the weights of the value (order 0), first (1) or second
+        (2) derivative along one axis for coordinates x: the derivatives of the Lagrange
+        basis l_k(t) = prod_{j != k} (t - j) / D_k, t = (x - x_s) / h.  A coordinate equal
+        to a node's takes that node's integer t, so that the interpolant returns the given
+        value there."""
+        n, h = self.gn, self.gh
+        tc = (x + 1.0) / h - 0.5
+        s = np.clip(np.floor(tc).astype(np.int64) - 2, 0, n - 6)
+        m = np.floor(tc + 0.5).astype(np.int64)
+        at_node = (m >= s) & (m <= s + 5) & (-1.0 + (m + 0.5) * h == x)
+        t = np.where(at_node, (m - s).astype(float), tc - s)
+        d = t[..., None] - np.arange(6.0)
+        w = np.zeros(x.shape + (6,))
+        for k in range(6):
+            others = [j for j in range(6) if j != k]
+            if order == 0:
+                acc = np.prod(d[..., others], axis=-1)
+            elif order == 1:
+                acc = sum(np.prod(d[..., [l for l in others if l != j]], axis=-1) for j in others)
+            else:
+                acc = sum(np.prod(d[..., [q for q in others if q not in (j, l)]], axis=-1)
+                          for j in others for l in others if l != j)
+            w[..., k] = acc / (_LAG_DEN[k] * h ** order)
+        return s, w
+
+    def _grid_eval(self, X, orders):
+        """Tensor-product interpolant (orders: derivative order along each axis)."""
+        d = self.dim
+        flat = X.reshape(-1, d)
+        sw = [self._lagrange(flat[:, a], orders[a]) for a in range(d)]
+        r6 = np.arange(6)
+        if d == 2:
+            (s0, w0), (s1, w1) = sw
+            V = self.values[(s0[:, None, None] + r6[None, :, None]), (s1[:, None, None] + r6[None, None, :])]
+            out = np.einsum("pi,pj,pij->p", w0, w1, V)
+        else:
+            (s0, w0), (s1, w1), (s2, w2) = sw
+            V = self.values[(s0[:, None, None, None] + r6[None, :, None, None]),
+                            (s1[:, None, None, None] + r6[None, None, :, None]),
+                            (s2[:, None, None, None] + r6[None, None, None, :])]
+            out = np.einsum("pi,pj,pk,pijk->p", w0, w1, w2, V)
+        return out.reshape(X.shape[:-1])
 
     # body function g and its gradient / Hessian -------------------------------------
     def g(self, X):
@@ -46,6 +120,12 @@ class LevelSet:
             rho = np.hypot(dx, dy)
             th = np.arctan2(dy, dx)
             return rho - (p[2] + p[3] * np.sin(p[4] * th + p[5]))
+        if self.kind == FOURIER:
+            dx, dy = X[..., 0] - p[0], X[..., 1] - p[1]
+            r, _, _ = self._fourier(np.arctan2(dy, dx))
+            return np.hypot(dx, dy) - r
+        if self.kind == LEVELSET_GRID:
+            return self._grid_eval(X, [0] * self.dim)
         if self.kind == PERTURBED_SPHERE:
             # g = r - rho0 - rho1 c Q(d) / r^3 with d = x - centre, r = |d|, Q = (dx^2 - dy^2) dz:
             # Q / r^3 is the harmonic (e_x^2 - e_y^2) e_z of the direction e = d / r
@@ -83,6 +163,16 @@ class LevelSet:
             er = np.stack([dx / rho, dy / rho], axis=-1)
             et = np.stack([-dy / rho, dx / rho], axis=-1)
             return er - (rp / rho)[..., None] * et
+        if self.kind == FOURIER:
+            dx, dy = X[..., 0] - p[0], X[..., 1] - p[1]
+            rho = np.hypot(dx, dy)
+            _, rp, _ = self._fourier(np.arctan2(dy, dx))
+            er = np.stack([dx / rho, dy / rho], axis=-1)
+            et = np.stack([-dy / rho, dx / rho], axis=-1)
+            return er - (rp / rho)[..., None] * et
+        if self.kind == LEVELSET_GRID:
+            return np.stack([self._grid_eval(X, [1 if b == a else 0 for b in range(self.dim)])
+                             for a in range(self.dim)], axis=-1)
         if self.kind == PERTURBED_SPHERE:
             d = X - np.array(p[:3])
             r = np.sqrt(np.sum(d * d, axis=-1))[..., None]
@@ -113,6 +203,10 @@ class LevelSet:
             r2 = -p[3] * p[4] ** 2 * np.sin(p[4] * th + p[5])
             # curvature of the polar curve r(theta)
             return np.abs(r * r + 2 * r1 * r1 - r * r2) / (r * r + r1 * r1) ** 1.5
+        if self.kind == FOURIER:
+            dx, dy = X[..., 0] - p[0], X[..., 1] - p[1]
+            r, r1, r2 = self._fourier(np.arctan2(dy, dx))
+            return np.abs(r * r + 2 * r1 * r1 - r * r2) / (r * r + r1 * r1) ** 1.5
         # shape operator P H P / |grad g| on the tangent space (H: Hessian of g)
         if self.kind == ELLIPSE:
             c, s = math.cos(p[4]), math.sin(p[4])
@@ -137,12 +231,22 @@ class LevelSet:
         return res.reshape(X.shape[:-1])
 
     def hess_g(self, X):
-        """Hessian of g for PERTURBED_SPHERE:
+        """Hessian of g for PERTURBED_SPHERE and LEVELSET_GRID; for the perturbed sphere:
         (I - e e^T) / r - rho1 c [Hess Q r^-3 - 3 r^-5 (grad Q d^T + d grad Q^T)
                                   + Q (-3 r^-5 I + 15 r^-7 d d^T)]."""
         p = self.p
+        if self.kind == LEVELSET_GRID:
+            d = self.dim
+            H = np.zeros(X.shape[:-1] + (d, d))
+            for a in range(d):
+                for b in range(a, d):
+                    orders = [0] * d
+                    orders[a] += 1
+                    orders[b] += 1
+                    H[..., a, b] = H[..., b, a] = self._grid_eval(X, orders)
+            return H
         if self.kind != PERTURBED_SPHERE:
-            raise ValueError("hess_g: perturbed sphere only")
+            raise ValueError("hess_g: perturbed sphere or grid level set only")
         d = X - np.array(p[:3])
         r = np.sqrt(np.sum(d * d, axis=-1))[..., None, None]
         dd = d[..., :, None] * d[..., None, :]

@@ -19,7 +19,9 @@ IIM_ERR_NOT_CONVERGED, IIM_ERR_BREAKDOWN, IIM_ERR_BUDGET, IIM_ERR_TIMEOUT = 5, 6
 IIM_ERR_CUDA, IIM_ERR_GEOMETRY, IIM_ERR_CAPACITY = 9, 10, 11
 STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "curvature", 3: "rank", 4: "singular", 5: "not converged",
                 6: "breakdown", 7: "budget", 8: "timeout", 9: "cuda", 10: "geometry", 11: "capacity"}
-GEOM = {"circle": 0, "ellipse": 1, "star": 2, "sphere": 3, "ellipsoid": 4, "perturbed_sphere": 5}
+GEOM = {"circle": 0, "ellipse": 1, "star": 2, "sphere": 3, "ellipsoid": 4, "perturbed_sphere": 5, "fourier": 6,
+        "levelset_grid": 7}
+MAX_FOURIER_MODES = 16
 BC = {"dirichlet": 0, "neumann": 1, "interface": 2}
 MG_FP32, MG_FP64, MG_FP32_BF16R = 0, 1, 2
 CYCLE_V, CYCLE_W = 1, 2
@@ -36,7 +38,8 @@ class Desc(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("geom_kind", ctypes.c_int),
                 ("plus_inside", ctypes.c_int), ("geom_params", ctypes.c_double * 8), ("bc", ctypes.c_int),
                 ("box_bc", ctypes.c_int), ("beta_plus", ctypes.c_double), ("beta_minus", ctypes.c_double),
-                ("order", ctypes.c_int)]
+                ("order", ctypes.c_int), ("geom_coef", ctypes.c_void_p), ("n_geom_coef", ctypes.c_int),
+                ("phi_dev", ctypes.c_void_p)]
 
 
 class Options(ctypes.Structure):
@@ -71,6 +74,9 @@ SIGNATURES = {
     "iim_problem_fit_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                              ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]),
     "iim_phase": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "iim_control_point_edges": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "iim_box_points": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "iim_problem_set_phi": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "iim_set_data": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 5),
     "iim_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "iim_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -150,7 +156,11 @@ def default_options(**kw) -> Options:
     return o
 
 
-def make_desc(dim, n, geom_kind, geom_params, plus_inside, bc, box_bc, beta_plus=1.0, beta_minus=1.0, order=4):
+def make_desc(dim, n, geom_kind, geom_params, plus_inside, bc, box_bc, beta_plus=1.0, beta_minus=1.0, order=4,
+              coef=None, phi=None):
+    """``coef``: the Fourier curve's a0, a1, b1, ... (host); ``phi``: a contiguous float64 CUDA
+    tensor of the level set at the grid's nodes (x0 fastest).  The descriptor keeps both
+    alive (they are read when the problem is created)."""
     d = Desc()
     d.dim, d.n, d.geom_kind, d.plus_inside = int(dim), int(n), int(geom_kind), int(bool(plus_inside))
     p = list(geom_params) + [0.0] * (8 - len(geom_params))
@@ -159,14 +169,29 @@ def make_desc(dim, n, geom_kind, geom_params, plus_inside, bc, box_bc, beta_plus
     d.bc, d.box_bc = int(bc), int(box_bc)
     d.beta_plus, d.beta_minus = float(beta_plus), float(beta_minus)
     d.order = int(order)
+    d._keep = []
+    if coef is not None and len(coef):
+        arr = (ctypes.c_double * len(coef))(*[float(v) for v in coef])
+        d._keep.append(arr)
+        d.geom_coef = ctypes.cast(arr, ctypes.c_void_p)
+        d.n_geom_coef = len(coef)
+    if phi is not None:
+        d._keep.append(phi)
+        d.phi_dev = _ptr(phi)
     return d
 
 
 def desc_from_spec(spec) -> Desc:
     """Descriptor from any object with the fields of a problem statement (n, geometry, bc, ...)."""
     g = spec.geometry
+    phi = None
+    if g.kind == GEOM["levelset_grid"]:
+        import numpy as np
+        import torch
+        phi = torch.as_tensor(np.ascontiguousarray(np.asarray(g.values).ravel(order="F")), dtype=torch.float64,
+                              device="cuda")
     return make_desc(g.dim, spec.n, g.kind, g.params, g.plus_inside, spec.bc, spec.box_bc,
-                     spec.beta_plus, spec.beta_minus, spec.order)
+                     spec.beta_plus, spec.beta_minus, spec.order, coef=getattr(g, "coef", None), phi=phi)
 
 
 def _ptr(t):
@@ -277,6 +302,31 @@ class Problem:
         _check(load().iim_control_points(self.h, _ptr(xc), _ptr(nc)))
         self._foreign_stream_sync(False)
         return xc[:self.K], nc[:self.K]
+
+    def control_point_edges(self):
+        """(axis, lower node, side) of every control point's grid edge (see iim_control_point_edges)."""
+        import torch
+        ax = torch.empty(max(self.K, 1), dtype=torch.int32, device="cuda")
+        lo = torch.empty(max(self.K, 1), dtype=torch.int32, device="cuda")
+        sd = torch.empty(max(self.K, 1), dtype=torch.uint8, device="cuda")
+        self._foreign_stream_sync(True)
+        _check(load().iim_control_point_edges(self.h, ctypes.c_void_p(ax.data_ptr()), ctypes.c_void_p(lo.data_ptr()),
+                                              ctypes.c_void_p(sd.data_ptr())), "iim_control_point_edges")
+        self._foreign_stream_sync(False)
+        return ax[:self.K], lo[:self.K], sd[:self.K]
+
+    def box_points(self):
+        """Outer-box Dirichlet sample points, shape (B, dim) (see iim_box_points)."""
+        xb = self._empty(max(self.B, 1), self.dim)
+        self._foreign_stream_sync(True)
+        _check(load().iim_box_points(self.h, _ptr(xb)), "iim_box_points")
+        self._foreign_stream_sync(False)
+        return xb[:self.B]
+
+    def set_phi(self, phi):
+        """Replace a grid level set's node values (then call setup())."""
+        self._foreign_stream_sync(True)
+        _check(load().iim_problem_set_phi(self.h, _ptr(phi)), "iim_problem_set_phi")
 
     def phase(self):
         import torch

@@ -1,5 +1,6 @@
 // C ABI of the library (declared in include/iim.h): problem life cycle, data,
 // operator / preconditioner calls, the FGMRES solve and the batched solve.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -156,10 +157,35 @@ static iim_status validate(const iim_problem_desc* d, const iim_options* o) {
     return IIM_ERR_INVALID_ARG;
   }
   if (d->n < 16 || d->n > (d->dim == 2 ? 32768 : 1024)) return IIM_ERR_INVALID_ARG;
-  bool k2 = d->geom_kind == IIM_GEOM_CIRCLE || d->geom_kind == IIM_GEOM_ELLIPSE || d->geom_kind == IIM_GEOM_STAR;
+  const bool grid = d->geom_kind == IIM_GEOM_LEVELSET_GRID;
+  bool k2 = d->geom_kind == IIM_GEOM_CIRCLE || d->geom_kind == IIM_GEOM_ELLIPSE || d->geom_kind == IIM_GEOM_STAR ||
+            d->geom_kind == IIM_GEOM_FOURIER || grid;
   bool k3 = d->geom_kind == IIM_GEOM_SPHERE || d->geom_kind == IIM_GEOM_ELLIPSOID ||
-            d->geom_kind == IIM_GEOM_PERTURBED_SPHERE;
+            d->geom_kind == IIM_GEOM_PERTURBED_SPHERE || grid;
   if ((d->dim == 2 && !k2) || (d->dim == 3 && !k3)) return IIM_ERR_INVALID_ARG;
+  if (grid && !d->phi_dev) {
+    set_error("a level set on the grid needs phi_dev");
+    return IIM_ERR_INVALID_ARG;
+  }
+  if (d->geom_kind == IIM_GEOM_FOURIER) {
+    const int nc = d->n_geom_coef;
+    if (!d->geom_coef || nc < 3 || nc % 2 == 0 || nc > 2 * IIM_MAX_FOURIER_MODES + 1) {
+      set_error("a Fourier curve needs 2 K + 1 coefficients, 1 <= K <= 16");
+      return IIM_ERR_INVALID_ARG;
+    }
+    // r(theta) > 0 on a fine sampling of the curve
+    double rmin = 1e300;
+    for (int i = 0; i < 8192; ++i) {
+      const double th = 6.283185307179586 * i / 8192.0;
+      double r = d->geom_coef[0];
+      for (int k = 1; 2 * k < nc; ++k) r += d->geom_coef[2 * k - 1] * std::cos(k * th) + d->geom_coef[2 * k] * std::sin(k * th);
+      rmin = std::min(rmin, r);
+    }
+    if (!(rmin > 0)) {
+      set_error("a Fourier curve needs r(theta) > 0");
+      return IIM_ERR_INVALID_ARG;
+    }
+  }
   if (d->bc < 0 || d->bc > 2 || d->box_bc < 0 || d->box_bc > 1) return IIM_ERR_INVALID_ARG;
   if (d->bc == IIM_BC_INTERFACE && d->box_bc != IIM_BOX_DIRICHLET) {
     set_error("interface problems need a Dirichlet outer box");
@@ -252,6 +278,10 @@ iim_status iim_problem_create(const iim_problem_desc* desc, const iim_options* o
   P.desc = *desc;
   P.opt = *opt;
   P.stream = (cudaStream_t)stream;
+  if (desc->geom_kind == IIM_GEOM_FOURIER) P.geom_coef.assign(desc->geom_coef, desc->geom_coef + desc->n_geom_coef);
+  P.desc.geom_coef = nullptr;
+  P.desc.n_geom_coef = 0;
+  P.desc.phi_dev = nullptr;
   const int d = desc->dim, n = desc->n;
   P.g.dim = d;
   P.g.n = n;
@@ -295,6 +325,14 @@ iim_status iim_problem_create(const iim_problem_desc* desc, const iim_options* o
   cudaMemcpyAsync(P.d_monos, mono.data(), sizeof(int) * mono.size(), cudaMemcpyHostToDevice, P.stream);
   cudaStreamSynchronize(P.stream);
   IIM_ALLOC(P.d_status, int, 4);
+  if (desc->geom_kind == IIM_GEOM_LEVELSET_GRID) {
+    IIM_ALLOC(P.phi_grid, double, N);
+    if (cudaMemcpyAsync(P.phi_grid, desc->phi_dev, sizeof(double) * N, cudaMemcpyDeviceToDevice, P.stream) !=
+        cudaSuccess) {
+      cuda_check("copy of the level set");
+      IIM_FAIL(IIM_ERR_INVALID_ARG);
+    }
+  }
   IIM_ALLOC(P.d_counts, int, kCountSlots);
   cudaMemsetAsync(P.d_status, 0, sizeof(int) * 4, P.stream);
   cudaMemsetAsync(P.d_counts, 0, sizeof(int) * kCountSlots, P.stream);
@@ -377,15 +415,17 @@ iim_status iim_problem_create(const iim_problem_desc* desc, const iim_options* o
     if (l == 0) L.phase = P.phase;
     else IIM_ALLOC(L.phase, uint8_t, L.g.N);
     IIM_ALLOC(L.aux, int32_t, L.g.N);
+    IIM_ALLOC(L.cls, uint8_t, L.g.N);
     IIM_ALLOC(L.flag, int32_t, L.g.N);
     IIM_ALLOC(L.idx, int32_t, L.g.N);
     L.u = dev_alloc(P, esz * L.g.N);
     L.u2 = dev_alloc(P, esz * L.g.N);
-    L.f = dev_alloc(P, esz * L.g.N);
+    const size_t fsz = L.f_bf16 ? 2 : esz;        // restricted residuals stored as BF16
+    L.f = dev_alloc(P, fsz * L.g.N);
     if (!L.u || !L.u2 || !L.f) IIM_FAIL(IIM_ERR_BUDGET);
     cudaMemsetAsync(L.u, 0, esz * L.g.N, P.stream);
     cudaMemsetAsync(L.u2, 0, esz * L.g.N, P.stream);
-    cudaMemsetAsync(L.f, 0, esz * L.g.N, P.stream);
+    cudaMemsetAsync(L.f, 0, fsz * L.g.N, P.stream);
   }
   setup_levels(P, true);
   cudaStreamSynchronize(P.stream);
@@ -463,6 +503,17 @@ static iim_status setup_enqueue(Problem& P) {
 
 // The set-up is a fixed sequence of kernels with no host decision in it, so (with
 // use_graph) it is captured once per geometry and replayed as one graph launch.
+iim_status iim_problem_set_phi(iim_problem* H, const double* phi_dev) {
+  if (!H || !phi_dev) return IIM_ERR_INVALID_ARG;
+  Problem& P = H->P;
+  if (P.desc.geom_kind != IIM_GEOM_LEVELSET_GRID || !P.phi_grid) {
+    set_error("iim_problem_set_phi: the problem's geometry is not a level set on the grid");
+    return IIM_ERR_INVALID_ARG;
+  }
+  cudaMemcpyAsync(P.phi_grid, phi_dev, sizeof(double) * P.g.N, cudaMemcpyDeviceToDevice, P.stream);
+  return cuda_check("iim_problem_set_phi");
+}
+
 iim_status iim_problem_setup(iim_problem* H, const double* params) {
   if (!H) return IIM_ERR_INVALID_ARG;
   Problem& P = H->P;
@@ -578,6 +629,27 @@ iim_status iim_control_points(iim_problem* H, double* xc, double* nrm) {
   if (xc) cudaMemcpyAsync(xc, P.cr_x, sizeof(double) * (size_t)K * P.g.dim, cudaMemcpyDeviceToDevice, P.stream);
   if (nrm) cudaMemcpyAsync(nrm, P.cr_n, sizeof(double) * (size_t)K * P.g.dim, cudaMemcpyDeviceToDevice, P.stream);
   return cuda_check("control points");
+}
+
+iim_status iim_control_point_edges(iim_problem* H, int32_t* axis, int32_t* lower, uint8_t* side) {
+  if (!H) return IIM_ERR_INVALID_ARG;
+  Problem& P = H->P;
+  int K = P.K = read_count(P, 0);
+  if (axis) cudaMemcpyAsync(axis, P.cr_axis, sizeof(int32_t) * (size_t)K, cudaMemcpyDeviceToDevice, P.stream);
+  if (lower) cudaMemcpyAsync(lower, P.cr_lo, sizeof(int32_t) * (size_t)K, cudaMemcpyDeviceToDevice, P.stream);
+  if (side) cudaMemcpyAsync(side, P.cr_loplus, (size_t)K, cudaMemcpyDeviceToDevice, P.stream);
+  return cuda_check("control point edges");
+}
+
+iim_status iim_box_points(iim_problem* H, double* xb) {
+  if (!H || !xb) return IIM_ERR_INVALID_ARG;
+  Problem& P = H->P;
+  if (!P.box_active) {
+    set_error("iim_box_points: the problem has no outer box");
+    return IIM_ERR_INVALID_ARG;
+  }
+  box_points(P, xb, P.stream);
+  return cuda_check("box points");
 }
 
 iim_status iim_phase(iim_problem* H, uint8_t* phase) {

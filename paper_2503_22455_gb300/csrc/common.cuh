@@ -25,13 +25,133 @@ constexpr int kNumSMs = 152;
 __host__ __device__ inline int status_code(int s) { return s; }
 
 // --------------------------------------------------------------------------- geometry
+constexpr int kMaxFourierModes = 16;
+
 struct Geom {
   int kind;
   int dim;
   double sign;                         // phi = sign * g
   double p[8];
   double cs, sn;                       // ellipse: cos and sin of the rotation angle p[4]
+  int modes;                           // FOURIER: number of modes K
+  double fc[2 * kMaxFourierModes + 1]; // FOURIER: a0, a1, b1, ..., aK, bK of r(theta)
+  const double* phi;                   // LEVELSET_GRID: values at the n^dim nodes, x0 fastest
+  int gn;                              // LEVELSET_GRID: nodes per axis
+  double gh;                           // LEVELSET_GRID: node spacing 2 / gn
 };
+
+// ---------------------------------------------------------------------------------------
+// Polar Fourier curve r(theta) = a0 + sum_k (a_k cos k theta + b_k sin k theta) around
+// (p0, p1): r and its first two derivatives in theta.
+__host__ __device__ inline void fourier_r(const Geom& G, double th, double* r, double* r1, double* r2) {
+  double v = G.fc[0], d1 = 0, d2 = 0;
+  for (int k = 1; k <= G.modes; ++k) {
+    const double a = G.fc[2 * k - 1], b = G.fc[2 * k];
+    double sk, ck;
+    sincos(k * th, &sk, &ck);
+    v += a * ck + b * sk;
+    d1 += k * (b * ck - a * sk);
+    d2 -= (double)k * k * (a * ck + b * sk);
+  }
+  *r = v;
+  *r1 = d1;
+  *r2 = d2;
+}
+
+// Level set given at the grid nodes: between nodes it is the tensor product of the degree-5
+// Lagrange interpolants through the 6 nodes around the point along each axis (the stencil
+// is shifted inwards at the grid's edge).  Along one axis, for coordinate x: s is the first
+// stencil node and w0 / w1 / w2 the weights of the value and of its first and second
+// derivative in x.  A coordinate equal to a node's (computed as for the grid) gets the
+// weights of that node alone, so the interpolant takes the given values at the nodes.
+__host__ __device__ inline void lag6(double x, int n, double h, int* s_out, double* w0, double* w1, double* w2) {
+  const double tc = (x + 1.0) / h - 0.5;
+  int s = (int)floor(tc) - 2;
+  s = s < 0 ? 0 : (s > n - 6 ? n - 6 : s);
+  *s_out = s;
+  // at a node the local coordinate is that node's integer index: the products below are
+  // then exact and the value weights are exactly 1 and 0
+  const int m = (int)floor(tc + 0.5);
+  const bool at_node = m >= s && m <= s + 5 && -1.0 + ((double)m + 0.5) * h == x;
+  const double t = at_node ? (double)(m - s) : tc - (double)s;
+  const double D[6] = {-120.0, 24.0, -12.0, 12.0, -24.0, 120.0};   // prod_{j != k} (k - j)
+  double d[6];
+  for (int k = 0; k < 6; ++k) d[k] = t - k;
+  for (int k = 0; k < 6; ++k) {
+    double v = 1.0;
+    for (int j = 0; j < 6; ++j)
+      if (j != k) v *= d[j];
+    w0[k] = v / D[k];
+    if (w1) {
+      double a = 0.0;
+      for (int j = 0; j < 6; ++j) {
+        if (j == k) continue;
+        double pr = 1.0;
+        for (int l = 0; l < 6; ++l)
+          if (l != k && l != j) pr *= d[l];
+        a += pr;
+      }
+      w1[k] = a / (D[k] * h);
+    }
+    if (w2) {
+      double a = 0.0;
+      for (int j = 0; j < 6; ++j) {
+        if (j == k) continue;
+        for (int l = 0; l < 6; ++l) {
+          if (l == k || l == j) continue;
+          double pr = 1.0;
+          for (int q = 0; q < 6; ++q)
+            if (q != k && q != j && q != l) pr *= d[q];
+          a += pr;
+        }
+      }
+      w2[k] = a / (D[k] * h * h);
+    }
+  }
+}
+
+// value (der = -1), first derivative along axis der (0..dim-1), or second derivative
+// d^2 / dx_a dx_b (der = 10 + 3 a + b) of the grid level set's interpolant at x
+__host__ __device__ inline double levelset_eval(const Geom& G, const double* x, int der) {
+  const int n = G.gn, d = G.dim;
+  int s[3] = {0, 0, 0};
+  double w[3][6];
+  double t0[6], t1[6], t2[6];
+  int da = -1, db = -1;
+  if (der >= 10) { da = (der - 10) / 3; db = (der - 10) % 3; }
+  else if (der >= 0) da = der;
+  for (int ax = 0; ax < d; ++ax) {
+    const int k1 = (ax == da) + (ax == db);        // derivative order along this axis
+    lag6(x[ax], n, G.gh, &s[ax], t0, k1 >= 1 ? t1 : nullptr, k1 >= 2 ? t2 : nullptr);
+    for (int k = 0; k < 6; ++k) w[ax][k] = k1 == 0 ? t0[k] : (k1 == 1 ? t1[k] : t2[k]);
+  }
+  double acc = 0.0;
+  if (d == 2) {
+    for (int j = 0; j < 6; ++j) {
+      if (w[1][j] == 0.0) continue;
+      const double* row = G.phi + (int64_t)(s[1] + j) * n + s[0];
+      double r = 0.0;
+      for (int i = 0; i < 6; ++i)
+        if (w[0][i] != 0.0) r += w[0][i] * row[i];
+      acc += w[1][j] * r;
+    }
+  } else {
+    for (int l = 0; l < 6; ++l) {
+      if (w[2][l] == 0.0) continue;
+      double pl = 0.0;
+      for (int j = 0; j < 6; ++j) {
+        if (w[1][j] == 0.0) continue;
+        const double* row = G.phi + ((int64_t)(s[2] + l) * n + (s[1] + j)) * n + s[0];
+        double r = 0.0;
+        for (int i = 0; i < 6; ++i)
+          if (w[0][i] != 0.0) r += w[0][i] * row[i];
+        pl += w[1][j] * r;
+      }
+      acc += w[2][l] * pl;
+    }
+  }
+  return acc;
+}
 
 // Perturbed sphere: g = r - rho0 - rho1 c Q(d) / r^3 (-rho0 at the centre), d = x - centre, r = |d|,
 // Q = (dx^2 - dy^2) dz, so that Q / r^3 is the degree-3 harmonic (e_x^2 - e_y^2) e_z of the
@@ -62,6 +182,13 @@ __host__ __device__ inline double geom_g(const Geom& G, const double* x) {
       double rho = hypot(dx, dy), th = atan2(dy, dx);
       return rho - (p[2] + p[3] * sin(p[4] * th + p[5]));
     }
+    case IIM_GEOM_FOURIER: {
+      const double dx = x[0] - p[0], dy = x[1] - p[1];
+      double r, r1, r2;
+      fourier_r(G, atan2(dy, dx), &r, &r1, &r2);
+      return hypot(dx, dy) - r;
+    }
+    case IIM_GEOM_LEVELSET_GRID: return levelset_eval(G, x, -1);
     case IIM_GEOM_PERTURBED_SPHERE: {
       double a = x[0] - p[0], b = x[1] - p[1], c = x[2] - p[2];
       double r = sqrt(a * a + b * b + c * c);
@@ -104,6 +231,18 @@ __host__ __device__ inline void geom_grad_g(const Geom& G, const double* x, doub
       double rp = p[3] * p[4] * cos(p[4] * th + p[5]);
       gr[0] = dx / rho + rp / rho * (dy / rho);
       gr[1] = dy / rho - rp / rho * (dx / rho);
+      return;
+    }
+    case IIM_GEOM_FOURIER: {
+      double dx = x[0] - p[0], dy = x[1] - p[1];
+      double rho = hypot(dx, dy), r, rp, r2;
+      fourier_r(G, atan2(dy, dx), &r, &rp, &r2);
+      gr[0] = dx / rho + rp / rho * (dy / rho);
+      gr[1] = dy / rho - rp / rho * (dx / rho);
+      return;
+    }
+    case IIM_GEOM_LEVELSET_GRID: {
+      for (int a = 0; a < G.dim; ++a) gr[a] = levelset_eval(G, x, a);
       return;
     }
     case IIM_GEOM_PERTURBED_SPHERE: {
@@ -212,6 +351,24 @@ __host__ __device__ inline double geom_curvature(const Geom& G, const double* x)
       double m = 0.5 * (s11 + s22), dd = sqrt(0.25 * (s11 - s22) * (s11 - s22) + s12 * s12);
       return fmax(fabs(m + dd), fabs(m - dd));
     }
+    case IIM_GEOM_FOURIER: {
+      double r, r1, r2;
+      fourier_r(G, atan2(x[1] - p[1], x[0] - p[0]), &r, &r1, &r2);
+      double den = r * r + r1 * r1;
+      return fabs(r * r + 2 * r1 * r1 - r * r2) / (den * sqrt(den));
+    }
+    case IIM_GEOM_LEVELSET_GRID: {
+      double gr[3], H[9];
+      for (int a = 0; a < G.dim; ++a) gr[a] = levelset_eval(G, x, a);
+      for (int a = 0; a < G.dim; ++a)
+        for (int b = a; b < G.dim; ++b) H[3 * a + b] = H[3 * b + a] = levelset_eval(G, x, 10 + 3 * a + b);
+      if (G.dim == 2) {
+        // curvature of the level curve: (g_xx g_y^2 - 2 g_xy g_x g_y + g_yy g_x^2) / |grad g|^3
+        double gn = hypot(gr[0], gr[1]);
+        return fabs(H[0] * gr[1] * gr[1] - 2 * H[1] * gr[0] * gr[1] + H[4] * gr[0] * gr[0]) / (gn * gn * gn);
+      }
+      return shape_max_curvature3(gr, H);
+    }
     case IIM_GEOM_PERTURBED_SPHERE: {
       double gr[3], H[9];
       geom_grad_g(G, x, gr);
@@ -284,6 +441,26 @@ __device__ inline float store_residual(float v, int bf16) {
   return bf16 ? __bfloat162float(__float2bfloat16_rn(v)) : v;
 }
 __device__ inline double store_residual(double v, int) { return v; }
+
+// The right-hand side f of a multigrid level as stored.  Levels whose f is a restricted
+// residual in the BF16-residual form keep it as 2-byte BF16 values (rounded to nearest
+// even when stored); every other f is stored in the level's precision.  Values read are
+// those store_residual gives, so both forms of storage compute the same numbers.
+__device__ inline float load_f(const float* f, int64_t i, int bf16) {
+  return bf16 ? __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(f)[i]) : f[i];
+}
+__device__ inline double load_f(const double* f, int64_t i, int) { return f[i]; }
+__device__ inline void store_f(float* f, int64_t i, float v, int bf16) {
+  if (bf16) reinterpret_cast<__nv_bfloat16*>(f)[i] = __float2bfloat16_rn(v);
+  else f[i] = v;
+}
+__device__ inline void store_f(double* f, int64_t i, double v, int) { f[i] = v; }
+// two consecutive values (i even)
+__device__ inline float2 load_f2(const float* f, int64_t i, int bf16) {
+  if (bf16) return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(reinterpret_cast<const __nv_bfloat16*>(f) + i));
+  return *reinterpret_cast<const float2*>(f + i);
+}
+__device__ inline double2 load_f2(const double* f, int64_t i, int) { return *reinterpret_cast<const double2*>(f + i); }
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 

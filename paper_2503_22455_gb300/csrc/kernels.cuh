@@ -1,5 +1,6 @@
 // Problem workspace and the entry points shared between the library's translation units.
 #pragma once
+#include <vector>
 
 #include "common.cuh"
 
@@ -21,6 +22,7 @@ struct Level {
   GridView g;
   uint8_t* phase = nullptr;
   int32_t* aux = nullptr;
+  uint8_t* cls = nullptr;         // per node: 1 unknown, 2 irregular row, 4 phase + (red-black tile kernels)
   int32_t* flag = nullptr;        // scratch for the irregular-node scan
   int32_t* idx = nullptr;
   int n_irr = 0, irr_cap = 0;
@@ -91,8 +93,10 @@ struct CorrectParams {
 constexpr int kCountK = 0, kCountAff = 1, kCountLevel0 = 2, kMaxLevels = 24, kCountCoarse = 40, kCountSlots = 48;
 
 struct Problem {
-  iim_problem_desc desc;
+  iim_problem_desc desc;          // geom_coef and phi_dev are cleared after create (copies below)
   iim_options opt;
+  std::vector<double> geom_coef;  // FOURIER coefficients
+  double* phi_grid = nullptr;     // LEVELSET_GRID: the problem's copy of the node values
   cudaStream_t stream = nullptr;
   Geom geom;
   GridView g;
@@ -193,6 +197,7 @@ void ho_apply(Problem& P, const double* u, double* w, bool with_data, cudaStream
 void ho_stencil(Problem& P, const double* u, double* w, cudaStream_t s);
 void ho_ghost(Problem& P, const double* u, bool with_data, cudaStream_t s);
 void ho_correct(Problem& P, const double* u, double* w, bool with_data, cudaStream_t s);
+void box_points(Problem& P, double* xb, cudaStream_t s);
 iim_status ho_apply_noalloc(Problem& P, const double* u, double* w, bool with_data, cudaStream_t s);
 void compute_rhs(Problem& P, const double* f, cudaStream_t s);
 iim_status boundary_values(Problem& P, const double* u, double* out, cudaStream_t s);

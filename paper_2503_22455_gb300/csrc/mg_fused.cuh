@@ -30,7 +30,7 @@ struct LevelK {
   const T* tab;
   T* u;
   T* f;
-  int f_bf16;     // f holds restricted residuals rounded to BF16
+  int f_bf16;     // f holds restricted residuals stored as BF16 (load_f / store_f)
 };
 
 template <typename T>
@@ -134,7 +134,7 @@ __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx
         const int64_t g = (int64_t)gy * n + gx;
         ra[q] = __ldg(L.aux + g);
         if (finest_in) rf[q] = mul_rn((T)__ldg(P.v + g), mul_rn(vs, one_beta || __ldg(P.phase + g) ? P.inv_bp : P.inv_bm));
-        else rf[q] = L.f[g];
+        else rf[q] = load_f(L.f, g, L.f_bf16);
         if (!DOWN_FIRST) ru[q] = P.u_in[g];
       }
     }
@@ -165,7 +165,7 @@ __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx
     for (int e = threadIdx.x; e < TX * TY; e += blockDim.x) {
       const int tx = e % TX, ty = e / TX;
       const int gx = bx * TX + tx, gy = by * TY + ty;
-      if (gx < n && gy < n) L.f[(int64_t)gy * n + gx] = fs[(ty + KH) * SX + tx + KH];
+      if (gx < n && gy < n) store_f(L.f, (int64_t)gy * n + gx, fs[(ty + KH) * SX + tx + KH], L.f_bf16);
     }
   }
   if (UP_FIRST) {
@@ -280,7 +280,7 @@ __device__ __forceinline__ void mg2d_tile(const Fine2DParams<T>& P, const int bx
       const int64_t ci = (int64_t)gcy * C.n + gcx;
       const int b = (KH + 2 * cy) * SX + KH + 2 * cx;
       const T acc = (fs[b] + fs[b + 1]) + (fs[b + SX] + fs[b + SX + 1]);
-      C.f[ci] = C.aux[ci] == -2 ? (T)0 : store_residual(acc * (T)0.25, C.f_bf16);
+      store_f(C.f, ci, C.aux[ci] == -2 ? (T)0 : acc * (T)0.25, C.f_bf16);
     }
   }
   for (int e = threadIdx.x; e < TX * TY; e += blockDim.x) {
@@ -405,7 +405,7 @@ __device__ __forceinline__ void vcycle_tail_body(const TailParams<T>& P, const d
     const T vs = v_in ? (T)(vscale ? *vscale : 1.0) : (T)1;
     for (int i = tid; i < L.N; i += nt) {
       T f = 0;
-      if (L.aux[i] != -2) f = v_in ? (T)v_in[i] * (vs * (P.phase[i] ? P.inv_bp : P.inv_bm)) : L.f[i];
+      if (L.aux[i] != -2) f = v_in ? (T)v_in[i] * (vs * (P.phase[i] ? P.inv_bp : P.inv_bm)) : load_f(L.f, i, L.f_bf16);
       sf[i] = f;
     }
   }

@@ -10,6 +10,7 @@
 #include <utility>
 
 #include "engine.cuh"
+#include "mg_rb.cuh"
 
 namespace iim {
 
@@ -61,7 +62,7 @@ __device__ inline T diag_of(const LevelView<T>& L, T dreg, int a) {
 
 template <typename T>
 __device__ __forceinline__ void smooth_body(const LevelView<T>& L, T ih2, T dreg, T* __restrict__ u,
-                                            const T* __restrict__ f, int colour, int64_t t) {
+                                            const T* __restrict__ f, int f_bf16, int colour, int64_t t) {
   // one thread per node of the colour: node = 2 * t + parity fix-up along x
   const GridView& g = L.g;
   int64_t rows = g.N / g.n;
@@ -78,23 +79,23 @@ __device__ __forceinline__ void smooth_body(const LevelView<T>& L, T ih2, T dreg
   int m[3] = {xi, ry, rz};
   T dg = diag_of(L, dreg, a);
   T s = offdiag_sum(L, ih2, i, m, a, u);
-  u[i] = dg != (T)0 ? (f[i] - s) / dg : (T)0;
+  u[i] = dg != (T)0 ? (load_f(f, i, f_bf16) - s) / dg : (T)0;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_smooth(LevelView<T> L, T ih2, T dreg, T* __restrict__ u,
-                                                const T* __restrict__ f, int colour) {
-  smooth_body<T>(L, ih2, dreg, u, f, colour, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+                                                const T* __restrict__ f, int f_bf16, int colour) {
+  smooth_body<T>(L, ih2, dreg, u, f, f_bf16, colour, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // coarse f = mean over the 2^d children of r = f - L u (zero at non-unknowns)
 template <typename T>
 __device__ __forceinline__ void resid_restrict_body(const LevelView<T>& F, T ih2, T dreg, const T* __restrict__ u,
-                                                    const T* __restrict__ f, const GridView& gc,
+                                                    const T* __restrict__ f, int f_in_bf16, const GridView& gc,
                                                     const int32_t* __restrict__ aux_c, T* __restrict__ fc, int64_t I,
                                                     int f_bf16) {
   if (I >= gc.N) return;
-  if (aux_c[I] == -2) { fc[I] = (T)0; return; }
+  if (aux_c[I] == -2) { store_f(fc, I, (T)0, f_bf16); return; }
   int mc[3];
   idx3(gc, I, mc);
   const GridView& g = F.g;
@@ -105,18 +106,19 @@ __device__ __forceinline__ void resid_restrict_body(const LevelView<T>& F, T ih2
     int64_t i = m[0] + (int64_t)g.n * m[1] + (int64_t)g.n * g.n * m[2];
     int a = F.aux[i];
     if (a == -2) continue;
-    T r = f[i] - (diag_of(F, dreg, a) * u[i] + offdiag_sum(F, ih2, i, m, a, u));
+    T r = load_f(f, i, f_in_bf16) - (diag_of(F, dreg, a) * u[i] + offdiag_sum(F, ih2, i, m, a, u));
     acc += r;
   }
-  fc[I] = store_residual(acc / (T)nch, f_bf16);
+  store_f(fc, I, acc / (T)nch, f_bf16);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_resid_restrict(LevelView<T> F, T ih2, T dreg, const T* __restrict__ u,
-                                                        const T* __restrict__ f, GridView gc,
+                                                        const T* __restrict__ f, int f_in_bf16, GridView gc,
                                                         const int32_t* __restrict__ aux_c, T* __restrict__ fc,
                                                         int f_bf16) {
-  resid_restrict_body<T>(F, ih2, dreg, u, f, gc, aux_c, fc, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, f_bf16);
+  resid_restrict_body<T>(F, ih2, dreg, u, f, f_in_bf16, gc, aux_c, fc, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                         f_bf16);
 }
 
 // u_fine += P e_coarse at fine unknowns
@@ -376,24 +378,6 @@ __global__ void k_coarse_lu(T* __restrict__ Ag, int nu, int32_t* __restrict__ pi
   }
 }
 
-// u_c = A^-1 f_c on the coarsest level (one CTA)
-template <typename T>
-__global__ void k_coarse_solve(int nu, const int32_t* __restrict__ map, const T* __restrict__ inv,
-                               const T* __restrict__ f, T* __restrict__ u, int64_t Nc) {
-  extern __shared__ unsigned char smraw[];
-  T* fb = (T*)smraw;
-  for (int64_t i = threadIdx.x; i < Nc; i += blockDim.x) u[i] = (T)0;
-  for (int r = threadIdx.x; r < nu; r += blockDim.x) fb[r] = f[map[r]];
-  __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x / 32;
-  for (int r = wid; r < nu; r += nw) {
-    T s = 0;
-    for (int c = lane; c < nu; c += 32) s += inv[(size_t)r * nu + c] * fb[c];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) u[map[r]] = s;
-  }
-}
-
 // ---------------------------------------------------------------------------- host side
 template <typename T>
 static LevelView<T> view(const Level& L) {
@@ -508,10 +492,66 @@ static void launch_fine2d(Problem& P, size_t l, int mode, const double* v, const
   }
 }
 
+// The red-black tile kernels (mg_rb.cuh) for the first visit's down (MODE 5) and up
+// (MODE 6) steps of levels with at least kRbMinN cells per axis: NW warps of RW rows each.
+constexpr int kRbMinN = 64;
+
+template <typename T, int NW, int RW>
+static void launch_rb(Problem& P, size_t l, int mode, const double* v, const double* vscale, double* z,
+                      const T* u_in, T* u_out, const T* uc, cudaStream_t s) {
+  const Level& L = P.lv[l];
+  const Level& C = P.lv[l + 1];
+  const LevelK<T> K = levk<T>(L);
+  Rb2DParams<T> rp;
+  rp.n = L.g.n;
+  rp.nc = C.g.n;
+  rp.ih2 = K.ih2;
+  rp.inv_dreg = K.inv_dreg;
+  rp.dreg = K.dreg;
+  rp.cls = L.cls;
+  rp.aux = L.aux;
+  rp.tab = K.tab;
+  rp.f_in = (const T*)L.f;
+  rp.f_bf16 = L.f_bf16;
+  rp.f_out = (T*)L.f;
+  rp.v = mode == 5 ? v : nullptr;
+  rp.vscale = vscale;
+  rp.inv_bp = (T)(1.0 / P.desc.beta_plus);
+  rp.inv_bm = (T)(1.0 / P.desc.beta_minus);
+  rp.u_in = u_in;
+  rp.u_out = u_out;
+  rp.z = mode == 6 ? z : nullptr;
+  rp.uc = uc;
+  rp.cls_c = C.cls;
+  rp.fc = (T*)C.f;
+  rp.fc_bf16 = C.f_bf16;
+  rp.neumann = P.desc.bc == IIM_BC_NEUMANN;
+  constexpr int SY = NW * RW, TY = SY - 2 * kRbHalo;
+  const dim3 grid(ceil_div(L.g.n, kRbTX), ceil_div(L.g.n, TY));
+  if (mode == 5) {
+    constexpr size_t sm = rb_smem_bytes<T, SY, false>();
+    if (sm > 48 * 1024) smem_optin((const void*)k_mg2d_rb<T, NW, RW, false>);
+    IIM_LAUNCH((k_mg2d_rb<T, NW, RW, false>), grid, NW * 32, sm, s, rp);
+  } else {
+    constexpr size_t sm = rb_smem_bytes<T, SY, true>();
+    if (sm > 48 * 1024) smem_optin((const void*)k_mg2d_rb<T, NW, RW, true>);
+    IIM_LAUNCH((k_mg2d_rb<T, NW, RW, true>), grid, NW * 32, sm, s, rp);
+  }
+}
+
 template <typename T>
 static void fine2d(Problem& P, size_t l, int mode, const double* v, const double* vscale, double* z, const T* u_in,
                    T* u_out, const T* uc, cudaStream_t s) {
-  if (P.lv[l].g.n >= 512) launch_fine2d<T, 64, 16>(P, l, mode, v, vscale, z, u_in, u_out, uc, s);
+  const int n = P.lv[l].g.n;
+  if ((mode == 5 || mode == 6) && n >= kRbMinN) {
+    // window heights measured best on GB300 (V-cycles of the 1024^2 and 2048^2 star problems):
+    // 64 rows (512 threads) from 2048, 32 rows (512 threads) from 512, 16 rows (256 threads) below
+    if (n >= 2048) launch_rb<T, 16, 4>(P, l, mode, v, vscale, z, u_in, u_out, uc, s);
+    else if (n >= 512) launch_rb<T, 16, 2>(P, l, mode, v, vscale, z, u_in, u_out, uc, s);
+    else launch_rb<T, 8, 2>(P, l, mode, v, vscale, z, u_in, u_out, uc, s);
+    return;
+  }
+  if (n >= 512) launch_fine2d<T, 64, 16>(P, l, mode, v, vscale, z, u_in, u_out, uc, s);
   else launch_fine2d<T, 32, 8>(P, l, mode, v, vscale, z, u_in, u_out, uc, s);
 }
 
@@ -580,17 +620,19 @@ static void vcycle(Problem& P, size_t l, size_t lt, cudaStream_t s, bool from_ze
   const int64_t ncol = (L.g.N / L.g.n) * ((L.g.n + 1) / 2);
   if (from_zero) IIM_LAUNCH(k_zero<T>, ceil_div(L.g.N, Tn), Tn, 0, s, u, L.g.N);
   for (int it = 0; it < P.opt.nu1; ++it)
-    for (int c = 0; c < 2; ++c) IIM_LAUNCH(k_smooth<T>, ceil_div(ncol, Tn), Tn, 0, s, V, K.ih2, K.dreg, u, f, c);
+    for (int c = 0; c < 2; ++c)
+      IIM_LAUNCH(k_smooth<T>, ceil_div(ncol, Tn), Tn, 0, s, V, K.ih2, K.dreg, u, f, L.f_bf16, c);
   Level& C = P.lv[l + 1];
-  IIM_LAUNCH(k_resid_restrict<T>, ceil_div(C.g.N, Tn), Tn, 0, s, V, K.ih2, K.dreg, u, f, C.g, C.aux, (T*)C.f,
-             C.f_bf16);
+  IIM_LAUNCH(k_resid_restrict<T>, ceil_div(C.g.N, Tn), Tn, 0, s, V, K.ih2, K.dreg, u, f, L.f_bf16, C.g, C.aux,
+             (T*)C.f, C.f_bf16);
   if (l + 1 == lt) vcycle<T>(P, l + 1, lt, s);
   else
     for (int g = 0; g < P.opt.cycle; ++g) vcycle<T>(P, l + 1, lt, s, g == 0);
   IIM_LAUNCH(k_prolong<T>, ceil_div(L.g.N, Tn), Tn, 0, s, L.g, L.aux, u, C.g, C.aux, (const T*)C.u,
              P.desc.bc == IIM_BC_NEUMANN);
   for (int it = 0; it < P.opt.nu2; ++it)
-    for (int c = 0; c < 2; ++c) IIM_LAUNCH(k_smooth<T>, ceil_div(ncol, Tn), Tn, 0, s, V, K.ih2, K.dreg, u, f, c);
+    for (int c = 0; c < 2; ++c)
+      IIM_LAUNCH(k_smooth<T>, ceil_div(ncol, Tn), Tn, 0, s, V, K.ih2, K.dreg, u, f, L.f_bf16, c);
 }
 
 template <typename T>
@@ -618,7 +660,7 @@ static void smooth_fine_t(Problem& P, int colour, cudaStream_t s) {
   LevelView<T> V = view<T>(L);
   LevelK<T> K = levk<T>(L);
   const int64_t ncol = (L.g.N / L.g.n) * ((L.g.n + 1) / 2);
-  IIM_LAUNCH(k_smooth<T>, ceil_div(ncol, 256), 256, 0, s, V, K.ih2, K.dreg, (T*)L.u, (const T*)L.f, colour);
+  IIM_LAUNCH(k_smooth<T>, ceil_div(ncol, 256), 256, 0, s, V, K.ih2, K.dreg, (T*)L.u, (const T*)L.f, L.f_bf16, colour);
 }
 
 // one red or black half sweep on the finest level (kernel timing)
@@ -764,10 +806,11 @@ __global__ void __launch_bounds__(256) k_eng_mg3d(EngArgs A, int list, int d, in
     } else if (KIND == 1) {
       if (i < K.N) K.u[i] = 0.f;
     } else if (KIND == 2) {
-      smooth_body<float>(V, K.ih2, K.dreg, K.u, K.f, colour, i);
+      smooth_body<float>(V, K.ih2, K.dreg, K.u, K.f, K.f_bf16, colour, i);
     } else if (KIND == 3) {
       const LevelView<float> C = eng_view(s, d + 1);
-      resid_restrict_body<float>(V, K.ih2, K.dreg, K.u, K.f, C.g, C.aux, s.lev[d + 1].f, i, s.lev[d + 1].f_bf16);
+      resid_restrict_body<float>(V, K.ih2, K.dreg, K.u, K.f, K.f_bf16, C.g, C.aux, s.lev[d + 1].f, i,
+                                 s.lev[d + 1].f_bf16);
     } else if (KIND == 4) {
       const LevelView<float> C = eng_view(s, d + 1);
       prolong_body<float>(V.g, K.aux, K.u, C.g, C.aux, s.lev[d + 1].u, s.neumann, i);

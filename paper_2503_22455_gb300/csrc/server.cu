@@ -47,6 +47,7 @@ enum ReqState { kQueued = 0, kCreating, kNeedData, kReady, kRunning, kRetired, k
 struct Request {
   int64_t id = 0;
   iim_problem_desc desc;
+  std::vector<double> geom_coef;  // the request's own copy of a Fourier curve's coefficients
   double t_submit = 0, t_done = 0;
   int state = kQueued;
   iim_problem* prob = nullptr;
@@ -207,9 +208,26 @@ iim_status iim_server_submit(iim_server* H, const iim_problem_desc* desc, int64_
     set_error("server: the request alone exceeds the memory budget");
     return IIM_ERR_BUDGET;
   }
+  if (desc->geom_kind == IIM_GEOM_LEVELSET_GRID) {
+    set_error("server: requests take analytic bodies or Fourier curves, not level sets on a grid");
+    return IIM_ERR_INVALID_ARG;
+  }
+  if (desc->geom_kind == IIM_GEOM_FOURIER &&
+      (!desc->geom_coef || desc->n_geom_coef < 3 || desc->n_geom_coef > 2 * IIM_MAX_FOURIER_MODES + 1)) {
+    set_error("server: a Fourier curve needs 2 K + 1 coefficients, 1 <= K <= 16");
+    return IIM_ERR_INVALID_ARG;
+  }
   Request* r = new Request();
   r->id = S.next_id++;
   r->desc = *desc;
+  if (desc->geom_kind == IIM_GEOM_FOURIER) {
+    r->geom_coef.assign(desc->geom_coef, desc->geom_coef + desc->n_geom_coef);
+    r->desc.geom_coef = r->geom_coef.data();
+  } else {
+    r->desc.geom_coef = nullptr;
+    r->desc.n_geom_coef = 0;
+  }
+  r->desc.phi_dev = nullptr;
   r->t_submit = S.now();
   std::memset(&r->info, 0, sizeof(r->info));
   S.reqs[r->id] = r;

@@ -1086,11 +1086,12 @@ __device__ inline void sw_side(const SWParams& P, const uint8_t* phase, int64_t 
 }
 
 __global__ void k_sw_classify(SWParams P, const uint8_t* __restrict__ phase, int32_t* __restrict__ aux,
-                              int32_t* __restrict__ flag, int* status) {
+                              uint8_t* __restrict__ cls, int32_t* __restrict__ flag, int* status) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const GridView& g = P.g;
   if (i >= g.N) return;
   int f = 0;
+  uint8_t c = phase[i] ? 4 : 0;        // phase +
   if (!(P.interface_ || phase[i])) {
     aux[i] = -2;
   } else {
@@ -1102,7 +1103,9 @@ __global__ void k_sw_classify(SWParams P, const uint8_t* __restrict__ phase, int
         if (pos < 0 || pos >= g.n || phase[i + s * stride_of(g, ax)] != phase[i]) f = 1;
       }
     aux[i] = -1;
+    c |= f ? 3 : 1;                    // unknown, and irregular: its row is filled by k_sw_fill
   }
+  cls[i] = c;
   flag[i] = f;
 }
 
@@ -1160,21 +1163,53 @@ __global__ void k_sw_fill(SWParams P, const uint8_t* __restrict__ phase, const i
   aux[i] = r;
 }
 
+// outer-box sample points: face f = 2 ax + (side > 0), then the other node indices of the
+// face in flat order (lowest remaining axis fastest); the point sits on the face
+__global__ void k_box_points(GridView g, double* __restrict__ xb) {
+  const int64_t per_face = g.N / g.n;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 2 * g.dim * per_face) return;
+  const int f = (int)(e / per_face), ax = f / 2;
+  int64_t r = e - (int64_t)f * per_face;
+  for (int k = 0; k < g.dim; ++k) {
+    double v;
+    if (k == ax) {
+      v = (f & 1) ? 1.0 : -1.0;
+    } else {
+      const int m = (int)(r % g.n);
+      r /= g.n;
+      v = node_x(g, m);
+    }
+    xb[e * g.dim + k] = v;
+  }
+}
+
+void box_points(Problem& P, double* xb, cudaStream_t s) {
+  const int64_t B = 2 * P.g.dim * (P.g.N / P.g.n);
+  IIM_LAUNCH(k_box_points, ceil_div(B, 256), 256, 0, s, P.g, xb);
+}
+
 // ------------------------------------------------------------------------------ host drivers
-static Geom make_geom(const iim_problem_desc& d) {
-  Geom G;
+static Geom make_geom(const Problem& P) {
+  const iim_problem_desc& d = P.desc;
+  Geom G = {};
   G.kind = d.geom_kind;
   G.dim = d.dim;
   G.sign = d.plus_inside ? -1.0 : 1.0;
   for (int k = 0; k < 8; ++k) G.p[k] = d.geom_params[k];
   G.cs = std::cos(d.geom_params[4]);    // used by the ellipse only
   G.sn = std::sin(d.geom_params[4]);
+  G.modes = (int)P.geom_coef.size() / 2;
+  for (size_t k = 0; k < P.geom_coef.size() && k < 2 * kMaxFourierModes + 1; ++k) G.fc[k] = P.geom_coef[k];
+  G.phi = P.phi_grid;
+  G.gn = P.g.n;
+  G.gh = P.g.h;
   return G;
 }
 
 iim_status setup_geometry(Problem& P, bool size_only) {
   cudaStream_t s = P.stream;
-  P.geom = make_geom(P.desc);
+  P.geom = make_geom(P);
   const GridView& g = P.g;
   const int T = 256;
   IIM_LAUNCH(k_phase, ceil_div(g.N, T), T, 0, s, P.geom, g, P.phase);
@@ -1287,7 +1322,7 @@ iim_status setup_levels(Problem& P, bool size_only) {
       S.cr_cap = P.K_cap;
     }
     if (l > 0) IIM_LAUNCH(k_phase, ceil_div(L.g.N, T), T, 0, P.stream, P.geom, L.g, L.phase);
-    IIM_LAUNCH(k_sw_classify, ceil_div(L.g.N, T), T, 0, P.stream, S, L.phase, L.aux, L.flag, P.d_status);
+    IIM_LAUNCH(k_sw_classify, ceil_div(L.g.N, T), T, 0, P.stream, S, L.phase, L.aux, L.cls, L.flag, P.d_status);
     scan_exclusive(L.flag, L.idx, L.g.N, P.d_counts + 2 + (int)l, P.scan_scratch, P.stream);
     if (size_only) continue;
     IIM_LAUNCH(k_compact, ceil_div(L.g.N, T), T, 0, P.stream, L.flag, L.idx, L.g.N, L.irr_cap, L.irr_node,

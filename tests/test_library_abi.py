@@ -81,13 +81,15 @@ def test_binding_constants_match_the_header():
     import workloads as W
     e = _header_enums()
     for key, name in (("circle", "CIRCLE"), ("ellipse", "ELLIPSE"), ("star", "STAR"), ("sphere", "SPHERE"),
-                      ("ellipsoid", "ELLIPSOID"), ("perturbed_sphere", "PERTURBED_SPHERE")):
+                      ("ellipsoid", "ELLIPSOID"), ("perturbed_sphere", "PERTURBED_SPHERE"), ("fourier", "FOURIER"),
+                      ("levelset_grid", "LEVELSET_GRID")):
         assert iim.GEOM[key] == e["IIM_GEOM_" + name] == getattr(W, name), key
     for key in ("dirichlet", "neumann", "interface"):
         assert iim.BC[key] == e["IIM_BC_" + key.upper()] == getattr(W, key.upper())
     assert (W.BOX_NONE, W.BOX_DIRICHLET) == (e["IIM_BOX_NONE"], e["IIM_BOX_DIRICHLET"])
     assert (iim.MG_FP32, iim.MG_FP64, iim.MG_FP32_BF16R) == (e["IIM_MG_FP32"], e["IIM_MG_FP64"], e["IIM_MG_FP32_BF16R"])
     assert (iim.CYCLE_V, iim.CYCLE_W) == (e["IIM_CYCLE_V"], e["IIM_CYCLE_W"])
+    assert iim.MAX_FOURIER_MODES == e["IIM_MAX_FOURIER_MODES"]
     assert (iim.KRYLOV_FGMRES, iim.KRYLOV_GMRES_LEFT) == (e["IIM_KRYLOV_FGMRES"], e["IIM_KRYLOV_GMRES_LEFT"])
     status = {k: v for k, v in e.items() if k.startswith("IIM_ERR_") or k == "IIM_OK"}
     assert len(status) == len(iim.STATUS_NAMES)
@@ -116,3 +118,55 @@ def test_invalid_options_are_rejected_without_touching_the_device(lib_path, fiel
     h = ctypes.c_void_p()
     st = lib.iim_problem_create(ctypes.byref(d), ctypes.byref(o), None, ctypes.byref(h))
     assert st == 1 and not h.value, (field, value, st)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """sizeof and every field offset of the descriptor, options and solve-info structs, as the
+    C compiler lays them out from include/iim.h, equal the binding's ctypes structs."""
+    import shutil
+    import subprocess
+    import paper_2503_22455_gb300 as iim
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"iim_problem_desc": iim.Desc, "iim_options": iim.Options, "iim_solve_info": iim.SolveInfo}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "iim.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+
+
+@pytest.mark.parametrize("case", ["even_count", "too_many_modes", "no_coef", "negative_radius", "grid_no_phi",
+                                  "fourier_3d"])
+def test_invalid_geometry_input_is_rejected_without_touching_the_device(lib_path, case):
+    import paper_2503_22455_gb300 as iim
+    lib = iim.load(lib_path)
+    kind, dim, coef = iim.GEOM["fourier"], 2, [0.5, 0.01, 0.02]
+    if case == "even_count":
+        coef = [0.5, 0.01]
+    elif case == "too_many_modes":
+        coef = [0.5] + [0.001] * (2 * iim.MAX_FOURIER_MODES + 2)
+    elif case == "no_coef":
+        coef = None
+    elif case == "negative_radius":
+        coef = [0.1, 0.2, 0.0]
+    elif case == "grid_no_phi":
+        kind, coef = iim.GEOM["levelset_grid"], None
+    elif case == "fourier_3d":
+        dim = 3
+    d = iim.make_desc(dim, 64, kind, (0.0, 0.0), False, iim.BC["dirichlet"], 0, order=4, coef=coef)
+    h = ctypes.c_void_p()
+    st = lib.iim_problem_create(ctypes.byref(d), ctypes.byref(iim.default_options()), None, ctypes.byref(h))
+    assert st == iim.IIM_ERR_INVALID_ARG and not h.value, (case, st)

@@ -19,6 +19,7 @@ import numpy as np
 
 # geometry kinds (same integer codes as the C header)
 CIRCLE, ELLIPSE, STAR, SPHERE, ELLIPSOID, PERTURBED_SPHERE = 0, 1, 2, 3, 4, 5
+FOURIER, LEVELSET_GRID = 6, 7
 # the perturbation of PERTURBED_SPHERE: the real spherical harmonic of degree 3, order 2,
 # (e_x^2 - e_y^2) e_z for the unit direction e, scaled to a maximum of 1 on the sphere
 PERTURB_SCALE = 1.5 * math.sqrt(3.0)
@@ -40,13 +41,21 @@ class Geometry:
       ELLIPSOID (cx, cy, cz, a0, a1, a2)         axis-aligned
       PERTURBED_SPHERE (cx, cy, cz, rho0, rho1)  r(e) = rho0 + rho1 Y(e), Y the degree-3
                                                  harmonic above (max |Y| = 1)
+      FOURIER   (cx, cy)                         r(theta) = a0 + sum_k a_k cos k theta + b_k sin k theta,
+                                                 ``coef`` = (a0, a1, b1, ..., aK, bK)
+      LEVELSET_GRID ()                           ``values``: the level set at the grid's nodes,
+                                                 shape (n,)*d indexed [i0, i1, (i2)]
     """
     kind: int
     params: tuple
     plus_inside: bool
+    coef: tuple = ()
+    values: object = None
 
     @property
     def dim(self) -> int:
+        if self.kind == LEVELSET_GRID:
+            return int(np.asarray(self.values).ndim)
         return 3 if self.kind in (SPHERE, ELLIPSOID, PERTURBED_SPHERE) else 2
 
 
@@ -325,6 +334,53 @@ def box_data(spec: ProblemSpec) -> np.ndarray:
     if spec.box_bc != BOX_DIRICHLET:
         return np.zeros(0)
     return spec.solution.u_plus(box_face_points(spec.n, spec.dim))
+
+
+# ----------------------------------------------------------------------------
+# level sets given at the grid's nodes (input for LEVELSET_GRID)
+# ----------------------------------------------------------------------------
+def sampled_levelset(fn, n: int, dim: int, plus_inside: bool = False) -> Geometry:
+    """A LEVELSET_GRID geometry from a field ``fn(X)`` evaluated at the nodes of an n^dim grid."""
+    return Geometry(LEVELSET_GRID, (), plus_inside, values=np.asarray(fn(node_coords(n, dim)), dtype=float))
+
+
+def quadric_field(center, axes, angle=0.0):
+    """phi = 1 - sum_k (y_k / a_k)^2, y = Rot(-angle)(x - center) (2D) or y = x - center (3D):
+    positive inside the ellipse (ellipsoid), a polynomial of degree 2."""
+    c = np.asarray(center, dtype=float)
+    a = np.asarray(axes, dtype=float)
+
+    def fn(X):
+        d = X - c
+        if c.size == 2:
+            cs, sn = math.cos(angle), math.sin(angle)
+            y0 = cs * d[..., 0] + sn * d[..., 1]
+            y1 = -sn * d[..., 0] + cs * d[..., 1]
+            return 1.0 - (y0 / a[0]) ** 2 - (y1 / a[1]) ** 2
+        return 1.0 - np.sum((d / a) ** 2, axis=-1)
+    return fn
+
+
+def star_field(cx, cy, r0, amp, m, phase):
+    """phi = r0 + amp sin(m theta + phase) - |x - c|: positive inside the star curve."""
+    def fn(X):
+        dx, dy = X[..., 0] - cx, X[..., 1] - cy
+        return r0 + amp * np.sin(m * np.arctan2(dy, dx) + phase) - np.hypot(dx, dy)
+    return fn
+
+
+def blob_field(center, radius, eps, k):
+    """A smooth body with no closed form here: phi = R^2 - |x - c|^2 + eps prod_i sin(k x_i + i),
+    positive inside (2D or 3D)."""
+    c = np.asarray(center, dtype=float)
+
+    def fn(X):
+        d = X - c
+        w = np.ones(X.shape[:-1])
+        for i in range(c.size):
+            w = w * np.sin(k * X[..., i] + i)
+        return radius ** 2 - np.sum(d * d, axis=-1) + eps * w
+    return fn
 
 
 # ----------------------------------------------------------------------------
