@@ -344,21 +344,17 @@ def run_batch(args):
         e.close()
 
 
-def run_serve(args):
-    """Poisson request stream (mean rate 200/s, 2000 requests, seed 22455): 2D n 128..1024
-    (stars), 3D n 64..192 (ellipsoids), interior Dirichlet / exterior Neumann, admitted by
-    a budget of 60% of free device memory into the request loop; p50/p99 latency from
-    submission to the solution on the host, and completed solves per second."""
+def serve_run(iim, torch, count, rate, seed, slots=256, ticks_per_run=4, mode=1, create_threads=16,
+              deadline_s=300.0, note=None):
+    """A Poisson request stream (mean rate ``rate``/s, ``count`` requests, seeded): 2D n
+    128..1024 (stars, ellipses), 3D n 64..192 (ellipsoids, perturbed spheres), interior
+    Dirichlet / exterior Neumann, admitted by a budget of 60% of free device memory into
+    the request loop; p50/p99 latency from submission to the solution on the host, and
+    completed solves per second."""
     import numpy as np
-    import torch
 
-    import paper_2503_22455_gb300 as iim
     import workloads as W
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    _load_lib(iim)
-    count = args.count or 2000
-    trace = W.serving_trace(count=count, rate=args.rate, seed=22455 + rank)
+    trace = W.serving_trace(count=count, rate=rate, seed=seed)
     opts = iim.default_options(tol=1e-10, mg_precision=iim.MG_FP32)
     free, total = torch.cuda.mem_get_info()
     budget = int(0.6 * free)
@@ -368,48 +364,147 @@ def run_serve(args):
         view.set_data(f, g, None, None, box)
 
     # warm-up: a few requests through a separate server (library, kernels, allocator)
-    warm = iim.Server(opts, budget_bytes=budget, max_slots=args.slots, ticks_per_run=args.ticks_per_run,
-                      mode=args.serve_mode, create_threads=args.create_threads)
+    warm = iim.Server(opts, budget_bytes=budget, max_slots=slots, ticks_per_run=ticks_per_run, mode=mode,
+                      create_threads=create_threads)
+    iim.serve(warm, [(0.0, iim.desc_from_spec(sp), sp) for _, sp in trace[:8]], set_data, realtime=False,
+              deadline_s=deadline_s, progress=note)
+    warm.close()
+    S = iim.Server(opts, budget_bytes=budget, max_slots=slots, ticks_per_run=ticks_per_run, mode=mode,
+                   create_threads=create_threads)
+    arrivals = [(t, iim.desc_from_spec(sp), sp) for t, sp in trace]
+    host = {}
+    out, wall = iim.serve(S, arrivals, set_data, realtime=True, timings=host, deadline_s=deadline_s, progress=note)
+    stats = S.stats()
+    S.close()
+    lat = np.array([o[2] for o in out.values()])
+    ok = [o for o in out.values() if o[3] == 0 and o[1].converged]
+    err = [(o[4].name, o[4].n, o[4].dim, int(o[3]), o[1].iters, o[1].relres) for o in out.values() if o[3] != 0]
+    return {
+        "solves_per_s": len(ok) / wall, "p50_latency_s": float(np.percentile(lat, 50)),
+        "p99_latency_s": float(np.percentile(lat, 99)), "mean_latency_s": float(lat.mean()), "wall_s": wall,
+        "requests": count, "rate_per_s": rate, "seed": seed, "offered_rate": count / trace[-1][0],
+        "completed": len(ok), "failed": len(err), "failures": err[:10], "budget_bytes": budget,
+        "peak_bytes": stats["peak_bytes"], "solver": "batched engine" if mode == 0 else
+        "per-request solve graphs on streams", "create_threads": create_threads,
+        "host_seconds": {"loop_step": host["step_s"], "client_set_data": host["set_data_s"], "take": host["take_s"],
+                         "server_copy_out": stats["host_copy_s"], "server_create_threads": stats["host_create_s"]},
+        "requests_2d": sum(1 for _, sp in trace if sp.dim == 2), "requests_3d": sum(1 for _, sp in trace if sp.dim == 3),
+    }
+
+
+def run_serve(args):
+    """The serving stream line on its own (2000 requests at 200/s by default)."""
+    import torch
+
+    import paper_2503_22455_gb300 as iim
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    _load_lib(iim)
+    count = args.count or 2000
+
     def note(t, taken, outstanding, st):
         print(f"serve: {t:.0f} s, {taken} taken, {outstanding} outstanding, states {st['states']}",
               file=sys.stderr, flush=True)
 
-    iim.serve(warm, [(0.0, iim.desc_from_spec(sp), sp) for _, sp in trace[:8]], set_data, realtime=False,
-              deadline_s=args.serve_deadline, progress=note)
-    warm.close()
-    S = iim.Server(opts, budget_bytes=budget, max_slots=args.slots, ticks_per_run=args.ticks_per_run,
-                   mode=args.serve_mode, create_threads=args.create_threads)
     clocks = Clocks(local)
     clocks.start()
-    arrivals = [(t, iim.desc_from_spec(sp), sp) for t, sp in trace]
-    host = {}
-    out, wall = iim.serve(S, arrivals, set_data, realtime=True, timings=host, deadline_s=args.serve_deadline,
-                          progress=note)
+    r = serve_run(iim, torch, count, args.rate, 22455 + rank, slots=args.slots, ticks_per_run=args.ticks_per_run,
+                  mode=args.serve_mode, create_threads=args.create_threads, deadline_s=args.serve_deadline, note=note)
     clk = clocks.stop()
-    stats = S.stats()
-    lat = np.array([o[2] for o in out.values()])
-    ok = [o for o in out.values() if o[3] == 0 and o[1].converged]
-    err = [(o[4].name, o[4].n, o[4].dim, int(o[3]), o[1].iters, o[1].relres) for o in out.values() if o[3] != 0]
     res = {
-        "metric": "IIM serving: solves/s and p50/p99 latency (s), rel. resid 1e-10", "value": len(ok) / wall,
+        "metric": "IIM serving: solves/s and p50/p99 latency (s), rel. resid 1e-10", "value": r["solves_per_s"],
         "unit": "solves/s", "n_gpus": world, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "mg_dtype": "f32", "data": "synthetic",
         "config": {"workload": f"serve_poisson_{count}", "rate_per_s": args.rate, "requests": count,
                    "mix": "75% 2D stars n 128..1024, 25% 3D ellipsoids n 64..192; Dirichlet / Neumann; (4,5)/(6,7) 2D",
-                   "budget_bytes": budget, "slots": args.slots, "ticks_per_run": args.ticks_per_run, "tol": 1e-10,
-                   "solver": "batched engine" if args.serve_mode == 0 else "per-request solve graphs on streams"},
-        "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-        "mean_latency_s": float(lat.mean()), "wall_s": wall, "completed": len(ok), "failed": len(err),
-        "failures": err[:10], "create_threads": args.create_threads,
-        "offered_rate": count / trace[-1][0], "peak_bytes": stats["peak_bytes"], "engine_runs": stats["runs"],
-        "host_seconds": {"loop_step": host["step_s"], "client_set_data": host["set_data_s"], "take": host["take_s"],
-                         "server_copy_out": stats["host_copy_s"], "server_create_threads": stats["host_create_s"]},
-        "requests_2d": sum(1 for _, sp in trace if sp.dim == 2), "requests_3d": sum(1 for _, sp in trace if sp.dim == 3),
+                   "budget_bytes": r["budget_bytes"], "slots": args.slots, "ticks_per_run": args.ticks_per_run,
+                   "tol": 1e-10, "solver": r["solver"]},
+        **{k: v for k, v in r.items() if k not in ("solves_per_s",)},
         "clocks": clk,
     }
     if rank == 0:
         print(json.dumps(res))
-    S.close()
+
+
+def batch_run(iim, torch, count, steps, seed=2503, engines=2):
+    """``count`` mixed 2D problems (50% interior Dirichlet, 50% exterior Neumann with a
+    Dirichlet box, (4,5)/(6,7), ellipses and 5-7 lobe stars, n 64..512) per step: device
+    set-up, data and solve of all of them, through per-problem solve graphs on a pool of
+    streams and through the batched engine.  L2 is flushed before each step."""
+    import workloads as W
+    specs = W.batch_specs(count, seed=seed)
+    main = torch.cuda.current_stream()
+    pool = [torch.cuda.Stream() for _ in range(16)]
+    opts = iim.default_options(tol=1e-10, mg_precision=iim.MG_FP32)
+    probs = [iim.Problem(iim.desc_from_spec(sp), opts, pool[i % len(pool)]) for i, sp in enumerate(specs)]
+    inputs = []
+    for P, sp in zip(probs, specs):
+        with torch.cuda.stream(P.stream):
+            inputs.append(_boundary_inputs(P, sp))
+    torch.cuda.synchronize()
+    xs = [torch.zeros(P.N, dtype=torch.float64, device="cuda") for P in probs]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    eng_streams = [main] + [torch.cuda.Stream() for _ in range(engines - 1)]
+    E = [iim.Engine(opts, max_slots=(count + engines - 1) // engines, stream=st) for st in eng_streams]
+
+    def prepare():
+        start = torch.cuda.Event()
+        start.record(main)
+        for P, (f, g, box) in zip(probs, inputs):
+            P.stream.wait_event(start)
+            with torch.cuda.stream(P.stream):
+                P.setup()
+                P.set_data(f, g, None, None, box)
+        for st in pool:
+            main.wait_stream(st)
+
+    def step_pool():
+        prepare()
+        infos, _ = iim.batch_solve(probs, xs)
+        for st in pool:
+            main.wait_stream(st)
+        return infos
+
+    def step_engine():
+        prepare()
+        ev = torch.cuda.Event()
+        ev.record(main)
+        for st in eng_streams[1:]:
+            st.wait_event(ev)
+        slots = [E[i % engines].admit(P) for i, P in enumerate(probs)]
+        for e in E:
+            e.run()
+        for e in E:
+            e.poll(wait=True)
+        infos = [E[i % engines].release(sl, x) for i, (sl, x) in enumerate(zip(slots, xs))]
+        for st in eng_streams[1:]:
+            main.wait_stream(st)
+        return infos
+
+    res = {}
+    for name, fn in (("stream_pool", step_pool), ("engine", step_engine)):
+        fn()
+        torch.cuda.synchronize()
+        t, iters = [], []
+        for k in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(main)
+            infos = fn()
+            b.record(main)
+            torch.cuda.synchronize()
+            if not all(i.converged for i in infos):
+                raise RuntimeError(f"batch ({name}): a problem did not converge")
+            t.append(a.elapsed_time(b))
+            iters += [i.iters for i in infos]
+        res[name] = {"solves_per_s": count * 1e3 / statistics.mean(t), "ms_per_step": statistics.mean(t),
+                     "iters_mean": statistics.mean(iters), "iters_max": max(iters)}
+    for e in E:
+        e.close()
+    for P in probs:
+        P.close()
+    return {"problems": count, "steps": steps, "seed": seed, **res,
+            "step": "setup+data+solve of every problem, L2 flushed before each step"}
 
 
 def ellipsoid_forms(iim, torch, main, flush, n, steps, warmup):
@@ -703,6 +798,8 @@ def run_ours(args):
     if args.other_configs and world == 1:
         other["circle_dirichlet_64_o4"] = circle64_run(iim, torch, main, flush)
         other["ellipsoid_neumann_256_o4"] = ellipsoid_forms(iim, torch, main, flush, 256, steps=2, warmup=1)
+        other["batch512_mixed_2d"] = batch_run(iim, torch, 512, steps=2)
+        other["serve_poisson_400"] = serve_run(iim, torch, 400, 200.0, 22455, deadline_s=240.0)
     e2e = None
     if not args.no_e2e:
         e2e = e2e_run(probs, torch, inputs, Wm, K, world, main)
@@ -790,9 +887,21 @@ def e2e_run(probs, torch, inputs, Wm, K, world, main):
             "d2h_bytes_per_step": probs[0].N * 8 * len(probs)}
 
 
+def source_sha(rel_path):
+    """First 16 hex digits of the SHA-256 of a source file of the library."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, rel_path), "rb") as f:
+            return hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+
+
 def ncu_traffic():
     """DRAM bytes (read + write) per launch of each profiled kernel, from the ncu captures
-    summarised in profiles/ (lines "traffic_bytes_per_launch: <kernel> <bytes>")."""
+    summarised in profiles/: lines "traffic_bytes_per_launch: <kernel> <bytes> <source file>
+    <sha16>", the last two naming the file that holds the kernel and its hash when captured.
+    A figure whose kernel source has changed since is returned as stale."""
     out = {}
     d = os.path.join(ROOT, "profiles")
     for name in sorted(os.listdir(d)) if os.path.isdir(d) else []:
@@ -800,7 +909,8 @@ def ncu_traffic():
             for line in open(os.path.join(d, name)):
                 if line.startswith("traffic_bytes_per_launch:"):
                     parts = line.split()
-                    out[parts[1]] = float(parts[2])
+                    fresh = len(parts) >= 5 and source_sha(parts[3]) == parts[4]
+                    out[parts[1]] = {"bytes": float(parts[2]), "fresh": fresh, "profile": name}
         except (OSError, ValueError, IndexError):
             continue
     return out
@@ -845,8 +955,13 @@ def roofline(P, iim, torch, stream, applies_per_solve):
         return {"kernel": r["kernel"], "achieved": a, "frac": a / peak, "us_per_launch": r["us"],
                 "flop_per_launch": r["flop"], "us_per_solve": r["us_per_solve"]}
 
+    tr = ncu_traffic().get(top["kernel"])
+    traffic = tr["bytes"] if tr and tr["fresh"] else None
+    traffic_note = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, profiles/" + tr["profile"]
+                    if traffic is not None else
+                    "null: no ncu capture of the kernel's current source" if tr is None or not tr["fresh"] else None)
     return {"kernel": top["kernel"], "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s (FP64)",
-            "frac": achieved / peak, "traffic": ncu_traffic().get(top["kernel"]), "us_per_launch": top["us"],
+            "frac": achieved / peak, "traffic": traffic, "traffic_note": traffic_note, "us_per_launch": top["us"],
             "flop_per_launch": top["flop"],
             "peak_note": "derived FP64 peak: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock (measured 0.598 TFMA/s "
                          "at 1.995 GHz agrees); the measured copy and bf16 peaks do not apply to FP64 work",

@@ -29,10 +29,12 @@
  *
  * Errors
  *   Every call returns an iim_status and never aborts; iim_last_error() gives
- *   a message for the calling thread.  Device-side failures (rank-deficient
- *   fits, NaN in the Krylov recurrence, ...) are recorded in a status word on
- *   the device and reported by the next call that synchronises
- *   (iim_problem_create, iim_solve, iim_status_get, iim_engine_release).
+ *   a message for the calling thread.  Device-side failures are recorded in two
+ *   status words on the device, one for the set-up (rank-deficient fits, the
+ *   curvature bound, ...; cleared by every set-up) and one for the solve (NaN in
+ *   the Krylov recurrence; cleared by every solve), and reported by the next call
+ *   that synchronises (iim_problem_create, iim_solve, iim_status_get,
+ *   iim_engine_release).  A problem stays usable after either kind of failure.
  */
 #ifndef IIM_H
 #define IIM_H
@@ -363,6 +365,18 @@ void iim_server_destroy(iim_server* s);
  * max_slots at once, overlapping on the device.  Results are the same either way
  * and independent of the other requests. */
 iim_status iim_server_set_mode(iim_server* s, int mode);
+
+/* Reuse of retired problems (on by default): a finished request's problem (its allocation,
+ * stream and solve graph) is kept, its bytes still counted against the budget, and a later
+ * request of the same kind (dimension, n, conditions, outer box, order, geometry kind, side,
+ * beta+, beta-; closed-form bodies only) takes it and re-runs its set-up in place with its own
+ * geometry parameters, instead of creating a problem.  Kept problems are freed, oldest first,
+ * when a new request needs their memory, or when reuse is switched off.  Results are those of
+ * a fresh problem (the set-up leaves nothing of the earlier geometry behind). */
+iim_status iim_server_set_pooling(iim_server* s, int on);
+/* Requests that took a kept problem, requests created afresh, kept problems freed for room,
+ * and problems kept now.  Any pointer may be NULL. */
+iim_status iim_server_pool_stats(iim_server* s, int64_t* hits, int64_t* misses, int64_t* evicted, int* pooled);
 
 /* Queue a request; *id identifies it.  IIM_ERR_BUDGET if it alone exceeds the budget. */
 iim_status iim_server_submit(iim_server* s, const iim_problem_desc* desc, int64_t* id);

@@ -60,14 +60,16 @@ class LevelSet:
     def _lagrange(self, x, order):
         """First stencil node s and the weights of the value (order 0), first (1) or second
         (2) derivative along one axis for coordinates x: the derivatives of the Lagrange
-        basis l_k(t) = prod_{j != k} (t - j) / D_k, t = (x - x_s) / h.  A coordinate equal
-        to a node's takes that node's integer t, so that the interpolant returns the given
-        value there."""
+        basis l_k(t) = prod_{j != k} (t - j) / D_k, t = (x - x_s) / h, over the six nodes
+        from two below the point's cell.  A coordinate within 1e-9 h of node m counts as
+        that node: the stencil starts at m - 2 and t is the exact integer m - s, so that the
+        interpolant returns the given value there (the two stencils holding a node agree on
+        its value but not on its derivatives, so the choice must not depend on rounding)."""
         n, h = self.gn, self.gh
         tc = (x + 1.0) / h - 0.5
-        s = np.clip(np.floor(tc).astype(np.int64) - 2, 0, n - 6)
         m = np.floor(tc + 0.5).astype(np.int64)
-        at_node = (m >= s) & (m <= s + 5) & (-1.0 + (m + 0.5) * h == x)
+        at_node = np.abs(tc - m) <= 1e-9
+        s = np.clip(np.where(at_node, m, np.floor(tc).astype(np.int64)) - 2, 0, n - 6)
         t = np.where(at_node, (m - s).astype(float), tc - s)
         d = t[..., None] - np.arange(6.0)
         w = np.zeros(x.shape + (6,))

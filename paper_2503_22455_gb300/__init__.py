@@ -121,6 +121,10 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
+    "iim_server_set_pooling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "iim_server_pool_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                             ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                             ctypes.POINTER(ctypes.c_int)]),
     "iim_last_error": (ctypes.c_char_p, []),
     "iim_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -519,7 +523,7 @@ class Server:
     """Request loop over an engine (see iim.h): submit, step, set data, take."""
 
     def __init__(self, options: Options | None = None, budget_bytes: int = 1 << 34, max_slots: int = 64,
-                 ticks_per_run: int = 4, cap: int = 4096, create_threads: int = 8, mode: int = 0):
+                 ticks_per_run: int = 4, cap: int = 4096, create_threads: int = 8, mode: int = 0, pooling=True):
         lib = load()
         self.options = options or default_options()
         h = ctypes.c_void_p()
@@ -527,6 +531,7 @@ class Server:
                                      int(ticks_per_run), int(create_threads), ctypes.byref(h)), "iim_server_create")
         self.h = h
         _check(lib.iim_server_set_mode(self.h, int(mode)), "iim_server_set_mode")
+        _check(lib.iim_server_set_pooling(self.h, int(bool(pooling))), "iim_server_set_pooling")
         self.mode = mode
         self.cap = cap
         self._need = (ctypes.c_int64 * cap)()
@@ -543,6 +548,12 @@ class Server:
             self.close()
         except Exception:
             pass
+
+    def pool_stats(self):
+        """(requests that reused a kept problem, requests created afresh, kept problems freed, kept now)"""
+        h, m, e, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        _check(load().iim_server_pool_stats(self.h, ctypes.byref(h), ctypes.byref(m), ctypes.byref(e), ctypes.byref(k)))
+        return {"hits": h.value, "misses": m.value, "evicted": e.value, "kept": k.value}
 
     def submit(self, desc: Desc) -> int:
         rid = ctypes.c_int64()

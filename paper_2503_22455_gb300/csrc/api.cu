@@ -451,14 +451,16 @@ iim_status iim_problem_create(const iim_problem_desc* desc, const iim_options* o
     cudaMemcpy(aux.data(), C.aux, sizeof(int32_t) * C.g.N, cudaMemcpyDeviceToHost);
     int nu = 0;
     for (auto a : aux) nu += a != -2;
-    if (nu > 4096) {
-      set_error("the coarsest multigrid level has more than 4096 unknowns: choose n with more factors of 2");
+    if (C.g.N + P.aug > 4096) {
+      set_error("the coarsest multigrid level has more than 4096 nodes: choose n with more factors of 2");
       IIM_FAIL(IIM_ERR_INVALID_ARG);
     }
+    // the dense coarse system holds a slot per node of the coarsest level (+ the augmentation),
+    // so that a later set-up with other geometry needs no other size
     P.coarse_nu = nu;
-    P.coarse_n = nu > 0 ? nu + P.aug : 0;
+    P.coarse_n = (int)C.g.N + P.aug;
     const size_t cn = (size_t)P.coarse_n;
-    IIM_ALLOC(P.coarse_map, int32_t, nu > 0 ? nu : 1);
+    IIM_ALLOC(P.coarse_map, int32_t, cn);
     IIM_ALLOC(P.coarse_piv, int32_t, cn > 0 ? cn : 1);
     IIM_ALLOC(P.coarse_lu64, double, 2 * cn * cn + 1);
     IIM_ALLOC(P.coarse_lu32, float, 2 * cn * cn + 1);
@@ -478,6 +480,8 @@ iim_status iim_problem_create(const iim_problem_desc* desc, const iim_options* o
 }
 
 static iim_status setup_enqueue(Problem& P) {
+  // the set-up status word reports this set-up alone (an earlier failed one is forgotten)
+  cudaMemsetAsync(P.d_status, 0, sizeof(int), P.stream);
   setup_geometry(P, false);
   if (!(P.side && P.ev_fork && P.ev_join)) {
     iim_status st = setup_fits(P);
@@ -503,6 +507,32 @@ static iim_status setup_enqueue(Problem& P) {
 
 // The set-up is a fixed sequence of kernels with no host decision in it, so (with
 // use_graph) it is captured once per geometry and replayed as one graph launch.
+}  // extern "C"
+
+namespace iim {
+// The set-up re-run in place with new geometry parameters, its kernels enqueued directly on the
+// problem's stream (no graph capture; a captured set-up graph of other parameters is dropped).
+// For the request loop's reuse of a retired problem.  Asynchronous.
+iim_status setup_direct(Problem& P, const double* params) {
+  bool changed = false;
+  for (int k = 0; k < 8; ++k) {
+    changed = changed || P.desc.geom_params[k] != params[k];
+    P.desc.geom_params[k] = params[k];
+  }
+  if (changed && P.setup_exec) {
+    cudaGraphExecDestroy(P.setup_exec);
+    cudaGraphDestroy(P.setup_graph);
+    P.setup_exec = nullptr;
+    P.setup_graph = nullptr;
+  }
+  iim_status st = setup_enqueue(P);
+  if (st != IIM_OK) return st;
+  return cuda_check("setup");
+}
+}  // namespace iim
+
+extern "C" {
+
 iim_status iim_problem_set_phi(iim_problem* H, const double* phi_dev) {
   if (!H || !phi_dev) return IIM_ERR_INVALID_ARG;
   Problem& P = H->P;

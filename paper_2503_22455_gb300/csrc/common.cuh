@@ -66,13 +66,16 @@ __host__ __device__ inline void fourier_r(const Geom& G, double th, double* r, d
 // weights of that node alone, so the interpolant takes the given values at the nodes.
 __host__ __device__ inline void lag6(double x, int n, double h, int* s_out, double* w0, double* w1, double* w2) {
   const double tc = (x + 1.0) / h - 0.5;
-  int s = (int)floor(tc) - 2;
+  // A coordinate within 1e-9 h of node m counts as that node: the stencil starts at m - 2
+  // and the local coordinate is the exact integer m - s, so the products below are exact,
+  // the value weights are 1 and 0 and the interpolant returns the given value.  (The two
+  // stencils that contain a node give it the same value but different derivatives, so the
+  // choice must not depend on the last bit of the coordinate.)
+  const int m = (int)floor(tc + 0.5);
+  const bool at_node = fabs(tc - (double)m) <= 1e-9;
+  int s = (at_node ? m : (int)floor(tc)) - 2;
   s = s < 0 ? 0 : (s > n - 6 ? n - 6 : s);
   *s_out = s;
-  // at a node the local coordinate is that node's integer index: the products below are
-  // then exact and the value weights are exactly 1 and 0
-  const int m = (int)floor(tc + 0.5);
-  const bool at_node = m >= s && m <= s + 5 && -1.0 + ((double)m + 0.5) * h == x;
   const double t = at_node ? (double)(m - s) : tc - (double)s;
   const double D[6] = {-120.0, 24.0, -12.0, 12.0, -24.0, 120.0};   // prod_{j != k} (k - j)
   double d[6];

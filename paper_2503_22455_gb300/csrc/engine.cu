@@ -108,7 +108,7 @@ static void fill_slot(Engine& E, int si, Problem& P) {
   sd.neumann = P.desc.bc == IIM_BC_NEUMANN;
   sd.g = P.g;
   sd.phase = P.phase;
-  sd.status = P.d_status;
+  sd.status = P.d_status + 1;           // the per-solve word (set-up failures stay in word 0)
   eng_operator_params(P, &sd.C, &sd.GP, &sd.CP);
   sd.sc = P.sc;
   sd.V = P.V;

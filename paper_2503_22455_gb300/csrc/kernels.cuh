@@ -154,10 +154,10 @@ struct Problem {
   int red_blocks = 0;
   // multigrid
   std::vector<Level> lv;
-  int coarse_nu = 0;              // unknowns on the coarsest level
-  int coarse_n = 0;               // size of the coarse dense system: coarse_nu (+1 when augmented)
+  int coarse_nu = 0;              // unknowns on the coarsest level at creation (information only)
+  int coarse_n = 0;               // size of the padded coarse system: the coarsest level's nodes (+1 when augmented)
   int aug = 0;                    // pure Neumann: the augmented system of Sec. 2.3 (one more unknown)
-  int32_t* coarse_map = nullptr;  // [coarse_nu] node of each coarse unknown
+  int32_t* coarse_map = nullptr;  // [coarse_n] node of each slot of the coarse system, -1 if none
   double* coarse_lu64 = nullptr;  // [nu][nu] LU factors (row major), FP64
   float* coarse_lu32 = nullptr;
   int32_t* coarse_piv = nullptr;
@@ -198,6 +198,7 @@ void ho_stencil(Problem& P, const double* u, double* w, cudaStream_t s);
 void ho_ghost(Problem& P, const double* u, bool with_data, cudaStream_t s);
 void ho_correct(Problem& P, const double* u, double* w, bool with_data, cudaStream_t s);
 void box_points(Problem& P, double* xb, cudaStream_t s);
+iim_status setup_direct(Problem& P, const double* params);
 iim_status ho_apply_noalloc(Problem& P, const double* u, double* w, bool with_data, cudaStream_t s);
 void compute_rhs(Problem& P, const double* f, cudaStream_t s);
 iim_status boundary_values(Problem& P, const double* u, double* out, cudaStream_t s);

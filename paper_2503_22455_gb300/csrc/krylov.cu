@@ -500,7 +500,7 @@ static void enqueue_iteration(Problem& P, int j, cudaStream_t s) {
   }
   orth(P, j, s, 0);
   if (P.opt.reorth) orth(P, j, s, 1);
-  IIM_LAUNCH(k_arnoldi_step, 1, 32, 0, s, P.sc, j, P.d_status);
+  IIM_LAUNCH(k_arnoldi_step, 1, 32, 0, s, P.sc, j, P.d_status + 1);
 }
 
 // left preconditioning: V0 = M (b - L x), measured (first: 0 restart, 3 start)
@@ -511,7 +511,7 @@ static void enqueue_left_residual(Problem& P, cudaStream_t s, int first) {
   IIM_LAUNCH(k_sub, 4 * kNumSMs, 256, 0, s, P.b, P.tmp, r, n);
   krylov_precondition(P, r, nullptr, P.V, s);
   IIM_LAUNCH(k_residual, P.red_blocks, kRedThreads, 0, s, nullptr, nullptr, P.V, n, P.partial, P.counter, P.sc,
-             first, P.d_status);
+             first, P.d_status + 1);
 }
 
 static void enqueue_restart(Problem& P, cudaStream_t s) {
@@ -524,7 +524,7 @@ static void enqueue_restart(Problem& P, cudaStream_t s) {
   IIM_LAUNCH(k_xupdate, 4 * kNumSMs, 256, 0, s, P.x, P.Z, P.Npad, P.g.N + P.aug, P.sc, 0);
   krylov_apply(P, P.x, P.tmp, s);
   IIM_LAUNCH(k_residual, P.red_blocks, kRedThreads, 0, s, P.b, P.tmp, P.V, P.g.N + P.aug, P.partial, P.counter, P.sc,
-             0, P.d_status);
+             0, P.d_status + 1);
 }
 
 static void enqueue_start(Problem& P, cudaStream_t s, int graph_mode) {
@@ -533,13 +533,13 @@ static void enqueue_start(Problem& P, cudaStream_t s, int graph_mode) {
     // |M b| first (the reference of the stopping test), then the preconditioned residual
     krylov_precondition(P, P.b, nullptr, P.V, s);
     IIM_LAUNCH(k_residual, P.red_blocks, kRedThreads, 0, s, nullptr, nullptr, P.V, P.g.N + P.aug, P.partial,
-               P.counter, P.sc, 2, P.d_status);
+               P.counter, P.sc, 2, P.d_status + 1);
     enqueue_left_residual(P, s, 3);
     return;
   }
   krylov_apply(P, P.x, P.tmp, s);
   IIM_LAUNCH(k_residual, P.red_blocks, kRedThreads, 0, s, P.b, P.tmp, P.V, P.g.N + P.aug, P.partial, P.counter, P.sc,
-             1, P.d_status);
+             1, P.d_status + 1);
 }
 
 static int64_t launches_now() { return iim_launch_count(); }

@@ -318,9 +318,8 @@ struct TailParams {
   int top_visits;                    // consecutive visits of the first level (gamma when the
                                      // tail is entered from a finer level, else 1)
   T* u_out;                          // where the first level's u goes (when z is not set)
-  int nu;                            // coarse unknowns
-  int ld;                            // leading dimension of inv (nu, or nu + 1 when augmented)
-  const int32_t* map;
+  int ld;                            // size of the padded coarse system (its inverse is ld x ld)
+  const int32_t* map;                // node of each slot of the coarse system, -1 for a slot no unknown uses
   const T* inv;                      // dense inverse of the coarsest SW matrix (row major)
   const double* v;                   // set when the tail starts at the finest level
   const double* vscale;
@@ -479,11 +478,16 @@ __device__ __forceinline__ void vcycle_tail_body(const TailParams<T>& P, const d
     for (int i = tid; i < L.N; i += nt) u[i] = 0;
     __syncthreads();
     const int lane = tid & 31, wid = tid >> 5, nw = nt / 32;
-    for (int r = wid; r < P.nu; r += nw) {
+    for (int r = wid; r < P.ld; r += nw) {
+      const int mr = P.map[r];
+      if (mr < 0) continue;                   // the same r for the whole warp
       T s = 0;
-      for (int c = lane; c < P.nu; c += 32) s += P.inv[(size_t)r * P.ld + c] * f[P.map[c]];
+      for (int c = lane; c < P.ld; c += 32) {
+        const int mc = P.map[c];
+        if (mc >= 0) s += P.inv[(size_t)r * P.ld + c] * f[mc];
+      }
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) u[P.map[r]] = s;
+      if (lane == 0) u[mr] = s;
     }
     __syncthreads();
   };

@@ -9,23 +9,23 @@
 //   up    the prolongated coarse correction, then both post-smoothing sweeps (on the
 //         finest level the result leaves as the FP64 vector z)
 //
-// Layout.  A CTA stages a 64-column x SY-row window (the 56 x (SY - 8) output tile and a
-// halo of 4) in two shared arrays, one per colour: row y of the red array holds the 32
-// red cells of window row y, in order of x, and likewise for black.  The window starts
-// at even grid coordinates, so cell (x, y) is red when x + y is even, and in row y the
-// red cell of compressed column k sits at x = 2k + (y & 1), the black one at
-// x = 2k + 1 - (y & 1).  A red cell's four neighbours are then black cells k + p - 1 and
-// k + p of its row and k of the rows above and below (p = y & 1); a black cell's are red
-// cells k - p and k + 1 - p and k above and below.  Warp w owns rows w RW .. w RW + RW - 1
-// and lane k owns compressed column k of each: a half sweep is RW conflict-free passes of
-// four loads, three adds, one fused multiply-add, one multiply and one store per lane.
-// Both arrays carry a ring of zeros: a cell at the window's edge computes a wrong value
-// from it, and that error moves one cell inwards per half sweep, so after four half
-// sweeps every cell at distance >= 3 (down) or >= 4 (up) from the edge is exact, which is
-// what the residual and the output tile need.
+// Layout.  A CTA owns a 64-column x SY-row window (the 56 x (SY - 8) output tile and a
+// halo of 4).  The window starts at even grid coordinates, so cell (x, y) is red when
+// x + y is even, and in row y the red cell of compressed column k sits at x = 2k + (y & 1),
+// the black one at x = 2k + 1 - (y & 1).  Warp w owns rows w RW .. w RW + RW - 1 and lane k
+// owns compressed column k of each, keeping the red and the black value of every one of its
+// rows in registers.  A red cell's four neighbours are then black cells k + p - 1 and k + p
+// of its row and k of the rows above and below (p = y & 1); a black cell's are red cells
+// k - p and k + 1 - p and k above and below.  So of the horizontal pair one is the lane's own
+// register and the other one shuffle away (lane k - 1 or k + 1), and the vertical pair is in
+// the lane's own registers except at the warp's first and last rows, which each warp
+// publishes in shared memory after every half sweep (one barrier per half sweep).  Outside
+// the window (lanes -1 and 32, rows -1 and SY) the values are taken as zero: a cell at the
+// window's edge computes a wrong value from them, and that error moves one cell inwards per
+// half sweep, so after four half sweeps every cell at distance >= 3 (down) or >= 4 (up) from
+// the edge is exact, which is what the residual and the output tile need.
 //
-// Each lane keeps its cells' right-hand sides and last values in registers; the
-// restriction of a 2x2 block (two rows of one compressed column: one red and one black
+// The restriction of a 2x2 block (two rows of one compressed column: one red and one black
 // cell in each) is summed in registers by the lane that computed its four residuals.
 // A cell's class is one byte (unknown, irregular row, phase +); irregular rows (cells
 // next to the boundary or interface) take their five coefficients from the level's
@@ -39,7 +39,6 @@ constexpr int kRbKW = 32;                 // cells of one colour per window row
 constexpr int kRbSX = 2 * kRbKW;          // window width
 constexpr int kRbHalo = 4;
 constexpr int kRbTX = kRbSX - 2 * kRbHalo;    // output columns per tile (56)
-constexpr int kRbPad = kRbKW + 2;         // padded row of a colour array
 constexpr int kRbIrrCap = 320;            // staged irregular rows per tile
 
 // cell classes (one byte per node and level)
@@ -73,25 +72,25 @@ template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };
 
 // shared-memory bytes of one CTA of the kernel below
-template <typename T, int SY, bool UP>
+template <typename T, int NW, int RW, bool UP>
 constexpr size_t rb_smem_bytes() {
-  return sizeof(T) * 2 * (size_t)(SY + 2) * kRbPad        // colour arrays with their ring
-         + sizeof(T) * 5 * (size_t)kRbIrrCap              // staged irregular rows
-         + sizeof(int) * (size_t)kRbIrrCap                // their nodes
-         + sizeof(int16_t) * (size_t)SY * kRbSX           // slot of each irregular cell
-         + (UP ? (sizeof(T) + 1) * (size_t)(SY / 2 + 2) * (kRbKW + 2) : 0)   // coarse window
+  return sizeof(T) * 2 * (size_t)NW * 2 * 32                    // published first / last rows
+         + sizeof(T) * 5 * (size_t)kRbIrrCap                    // staged irregular rows
+         + sizeof(int) * (size_t)kRbIrrCap                      // their nodes
+         + sizeof(int16_t) * (size_t)NW * RW * kRbSX            // slot of each irregular cell
+         + (UP ? (sizeof(T) + 1) * (size_t)(NW * RW / 2 + 2) * (kRbKW + 2) : 0)   // coarse window
          + 16;
 }
 
 template <typename T, int NW, int RW, bool UP>
 __global__ void __launch_bounds__(NW * 32, (NW == 16 ? 2 : 4)) k_mg2d_rb(Rb2DParams<T> P) {
-  constexpr int SY = NW * RW, TY = SY - 2 * kRbHalo, ROWS = SY + 2;
+  constexpr int SY = NW * RW, TY = SY - 2 * kRbHalo;
   static_assert(RW % 2 == 0, "a lane's rows come in pairs (the 2x2 restriction)");
+  static_assert(SY > 2 * kRbHalo, "the window must be taller than its two halos");
   using T2 = typename Vec2<T>::type;
   extern __shared__ __align__(16) unsigned char rb_smem[];
-  T* sR = (T*)rb_smem;
-  T* sB = sR + ROWS * kRbPad;
-  T* sTab = sB + ROWS * kRbPad;
+  T* sPub = (T*)rb_smem;                                   // [colour][warp][first, last][lane]
+  T* sTab = sPub + 2 * NW * 2 * 32;
   int* sList = (int*)(sTab + 5 * kRbIrrCap);
   int16_t* sCode = (int16_t*)(sList + kRbIrrCap);
   T* sUc = (T*)(sCode + SY * kRbSX);                       // up: coarse window (SY/2 + 2) x 34
@@ -104,18 +103,9 @@ __global__ void __launch_bounds__(NW * 32, (NW == 16 ? 2 : 4)) k_mg2d_rb(Rb2DPar
   const int x0 = blockIdx.x * kRbTX - kRbHalo, y0 = blockIdx.y * TY - kRbHalo;
   const bool finest_in = !UP && P.v != nullptr;
   const bool one_beta = P.inv_bp == P.inv_bm;
-  auto at = [](int y, int k) { return (y + 1) * kRbPad + k + 1; };   // padded index
   auto in_tile = [&](int y) { return y >= kRbHalo && y < SY - kRbHalo && lane >= kRbHalo / 2 && lane < kRbKW - kRbHalo / 2; };
 
   if (threadIdx.x == 0) s_nirr = 0;
-  // the zero ring (and, for the down step, the arrays start at u = 0)
-  for (int e = threadIdx.x; e < ROWS * kRbPad; e += NW * 32) {
-    const int r = e / kRbPad, k = e - r * kRbPad;
-    if (!UP || r == 0 || r == ROWS - 1 || k == 0 || k == kRbPad - 1) {
-      sR[e] = (T)0;
-      sB[e] = (T)0;
-    }
-  }
 
   // ---------------------------------------------------------------- load
   // every global load of the lane is issued before any of them is used
@@ -148,7 +138,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 16 ? 2 : 4)) k_mg2d_rb(Rb2DPar
     }
   }
   const T vs = finest_in ? (T)(P.vscale ? *P.vscale : 1.0) : (T)1;
-  __syncthreads();                    // s_nirr and the zeroed arrays
+  __syncthreads();                    // s_nirr
   T fr[RW], fb[RW], ur[RW], ub[RW];
   unsigned unk = 0, irr = 0;          // bit 2 j + c: cell of row j, colour c (0 red, 1 black)
 #pragma unroll
@@ -270,33 +260,43 @@ __global__ void __launch_bounds__(NW * 32, (NW == 16 ? 2 : 4)) k_mg2d_rb(Rb2DPar
         else ub[j] += acc;
       }
     }
-#pragma unroll
-    for (int j = 0; j < RW; ++j) {
-      const int y = warp * RW + j;
-      sR[at(y, lane)] = ur[j];
-      sB[at(y, lane)] = ub[j];
-    }
   }
+  // the warp's first and last rows, for the vertical neighbours of the warps around it
+  auto pub = [&](int c, int w, int which) -> T* { return sPub + ((c * NW + w) * 2 + which) * 32; };
+  auto publish = [&](int c) {
+    pub(c, warp, 0)[lane] = c == 0 ? ur[0] : ub[0];
+    pub(c, warp, 1)[lane] = c == 0 ? ur[RW - 1] : ub[RW - 1];
+  };
+  // the four neighbours (values of the other colour) of the colour-c cell of row j
+  auto nbrs = [&](int j, int c, T& lft, T& rgt, T& dn, T& upv) {
+    const int p = j & 1;
+    const T own = c == 0 ? ub[j] : ur[j];            // other colour, same compressed column
+    if ((c == 0) == (p == 0)) {                      // red p = 0, black p = 1: left from lane - 1
+      const T v = __shfl_up_sync(0xffffffffu, own, 1);
+      lft = lane == 0 ? (T)0 : v;
+      rgt = own;
+    } else {                                         // red p = 1, black p = 0: right from lane + 1
+      const T v = __shfl_down_sync(0xffffffffu, own, 1);
+      lft = own;
+      rgt = lane == 31 ? (T)0 : v;
+    }
+    if (j > 0) dn = c == 0 ? ub[j - 1] : ur[j - 1];
+    else dn = warp > 0 ? pub(1 - c, warp - 1, 1)[lane] : (T)0;
+    if (j < RW - 1) upv = c == 0 ? ub[j + 1] : ur[j + 1];
+    else upv = warp < NW - 1 ? pub(1 - c, warp + 1, 0)[lane] : (T)0;
+  };
+  publish(0);
+  publish(1);
   __syncthreads();
 
   // ---------------------------------------------------------------- four half sweeps
   auto half_sweep = [&](const int colour, const bool from_zero) {
-    T* own = colour == 0 ? sR : sB;
-    const T* oth = colour == 0 ? sB : sR;
 #pragma unroll
     for (int j = 0; j < RW; ++j) {
-      const int y = warp * RW + j, p = j & 1;
       const int bit = 2 * j + colour;
-      // horizontal neighbours in the other colour's row: red k + p - 1, k + p; black k - p, k + 1 - p
-      const int kl = colour == 0 ? lane + p - 1 : lane - p;
       const T f = colour == 0 ? fr[j] : fb[j];
       T lft = 0, rgt = 0, dn = 0, upv = 0;
-      if (!from_zero) {
-        lft = oth[at(y, kl)];
-        rgt = oth[at(y, kl + 1)];
-        dn = oth[at(y - 1, lane)];
-        upv = oth[at(y + 1, lane)];
-      }
+      if (!from_zero) nbrs(j, colour, lft, rgt, dn, upv);
       T nv = gs_regular(f, from_zero ? (T)0 : (lft + rgt) + (dn + upv), P.ih2, P.inv_dreg);
       if ((irr_w >> bit) & 1u) {
         if ((irr >> bit) & 1u) {
@@ -308,11 +308,11 @@ __global__ void __launch_bounds__(NW * 32, (NW == 16 ? 2 : 4)) k_mg2d_rb(Rb2DPar
         }
       }
       if ((unk >> bit) & 1u) {
-        own[at(y, lane)] = nv;
         if (colour == 0) ur[j] = nv;
         else ub[j] = nv;
       }
     }
+    publish(colour);
     __syncthreads();
   };
   half_sweep(0, !UP);
@@ -326,18 +326,15 @@ __global__ void __launch_bounds__(NW * 32, (NW == 16 ? 2 : 4)) k_mg2d_rb(Rb2DPar
 #pragma unroll
     for (int j = 0; j < RW; j += 2) {
       const int y = warp * RW + j;        // even: rows y, y + 1 form the 2x2 blocks
-      if (y < kRbHalo || y >= SY - kRbHalo || lane < kRbHalo / 2 || lane >= kRbKW - kRbHalo / 2) continue;
+      if (y < kRbHalo || y >= SY - kRbHalo) continue;          // warp-uniform
       T r[2][2];                            // [row j, j + 1][red, black]
 #pragma unroll
       for (int jj = 0; jj < 2; ++jj) {
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-          const int yy = y + jj, p = jj;    // (j + jj) & 1 with j even
           const int bit = 2 * (j + jj) + c;
-          const T* oth = c == 0 ? sB : sR;
-          const int kl = c == 0 ? lane + p - 1 : lane - p;
-          const T lft = oth[at(yy, kl)], rgt = oth[at(yy, kl + 1)];
-          const T dn = oth[at(yy - 1, lane)], upv = oth[at(yy + 1, lane)];
+          T lft, rgt, dn, upv;
+          nbrs(j + jj, c, lft, rgt, dn, upv);
           const T u = c == 0 ? ur[j + jj] : ub[j + jj];
           const T f = c == 0 ? fr[j + jj] : fb[j + jj];
           T rr = 0;
@@ -357,7 +354,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 16 ? 2 : 4)) k_mg2d_rb(Rb2DPar
       // x order in the block: row y (p = 0) red then black, row y + 1 (p = 1) black then red
       const int gcx = (x0 + kRbHalo) / 2 + lane - kRbHalo / 2;
       const int gcy = (y0 + kRbHalo) / 2 + (y - kRbHalo) / 2;
-      if (gcx < nc && gcy < nc) {
+      if (lane >= kRbHalo / 2 && lane < kRbKW - kRbHalo / 2 && gcx < nc && gcy < nc) {
         const int64_t ci = (int64_t)gcy * nc + gcx;
         const T acc = (r[0][0] + r[0][1]) + (r[1][1] + r[1][0]);
         store_f(P.fc, ci, (P.cls_c[ci] & kClsUnknown) ? acc * (T)0.25 : (T)0, P.fc_bf16);

@@ -199,24 +199,32 @@ __global__ void k_bridge_out(GridView g, const T* __restrict__ u, double* __rest
 // ---------------------------------------------------------------------------- coarsest level
 // dense coarse matrix (row major, nu x nu) from the level's stencil
 template <typename T>
-__global__ void k_coarse_assemble(LevelView<double> L, const int32_t* __restrict__ map, int nu_in,
-                                  const int32_t* __restrict__ inv, T* __restrict__ A, int aug) {
-  // rows r < nu: the SW operator; augmented (pure Neumann): a last column and row of
-  // ones over the unknowns and a zero corner (Sec. 2.3), leading dimension nu + 1
+__global__ void k_coarse_assemble(LevelView<double> L, const int32_t* __restrict__ map, const int* __restrict__ nu_dev,
+                                  int cap, const int32_t* __restrict__ inv, T* __restrict__ A, int aug) {
+  // cap x cap system, cap = the coarsest level's node count (+1 when augmented), so that its
+  // size does not depend on the geometry: rows r < nu (the level's unknowns, counted on the
+  // device) the SW operator; rows nu <= r < cap - aug the identity (slots no unknown uses);
+  // augmented (pure Neumann, Sec. 2.3): the last row and column of ones over the unknowns
+  // and a zero corner
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nu = nu_in + aug;
-  if (r >= nu) return;
-  if (r == nu_in) {
-    for (int c = 0; c < nu_in; ++c) A[(size_t)r * nu + c] = 1;
-    A[(size_t)r * nu + nu_in] = 0;
+  if (r >= cap) return;
+  const int nu = *nu_dev;
+  const int ia = cap - 1;
+  for (int c = 0; c < cap; ++c) A[(size_t)r * cap + c] = (T)0;
+  if (aug && r == ia) {
+    for (int c = 0; c < nu; ++c) A[(size_t)r * cap + c] = 1;
     return;
   }
-  for (int c = 0; c < nu; ++c) A[(size_t)r * nu + c] = (aug && c == nu_in) ? (T)1 : (T)0;
+  if (r >= nu) {
+    A[(size_t)r * cap + r] = 1;
+    return;
+  }
+  if (aug) A[(size_t)r * cap + ia] = 1;
   int64_t i = map[r];
   int a = L.aux[i];
   int m[3];
   idx3(L.g, i, m);
-  A[(size_t)r * nu + r] = (T)diag_of(L, -2.0 * L.g.dim / (L.g.h * L.g.h), a);
+  A[(size_t)r * cap + r] = (T)diag_of(L, -2.0 * L.g.dim / (L.g.h * L.g.h), a);
   const GridView& g = L.g;
   for (int ax = 0; ax < g.dim; ++ax) {
     int64_t st = ax == 0 ? 1 : (ax == 1 ? (int64_t)g.n : (int64_t)g.n * g.n);
@@ -226,7 +234,7 @@ __global__ void k_coarse_assemble(LevelView<double> L, const int32_t* __restrict
       double cf = a == -1 ? 1.0 / (g.h * g.h) : tabv(L, a, (s < 0 ? 1 : 2) + 2 * ax);
       if (cf == 0.0) continue;
       int col = inv[i + s * st];
-      if (col >= 0) A[(size_t)r * nu + col] = (T)cf;
+      if (col >= 0) A[(size_t)r * cap + col] = (T)cf;
     }
   }
 }
@@ -431,7 +439,6 @@ TailParams<T> make_tail_params(Problem& P, size_t l0, T* u_out, size_t smem_limi
   tp.gamma = P.opt.cycle;
   tp.top_visits = 1;
   tp.neumann = P.desc.bc == IIM_BC_NEUMANN;
-  tp.nu = P.coarse_nu;
   tp.ld = P.coarse_n;
   tp.map = P.coarse_map;
   const T* inv = (const T*)(sizeof(T) == 8 ? (void*)P.coarse_lu64 : (void*)P.coarse_lu32);
@@ -529,11 +536,11 @@ static void launch_rb(Problem& P, size_t l, int mode, const double* v, const dou
   constexpr int SY = NW * RW, TY = SY - 2 * kRbHalo;
   const dim3 grid(ceil_div(L.g.n, kRbTX), ceil_div(L.g.n, TY));
   if (mode == 5) {
-    constexpr size_t sm = rb_smem_bytes<T, SY, false>();
+    constexpr size_t sm = rb_smem_bytes<T, NW, RW, false>();
     if (sm > 48 * 1024) smem_optin((const void*)k_mg2d_rb<T, NW, RW, false>);
     IIM_LAUNCH((k_mg2d_rb<T, NW, RW, false>), grid, NW * 32, sm, s, rp);
   } else {
-    constexpr size_t sm = rb_smem_bytes<T, SY, true>();
+    constexpr size_t sm = rb_smem_bytes<T, NW, RW, true>();
     if (sm > 48 * 1024) smem_optin((const void*)k_mg2d_rb<T, NW, RW, true>);
     IIM_LAUNCH((k_mg2d_rb<T, NW, RW, true>), grid, NW * 32, sm, s, rp);
   }
@@ -701,19 +708,23 @@ bool mg_one_kernel(Problem& P, int which, const double* v, double* z, cudaStream
   return mg_one_kernel_t<float>(P, which, v, z, s);
 }
 
-// coarse matrix, LU and inverse; coarse_lu{64,32} hold [A (nu*nu) | inverse (nu*nu)]
+// coarse matrix, LU and inverse; coarse_lu{64,32} hold [A (cn*cn) | inverse (cn*cn)], cn the
+// fixed size of the padded system (a re-run set-up with another geometry changes only the
+// device-side unknown count)
 void mg_coarse_factor(Problem& P, cudaStream_t s) {
   Level& C = P.lv.back();
-  const int nu = P.coarse_nu, cn = P.coarse_n;
-  if (nu <= 0) return;
+  const int cn = P.coarse_n;
+  if (cn <= 0) return;
   const int Tn = 256;
   IIM_LAUNCH(k_unknown_flag, ceil_div(C.g.N, Tn), Tn, 0, s, C.g, C.aux, C.flag);
   scan_exclusive(C.flag, C.idx, C.g.N, P.d_counts + kCountCoarse, P.scan_scratch, s);
   int32_t* inv = C.flag;            // reuse: node -> unknown index
+  cudaMemsetAsync(P.coarse_map, 0xff, sizeof(int32_t) * (size_t)cn, s);    // -1: a slot no unknown uses
   IIM_LAUNCH(k_coarse_map, ceil_div(C.g.N, Tn), Tn, 0, s, C.g, C.aux, C.idx, P.coarse_map, inv);
   LevelView<double> V = view<double>(C);
+  const int* nu = P.d_counts + kCountCoarse;
   if (P.opt.mg_precision == IIM_MG_FP64) {
-    IIM_LAUNCH(k_coarse_assemble<double>, ceil_div(cn, 128), 128, 0, s, V, P.coarse_map, nu, inv, P.coarse_lu64,
+    IIM_LAUNCH(k_coarse_assemble<double>, ceil_div(cn, 128), 128, 0, s, V, P.coarse_map, nu, cn, inv, P.coarse_lu64,
                P.aug);
     size_t sm = sizeof(double) * (size_t)cn * cn;
     int in_smem = sm <= 200 * 1024;
@@ -722,7 +733,7 @@ void mg_coarse_factor(Problem& P, cudaStream_t s) {
     IIM_LAUNCH(k_coarse_lu<double>, 1, 1024, in_smem ? sm : 0, s, P.coarse_lu64, cn, P.coarse_piv,
                P.coarse_lu64 + (size_t)cn * cn, P.d_status, in_smem);
   } else {
-    IIM_LAUNCH(k_coarse_assemble<float>, ceil_div(cn, 128), 128, 0, s, V, P.coarse_map, nu, inv, P.coarse_lu32,
+    IIM_LAUNCH(k_coarse_assemble<float>, ceil_div(cn, 128), 128, 0, s, V, P.coarse_map, nu, cn, inv, P.coarse_lu32,
                P.aug);
     size_t sm = sizeof(float) * (size_t)cn * cn;
     int in_smem = sm <= 200 * 1024;

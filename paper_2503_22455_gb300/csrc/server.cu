@@ -48,6 +48,8 @@ struct Request {
   int64_t id = 0;
   iim_problem_desc desc;
   std::vector<double> geom_coef;  // the request's own copy of a Fourier curve's coefficients
+  bool reuse = false;             // takes a retired problem of the same kind from the pool
+  size_t freed_bytes = 0;         // a pooled problem the worker had to destroy (reuse failed)
   double t_submit = 0, t_done = 0;
   int state = kQueued;
   iim_problem* prob = nullptr;
@@ -62,8 +64,38 @@ struct Request {
   iim_status error = IIM_OK;
 };
 
+// Retired problems kept for reuse: a request of the same kind (dimension, size, conditions,
+// order, geometry kind, side, coefficients) takes one and re-runs its set-up in place with
+// its own geometry parameters, keeping the allocation, the stream and the solve graph.
+struct PoolKey {
+  int dim, n, bc, box_bc, order, kind, plus_inside;
+  double bp, bm;
+  bool operator==(const PoolKey& o) const {
+    return dim == o.dim && n == o.n && bc == o.bc && box_bc == o.box_bc && order == o.order && kind == o.kind &&
+           plus_inside == o.plus_inside && bp == o.bp && bm == o.bm;
+  }
+};
+struct PoolEntry {
+  PoolKey key;
+  iim_problem* prob;
+  cudaStream_t stream;
+  size_t bytes;
+  int64_t stamp;
+};
+
+static bool poolable(const iim_problem_desc& d) {
+  // analytic bodies: their whole geometry is in geom_params (the set-up can change it in place)
+  return d.geom_kind != IIM_GEOM_FOURIER && d.geom_kind != IIM_GEOM_LEVELSET_GRID;
+}
+static PoolKey pool_key(const iim_problem_desc& d) {
+  return PoolKey{d.dim, d.n, d.bc, d.box_bc, d.order, d.geom_kind, d.plus_inside, d.beta_plus, d.beta_minus};
+}
+
 struct Server {
   iim_options opt;
+  std::vector<PoolEntry> pool;   // retired problems (their bytes stay counted in in_use)
+  int64_t pool_stamp = 0, pool_hits = 0, pool_misses = 0, pool_evicted = 0;
+  bool pooling = true;
   size_t budget = 0, in_use = 0, peak = 0;
   int max_slots = 0, ticks_per_run = 1;
   iim_engine* engine = nullptr;
@@ -109,10 +141,30 @@ static void create_worker(Server* S) {
       S->to_create.pop_front();
     }
     const auto t = Clock::now();
-    r->create_status = iim_problem_create(&r->desc, &S->opt, r->stream, &r->prob);
-    if (r->create_status != IIM_OK) r->prob = nullptr;
+    bool fresh = true;
+    if (r->reuse && r->prob) {
+      // re-run the set-up in place with this request's geometry, on the problem's own stream
+      iim_status st = setup_direct(r->prob->P, r->desc.geom_params);
+      if (st == IIM_OK) st = iim_status_get(r->prob);
+      if (st == IIM_OK) {
+        r->create_status = IIM_OK;
+        fresh = false;
+      } else {
+        // capacity or geometry: give the problem up and create one for this request
+        r->freed_bytes = r->prob->P.bytes;
+        cudaStream_t keep = r->stream;
+        iim_problem_destroy(r->prob);
+        r->prob = nullptr;
+        r->stream = keep;
+        r->reuse = false;
+      }
+    }
+    if (fresh) {
+      r->create_status = iim_problem_create(&r->desc, &S->opt, r->stream, &r->prob);
+      if (r->create_status != IIM_OK) r->prob = nullptr;
+    }
     // streams mode: capture the request's solve graph here, off the loop's thread
-    if (r->prob && S->mode == 1 && S->opt.use_graph) {
+    if (r->prob && fresh && S->mode == 1 && S->opt.use_graph) {
       r->create_status = krylov_build_graph(r->prob->P, r->prob->P.x);
       if (r->create_status != IIM_OK) {
         iim_problem_destroy(r->prob);
@@ -134,7 +186,15 @@ struct iim_server {
   Server S;
 };
 
-static void free_problem(Server& S, Request* r) {
+static void free_problem(Server& S, Request* r, bool keep = false) {
+  if (r->prob && keep && S.pooling && poolable(r->desc) && r->stream) {
+    // the problem (and its stream, which its solve graph and set-up use) waits for a request
+    // of the same kind; its bytes stay counted until it is reused or evicted
+    S.pool.push_back(PoolEntry{pool_key(r->desc), r->prob, r->stream, r->bytes, ++S.pool_stamp});
+    r->prob = nullptr;
+    r->stream = nullptr;
+    return;
+  }
   if (r->prob) {
     iim_problem_destroy(r->prob);
     r->prob = nullptr;
@@ -142,6 +202,22 @@ static void free_problem(Server& S, Request* r) {
   }
   if (r->stream) S.free_streams.push_back(r->stream);
   r->stream = nullptr;
+}
+
+// free pooled problems, oldest first, until need more bytes fit the budget (or none is left)
+static void pool_evict(Server& S, size_t need) {
+  while (!S.pool.empty() && S.in_use + need > S.budget) {
+    size_t old = 0;
+    for (size_t k = 1; k < S.pool.size(); ++k)
+      if (S.pool[k].stamp < S.pool[old].stamp) old = k;
+    PoolEntry e = S.pool[old];
+    S.pool[old] = S.pool.back();
+    S.pool.pop_back();
+    iim_problem_destroy(e.prob);
+    S.in_use -= e.bytes;
+    S.free_streams.push_back(e.stream);
+    ++S.pool_evicted;
+  }
 }
 
 extern "C" {
@@ -195,10 +271,33 @@ void iim_server_destroy(iim_server* H) {
     free_problem(S, r);
     delete r;
   }
+  for (PoolEntry& e : S.pool) {
+    iim_problem_destroy(e.prob);
+    S.free_streams.push_back(e.stream);
+  }
+  S.pool.clear();
   iim_engine_destroy(S.engine);
   for (cudaStream_t s : S.free_streams) cudaStreamDestroy(s);
   cudaStreamDestroy(S.stream);
   delete H;
+}
+
+iim_status iim_server_set_pooling(iim_server* H, int on) {
+  if (!H) return IIM_ERR_INVALID_ARG;
+  Server& S = H->S;
+  S.pooling = on != 0;
+  if (!S.pooling) pool_evict(S, S.budget + 1);       // frees every pooled problem
+  return IIM_OK;
+}
+
+iim_status iim_server_pool_stats(iim_server* H, int64_t* hits, int64_t* misses, int64_t* evicted, int* pooled) {
+  if (!H) return IIM_ERR_INVALID_ARG;
+  Server& S = H->S;
+  if (hits) *hits = S.pool_hits;
+  if (misses) *misses = S.pool_misses;
+  if (evicted) *evicted = S.pool_evicted;
+  if (pooled) *pooled = (int)S.pool.size();
+  return IIM_OK;
 }
 
 iim_status iim_server_submit(iim_server* H, const iim_problem_desc* desc, int64_t* id) {
@@ -335,7 +434,7 @@ iim_status iim_server_step(iim_server* H, int64_t* need_data, int cap_need, int*
     r->t_done = S.now();
     r->state = r->info.status == IIM_OK ? kFinished : kFailed;
     r->error = (iim_status)r->info.status;
-    free_problem(S, r);
+    free_problem(S, r, r->state == kFinished);
     S.note_fin.push_back(r->id);
   }
   // 4. requests the workers have created: check the exact size against the budget
@@ -348,6 +447,15 @@ iim_status iim_server_step(iim_server* H, int64_t* need_data, int cap_need, int*
     --S.creating;
     S.in_use -= r->reserved;
     r->reserved = 0;
+    S.in_use -= r->freed_bytes;          // a pooled problem given up by the worker
+    r->freed_bytes = 0;
+    if (r->reuse && r->create_status == IIM_OK) {
+      // the reused problem's bytes have been counted all along
+      r->reuse = false;
+      r->state = kNeedData;
+      S.note_need.push_back(r->id);
+      continue;
+    }
     if (r->create_status != IIM_OK) {
       r->state = kFailed;
       r->error = r->create_status;
@@ -384,9 +492,38 @@ iim_status iim_server_step(iim_server* H, int64_t* need_data, int cap_need, int*
   // 5. admission by budget, in submission order: reserve and hand to the workers
   while (!S.queue.empty()) {
     Request* r = S.queue.front();
+    if (S.pooling && poolable(r->desc)) {
+      // a retired problem of the same kind: no allocation, its set-up is re-run in place
+      const PoolKey key = pool_key(r->desc);
+      int best = -1;
+      for (size_t k = 0; k < S.pool.size(); ++k)
+        if (S.pool[k].key == key && (best < 0 || S.pool[k].stamp > S.pool[best].stamp)) best = (int)k;
+      if (best >= 0) {
+        PoolEntry e = S.pool[best];
+        S.pool[best] = S.pool.back();
+        S.pool.pop_back();
+        S.queue.pop_front();
+        r->prob = e.prob;
+        r->stream = e.stream;
+        r->bytes = e.bytes;
+        r->reuse = true;
+        r->reserved = 0;
+        r->state = kCreating;
+        ++S.creating;
+        ++S.pool_hits;
+        {
+          std::lock_guard<std::mutex> lk(S.mu);
+          S.to_create.push_back(r);
+        }
+        S.cv.notify_one();
+        continue;
+      }
+    }
     const size_t need = r->known_bytes ? r->known_bytes : estimate_bytes(r->desc, S.opt);
+    pool_evict(S, need);
     if (S.in_use + need > S.budget) break;
     S.queue.pop_front();
+    ++S.pool_misses;
     if (!S.free_streams.empty()) {
       r->stream = S.free_streams.back();
       S.free_streams.pop_back();

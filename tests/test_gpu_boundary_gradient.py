@@ -1,10 +1,12 @@
 """Boundary quantities and the gradient (Sec. 2.4) on the GPU against the oracle.
 
 Tolerance 1e-11 relative to the largest value.  The fit coefficients come from two
-QR implementations (LAPACK in the oracle, Householder on the device) and agree to
-about cond(V) x 1e-16 ~ 1e-12 for q = 6; unlike the Laplacian, whose diagonal term
-dominates, the first-derivative sums carry that difference undamped (measured
-4.7e-12 for the (6,7) star on a random vector).  The inputs are a random vector and
+QR implementations (LAPACK in the oracle, Householder on the device), each within its
+rounding level of the exact least-squares rows (the oracle's ghost rows lie within
+1.1e-13 of 40-digit rows relative to the row's size, tests/test_oracle_fits_precision.py);
+unlike the Laplacian, whose diagonal term dominates, the first-derivative sums carry the
+two FP64 errors undamped and with a factor 1/h (measured 4.7e-12 for the (6,7) star on a
+random vector), so 1e-12 is below what two FP64 implementations can agree to here.  The inputs are a random vector and
 the converged solution; the GPU's data are evaluated at its own control points,
 which agree with the oracle's to a few ulps (test_gpu_parity).
 """

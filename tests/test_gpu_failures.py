@@ -58,7 +58,7 @@ def test_max_iter_reports_not_converged(env):
 
 def test_budget_refusal_does_not_block_the_queue(env):
     torch, iim = env
-    small = [W.circle_dirichlet_64(64), W.star_interface_1024(96), W.circle_dirichlet_64(80)]
+    small = [W.circle_dirichlet_64(64), W.star_interface_1024(128), W.circle_dirichlet_64(80)]
     sizes = []
     for sp in small:
         P = gpu_problem(iim, sp)

@@ -152,6 +152,7 @@ def test_set_phi_equals_a_fresh_problem(env):
     P = gpu_problem(iim, s1)
     P.set_phi(dev(W.to_flat(g2.values)))
     P.setup()
+    P.refresh_sizes()
     Q = gpu_problem(iim, s2)
     assert P.K == Q.K
     assert np.array_equal(P.phase().cpu().numpy(), Q.phase().cpu().numpy())

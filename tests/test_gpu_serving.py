@@ -25,11 +25,14 @@ def env():
     return need_gpu()
 
 
-def _serve(iim, specs, budget, ticks_per_run=3, mode=0):
-    S = iim.Server(iim.default_options(), budget_bytes=budget, max_slots=8, ticks_per_run=ticks_per_run, mode=mode)
+def _serve(iim, specs, budget, ticks_per_run=3, mode=0, pooling=True, pool_stats=None):
+    S = iim.Server(iim.default_options(), budget_bytes=budget, max_slots=8, ticks_per_run=ticks_per_run, mode=mode,
+                   pooling=pooling)
     arrivals = [(0.0, iim.desc_from_spec(sp), sp) for sp in specs]
     out, wall = iim.serve(S, arrivals, lambda view, sp: set_gpu_data(view, sp), realtime=False)
     stats = S.stats()
+    if pool_stats is not None:
+        pool_stats.update(S.pool_stats())
     S.close()
     return [out[rid] for rid in sorted(out)], stats
 
@@ -93,3 +96,33 @@ def test_every_request_reported_with_one_id_per_step(env, mode):
     assert len(out) == len(specs)
     assert all(o[3] == 0 for o in out.values())
     assert sum(st["states"].values()) == 0
+
+
+@pytest.mark.parametrize("mode", [1, 0])
+def test_kept_problems_give_the_results_of_fresh_ones(env, mode):
+    """Requests of a few kinds repeated with other geometry parameters, through a budget that
+    holds about two problems: finished problems are kept and taken by later requests of the
+    same kind (set-up re-run in place), or freed for room.  Every result equals, bit for bit,
+    the result with reuse switched off (every request created afresh)."""
+    torch, iim = env
+    specs = []
+    for k in range(4):
+        specs.append(W.ProblemSpec(n=96, geometry=W.Geometry(W.CIRCLE, (0.01 * k, -0.02, 0.45 + 0.03 * k), True),
+                                   bc=W.DIRICHLET, order=4, solution=W.sin_cos_2d(2.0, 0.3, 1.5, 0.7)))
+        specs.append(W.ProblemSpec(n=80, geometry=W.Geometry(W.ELLIPSE, (0.02, -0.03, 0.38 + 0.02 * k, 0.3, 0.2 * k),
+                                                             False),
+                                   bc=W.NEUMANN, order=6, box_bc=W.BOX_DIRICHLET, beta_plus=2.0,
+                                   solution=W.sin_cos_2d(2.0, 0.3, 1.5, 0.7)))
+    sizes = []
+    for sp in specs[:2]:
+        P = gpu_problem(iim, sp)
+        sizes.append(P.device_bytes())
+        P.close()
+    budget = int(2.6 * max(sizes))
+    ps = {}
+    kept, _ = _serve(iim, specs, budget, mode=mode, pooling=True, pool_stats=ps)
+    fresh, _ = _serve(iim, specs, budget, mode=mode, pooling=False)
+    assert ps["hits"] > 0
+    for (xa, ia, _, sa, sp), (xb, ib, _, sb, _) in zip(kept, fresh):
+        assert sa == 0 and sb == 0 and ia.converged and ib.converged, sp.name
+        assert ia.iters == ib.iters and np.array_equal(xa, xb), (sp.geometry, ia.as_dict(), ib.as_dict())

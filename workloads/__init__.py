@@ -117,10 +117,10 @@ def from_flat(v: np.ndarray, n: int, dim: int) -> np.ndarray:
 # ----------------------------------------------------------------------------
 def harmonic_exp_sin() -> Manufactured:
     """u = exp(x) sin(y): harmonic (Laplace problem of the 64^2 circle case)."""
-    u = lambda X: np.exp(X[..., 0]) * np.sin(X[..., 1])
-    g = lambda X: np.stack([np.exp(X[..., 0]) * np.sin(X[..., 1]),
-                            np.exp(X[..., 0]) * np.cos(X[..., 1])], axis=-1)
-    lap = lambda X: np.zeros(X.shape[:-1])
+    u = lambda X, xp=np: xp.exp(X[..., 0]) * xp.sin(X[..., 1])
+    g = lambda X, xp=np: xp.stack([xp.exp(X[..., 0]) * xp.sin(X[..., 1]),
+                                   xp.exp(X[..., 0]) * xp.cos(X[..., 1])], axis=-1)
+    lap = lambda X, xp=np: 0.0 * X[..., 0]
     return Manufactured(u, g, lap)
 
 
@@ -275,7 +275,7 @@ def source_term_device(spec: ProblemSpec, phase_plus):
     """source_term on the device for the boundary problems of the batch and serving
     mixes: ``phase_plus`` is the problem's phase (torch uint8/bool, flat order); the
     result is a flat float64 torch tensor on the same device.  Needs a solution
-    family written for an array namespace (sin_cos_2d, sin_sin_cos_3d)."""
+    family written for an array namespace (harmonic_exp_sin, sin_cos_2d, sin_sin_cos_3d)."""
     import torch
     n, d = spec.n, spec.dim
     x = -1.0 + (torch.arange(n, dtype=torch.float64, device=phase_plus.device) + 0.5) * (2.0 / n)
