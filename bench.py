@@ -426,87 +426,6 @@ def run_serve(args):
         print(json.dumps(res))
 
 
-def batch_run(iim, torch, count, steps, seed=2503, engines=2):
-    """``count`` mixed 2D problems (50% interior Dirichlet, 50% exterior Neumann with a
-    Dirichlet box, (4,5)/(6,7), ellipses and 5-7 lobe stars, n 64..512) per step: device
-    set-up, data and solve of all of them, through per-problem solve graphs on a pool of
-    streams and through the batched engine.  L2 is flushed before each step."""
-    import workloads as W
-    specs = W.batch_specs(count, seed=seed)
-    main = torch.cuda.current_stream()
-    pool = [torch.cuda.Stream() for _ in range(16)]
-    opts = iim.default_options(tol=1e-10, mg_precision=iim.MG_FP32)
-    probs = [iim.Problem(iim.desc_from_spec(sp), opts, pool[i % len(pool)]) for i, sp in enumerate(specs)]
-    inputs = []
-    for P, sp in zip(probs, specs):
-        with torch.cuda.stream(P.stream):
-            inputs.append(_boundary_inputs(P, sp))
-    torch.cuda.synchronize()
-    xs = [torch.zeros(P.N, dtype=torch.float64, device="cuda") for P in probs]
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    eng_streams = [main] + [torch.cuda.Stream() for _ in range(engines - 1)]
-    E = [iim.Engine(opts, max_slots=(count + engines - 1) // engines, stream=st) for st in eng_streams]
-
-    def prepare():
-        start = torch.cuda.Event()
-        start.record(main)
-        for P, (f, g, box) in zip(probs, inputs):
-            P.stream.wait_event(start)
-            with torch.cuda.stream(P.stream):
-                P.setup()
-                P.set_data(f, g, None, None, box)
-        for st in pool:
-            main.wait_stream(st)
-
-    def step_pool():
-        prepare()
-        infos, _ = iim.batch_solve(probs, xs)
-        for st in pool:
-            main.wait_stream(st)
-        return infos
-
-    def step_engine():
-        prepare()
-        ev = torch.cuda.Event()
-        ev.record(main)
-        for st in eng_streams[1:]:
-            st.wait_event(ev)
-        slots = [E[i % engines].admit(P) for i, P in enumerate(probs)]
-        for e in E:
-            e.run()
-        for e in E:
-            e.poll(wait=True)
-        infos = [E[i % engines].release(sl, x) for i, (sl, x) in enumerate(zip(slots, xs))]
-        for st in eng_streams[1:]:
-            main.wait_stream(st)
-        return infos
-
-    res = {}
-    for name, fn in (("stream_pool", step_pool), ("engine", step_engine)):
-        fn()
-        torch.cuda.synchronize()
-        t, iters = [], []
-        for k in range(steps):
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(main)
-            infos = fn()
-            b.record(main)
-            torch.cuda.synchronize()
-            if not all(i.converged for i in infos):
-                raise RuntimeError(f"batch ({name}): a problem did not converge")
-            t.append(a.elapsed_time(b))
-            iters += [i.iters for i in infos]
-        res[name] = {"solves_per_s": count * 1e3 / statistics.mean(t), "ms_per_step": statistics.mean(t),
-                     "iters_mean": statistics.mean(iters), "iters_max": max(iters)}
-    for e in E:
-        e.close()
-    for P in probs:
-        P.close()
-    return {"problems": count, "steps": steps, "seed": seed, **res,
-            "step": "setup+data+solve of every problem, L2 flushed before each step"}
-
-
 def ellipsoid_forms(iim, torch, main, flush, n, steps, warmup):
     """The exterior Neumann ellipsoid with a Dirichlet box, (4,5), n^3: per form (FP32
     multigrid, FP32 multigrid with the restricted residuals stored as BF16, all FP64),
@@ -659,6 +578,24 @@ def run_ellipsoid(args):
         print(json.dumps(out))
 
 
+def child_line(extra, timeout_s):
+    """Run this script with ``extra`` arguments in a child process (its own CUDA context) and
+    return the JSON line it prints, or {"error": ...} when it fails or runs past timeout_s
+    seconds (the child is killed then)."""
+    cmd = [sys.executable, os.path.abspath(__file__), *extra]
+    t0 = time.perf_counter()
+    try:
+        p = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s)
+    except subprocess.TimeoutExpired:
+        return {"error": f"killed after {timeout_s} s", "args": extra}
+    for line in reversed(p.stdout.splitlines()):
+        if line.startswith("{"):
+            out = json.loads(line)
+            out["child_wall_s"] = time.perf_counter() - t0
+            return out
+    return {"error": f"exit status {p.returncode}: {p.stderr[-400:]}", "args": extra}
+
+
 def _load_lib(iim):
     import __graft_entry__ as ge
     try:
@@ -797,9 +734,14 @@ def run_ours(args):
     other = {}
     if args.other_configs and world == 1:
         other["circle_dirichlet_64_o4"] = circle64_run(iim, torch, main, flush)
-        other["ellipsoid_neumann_256_o4"] = ellipsoid_forms(iim, torch, main, flush, 256, steps=2, warmup=1)
-        other["batch512_mixed_2d"] = batch_run(iim, torch, 512, steps=2)
-        other["serve_poisson_400"] = serve_run(iim, torch, 400, 200.0, 22455, deadline_s=240.0)
+        # the larger configurations run in child processes of their own, each with a time
+        # limit, so that none of them can hold up this line
+        other["ellipsoid_neumann_256_o4"] = child_line(["--workload", "ellipsoid256", "--steps", "2", "--warmup", "1"],
+                                                       timeout_s=420)
+        other["batch512_mixed_2d"] = child_line(["--workload", "batch512", "--count", "512", "--steps", "2"],
+                                                timeout_s=420)
+        other["serve_poisson_400"] = child_line(["--workload", "serve", "--count", "400", "--serve-deadline", "240"],
+                                                timeout_s=420)
     e2e = None
     if not args.no_e2e:
         e2e = e2e_run(probs, torch, inputs, Wm, K, world, main)

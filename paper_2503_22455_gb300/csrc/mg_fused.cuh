@@ -318,8 +318,11 @@ struct TailParams {
   int top_visits;                    // consecutive visits of the first level (gamma when the
                                      // tail is entered from a finer level, else 1)
   T* u_out;                          // where the first level's u goes (when z is not set)
-  int ld;                            // size of the padded coarse system (its inverse is ld x ld)
-  const int32_t* map;                // node of each slot of the coarse system, -1 for a slot no unknown uses
+  int ld;                            // stride of the coarse inverse (the coarsest level's nodes + aug)
+  const int* nu_dev;                 // the coarsest level's unknowns (device count of the current set-up)
+  int aug;                           // 1: the coarse system carries the augmentation (pure Neumann)
+  const int32_t* map;                // node of each unknown of the coarse system (-1 past the unknowns)
+  int* status;                       // where a coarse count out of range is reported
   const T* inv;                      // dense inverse of the coarsest SW matrix (row major)
   const double* v;                   // set when the tail starts at the finest level
   const double* vscale;
@@ -332,18 +335,19 @@ template <typename T>
 __device__ inline T tabd(const T* tb, int dim, int r, int k) { return tb[r * (2 * dim + 1) + k]; }
 
 // offdiagonal part of (L u)_i from shared-memory u; m = (i0, i1, i2)
-template <typename T>
+template <typename T, int DIM>
 __device__ inline T tail_offdiag(const LevelK<T>& L, const T* tb, const T* u, int i, const int* m, int a) {
   const int n = L.n;
   if (a == -1) {
     T s = (u[i - 1] + u[i + 1]) + (u[i - n] + u[i + n]);
-    if (L.dim > 2) s += u[i - n * n] + u[i + n * n];
+    if (DIM > 2) s += u[i - n * n] + u[i + n * n];
     return s * L.ih2;
   }
   T s = 0;
   int st = 1;
-  for (int ax = 0; ax < L.dim; ++ax) {
-    const T cl = tabd(tb, L.dim, a, 1 + 2 * ax), cr = tabd(tb, L.dim, a, 2 + 2 * ax);
+#pragma unroll
+  for (int ax = 0; ax < DIM; ++ax) {
+    const T cl = tabd(tb, DIM, a, 1 + 2 * ax), cr = tabd(tb, DIM, a, 2 + 2 * ax);
     if (cl != (T)0 && m[ax] > 0) s += cl * u[i - st];
     if (cr != (T)0 && m[ax] < n - 1) s += cr * u[i + st];
     st *= n;
@@ -353,13 +357,14 @@ __device__ inline T tail_offdiag(const LevelK<T>& L, const T* tb, const T* u, in
 
 // node -> (i0, i1, i2) for the nodes i = t, t + stride, ...: one division per level, then
 // a carry per step (stride is the block size)
+template <int DIM>
 struct NodeWalk {
-  int n, dim, i0, i1, i2, d0, drow;
-  __device__ NodeWalk(int n_, int dim_, int start, int stride) : n(n_), dim(dim_) {
+  int n, i0, i1, i2, d0, drow;
+  __device__ NodeWalk(int n_, int start, int stride) : n(n_) {
     i0 = start % n;
     const int r = start / n;
-    i1 = dim > 2 ? r % n : r;
-    i2 = dim > 2 ? r / n : 0;
+    i1 = DIM > 2 ? r % n : r;
+    i2 = DIM > 2 ? r / n : 0;
     d0 = stride % n;
     drow = stride / n;
   }
@@ -368,11 +373,11 @@ struct NodeWalk {
     int rows = drow;
     if (i0 >= n) { i0 -= n; ++rows; }
     i1 += rows;
-    if (dim > 2 && i1 >= n) { i2 += i1 / n; i1 %= n; }
+    if (DIM > 2 && i1 >= n) { i2 += i1 / n; i1 %= n; }
   }
 };
 
-template <typename T>
+template <typename T, int DIM>
 __device__ __forceinline__ void vcycle_tail_body(const TailParams<T>& P, const double* v_in, const double* vscale,
                                                  double* z_out) {
   extern __shared__ unsigned char smraw[];
@@ -388,13 +393,13 @@ __device__ __forceinline__ void vcycle_tail_body(const TailParams<T>& P, const d
     for (int i = tid; i < P.L[k].N; i += nt) {
       sa[P.off[k] + i] = P.L[k].aux[i];
       const int r = i / n;
-      sco[P.off[k] + i] = (i - r * n) | ((P.L[k].dim > 2 ? r % n : r) << 10) | ((P.L[k].dim > 2 ? r / n : 0) << 20);
+      sco[P.off[k] + i] = (i - r * n) | ((DIM > 2 ? r % n : r) << 10) | ((DIM > 2 ? r / n : 0) << 20);
     }
   }
   if (P.stage_tables) {
     for (int k = 0; k < P.nlev; ++k) {
       const int rows = min(*P.tcount[k], P.tcap[k]);
-      const int len = rows * (2 * P.L[k].dim + 1);
+      const int len = rows * (2 * DIM + 1);
       for (int e = tid; e < len; e += nt) st[P.toff[k] + e] = P.L[k].tab[e];
     }
   }
@@ -425,10 +430,10 @@ __device__ __forceinline__ void vcycle_tail_body(const TailParams<T>& P, const d
       } else if (a == -2) {
         u[i] = 0;
       } else {
-        const T s = from_zero ? (T)0 : tail_offdiag(L, tb, u, i, m, a);
+        const T s = from_zero ? (T)0 : tail_offdiag<T, DIM>(L, tb, u, i, m, a);
         if (a == -1) u[i] = (f[i] - s) * L.inv_dreg;
         else {
-          const T dg = tabd(tb, L.dim, a, 0);
+          const T dg = tabd(tb, DIM, a, 0);
           u[i] = dg != (T)0 ? (f[i] - s) / dg : (T)0;
         }
       }
@@ -449,19 +454,19 @@ __device__ __forceinline__ void vcycle_tail_body(const TailParams<T>& P, const d
     const int* aux = sa + P.off[k];
     const int* auxc = sa + P.off[k + 1];
     const T* tb = table(k);
-    const T wch = L.dim > 2 ? (T)0.125 : (T)0.25;
-    NodeWalk w(C.n, C.dim, tid, nt);
+    const T wch = DIM > 2 ? (T)0.125 : (T)0.25;
+    NodeWalk<DIM> w(C.n, tid, nt);
     for (int I = tid; I < C.N; I += nt, w.advance()) {
       T acc = 0;
       if (auxc[I] != -2) {
-        const int nch = 1 << L.dim;
+        constexpr int nch = 1 << DIM;
         for (int c = 0; c < nch; ++c) {
-          const int m[3] = {2 * w.i0 + (c & 1), 2 * w.i1 + ((c >> 1) & 1), L.dim > 2 ? 2 * w.i2 + ((c >> 2) & 1) : 0};
+          const int m[3] = {2 * w.i0 + (c & 1), 2 * w.i1 + ((c >> 1) & 1), DIM > 2 ? 2 * w.i2 + ((c >> 2) & 1) : 0};
           const int i = m[0] + L.n * (m[1] + L.n * m[2]);
           const int a = aux[i];
           if (a == -2) continue;
-          const T dg = a == -1 ? L.dreg : tabd(tb, L.dim, a, 0);
-          acc += f[i] - (dg * u[i] + tail_offdiag(L, tb, u, i, m, a));
+          const T dg = a == -1 ? L.dreg : tabd(tb, DIM, a, 0);
+          acc += f[i] - (dg * u[i] + tail_offdiag<T, DIM>(L, tb, u, i, m, a));
         }
         acc *= wch;
       }
@@ -478,16 +483,16 @@ __device__ __forceinline__ void vcycle_tail_body(const TailParams<T>& P, const d
     for (int i = tid; i < L.N; i += nt) u[i] = 0;
     __syncthreads();
     const int lane = tid & 31, wid = tid >> 5, nw = nt / 32;
-    for (int r = wid; r < P.ld; r += nw) {
-      const int mr = P.map[r];
-      if (mr < 0) continue;                   // the same r for the whole warp
+    int nu = *P.nu_dev;                       // unknowns; the augmentation (if any) follows them
+    if (nu < 0 || nu + P.aug > P.ld) {        // a count the dense system has no room for
+      if (tid == 0 && P.status) set_status(P.status, IIM_ERR_CAPACITY);
+      nu = 0;
+    }
+    for (int r = wid; r < nu; r += nw) {
       T s = 0;
-      for (int c = lane; c < P.ld; c += 32) {
-        const int mc = P.map[c];
-        if (mc >= 0) s += P.inv[(size_t)r * P.ld + c] * f[mc];
-      }
+      for (int c = lane; c < nu; c += 32) s += P.inv[(size_t)r * P.ld + c] * f[P.map[c]];
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) u[mr] = s;
+      if (lane == 0) u[P.map[r]] = s;
     }
     __syncthreads();
   };
@@ -499,22 +504,22 @@ __device__ __forceinline__ void vcycle_tail_body(const TailParams<T>& P, const d
     const T* ec = su + P.off[k + 1];
     const int* aux = sa + P.off[k];
     const int* auxc = sa + P.off[k + 1];
-    NodeWalk w(L.n, L.dim, tid, nt);
+    NodeWalk<DIM> w(L.n, tid, nt);
     for (int i = tid; i < L.N; i += nt, w.advance()) {
       if (aux[i] == -2) continue;
       const int I[3] = {w.i0 >> 1, w.i1 >> 1, w.i2 >> 1};
       const int sg[3] = {(w.i0 & 1) ? 1 : -1, (w.i1 & 1) ? 1 : -1, (w.i2 & 1) ? 1 : -1};
       T acc = 0;
       int cnt = 0;
-      const int nsel = 1 << L.dim;
+      constexpr int nsel = 1 << DIM;
       for (int sel = 0; sel < nsel; ++sel) {
         int c[3];
         T wgt = 1;
         bool inb = true;
         for (int q = 0; q < 3; ++q) {
           const int b = (sel >> q) & 1;
-          c[q] = q < L.dim ? I[q] + b * sg[q] : 0;
-          if (q < L.dim) {
+          c[q] = q < DIM ? I[q] + b * sg[q] : 0;
+          if (q < DIM) {
             if (c[q] < 0 || c[q] >= C.n) inb = false;
             wgt *= b ? (T)0.25 : (T)0.75;
           }
@@ -587,9 +592,9 @@ __device__ __forceinline__ void vcycle_tail_body(const TailParams<T>& P, const d
   }
 }
 
-template <typename T>
+template <typename T, int DIM>
 __global__ void __launch_bounds__(kTailThreads) k_vcycle_tail(TailParams<T> P) {
-  vcycle_tail_body<T>(P, P.v, P.vscale, P.z);
+  vcycle_tail_body<T, DIM>(P, P.v, P.vscale, P.z);
 }
 
 }  // namespace iim

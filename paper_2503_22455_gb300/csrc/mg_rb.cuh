@@ -83,7 +83,8 @@ constexpr size_t rb_smem_bytes() {
 }
 
 template <typename T, int NW, int RW, bool UP>
-__global__ void __launch_bounds__(NW * 32, (NW == 16 ? 2 : 4)) k_mg2d_rb(Rb2DParams<T> P) {
+// two-row windows fit in 40 registers (no spills): 1536 threads per SM; four-row windows would spill there
+__global__ void __launch_bounds__(NW * 32, RW == 2 ? 1536 / (NW * 32) : 1024 / (NW * 32)) k_mg2d_rb(Rb2DParams<T> P) {
   constexpr int SY = NW * RW, TY = SY - 2 * kRbHalo;
   static_assert(RW % 2 == 0, "a lane's rows come in pairs (the 2x2 restriction)");
   static_assert(SY > 2 * kRbHalo, "the window must be taller than its two halos");

@@ -7,6 +7,7 @@
 // (Neumann, Sec. 3.3); a dense direct solve on the coarsest level.  Interface
 // problems run on lap(u) = f/beta per phase (Sec. 3.3): the FP64 Krylov vector
 // is divided by beta_sigma when it enters the FP32 hierarchy.
+#include <algorithm>
 #include <utility>
 
 #include "engine.cuh"
@@ -200,31 +201,29 @@ __global__ void k_bridge_out(GridView g, const T* __restrict__ u, double* __rest
 // dense coarse matrix (row major, nu x nu) from the level's stencil
 template <typename T>
 __global__ void k_coarse_assemble(LevelView<double> L, const int32_t* __restrict__ map, const int* __restrict__ nu_dev,
-                                  int cap, const int32_t* __restrict__ inv, T* __restrict__ A, int aug) {
-  // cap x cap system, cap = the coarsest level's node count (+1 when augmented), so that its
-  // size does not depend on the geometry: rows r < nu (the level's unknowns, counted on the
-  // device) the SW operator; rows nu <= r < cap - aug the identity (slots no unknown uses);
-  // augmented (pure Neumann, Sec. 2.3): the last row and column of ones over the unknowns
-  // and a zero corner
+                                  int ld, const int32_t* __restrict__ inv, T* __restrict__ A, int aug, int* status) {
+  // The coarse system of the current set-up in the leading n x n block (n = nu + aug, nu the
+  // coarsest level's unknowns, counted on the device) of an array of fixed stride ld (the
+  // level's node count + aug), so that a later set-up with another geometry needs no other
+  // size: rows r < nu the SW operator; augmented (pure Neumann, Sec. 2.3): a last column and
+  // row of ones over the unknowns and a zero corner
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= cap) return;
-  const int nu = *nu_dev;
-  const int ia = cap - 1;
-  for (int c = 0; c < cap; ++c) A[(size_t)r * cap + c] = (T)0;
-  if (aug && r == ia) {
-    for (int c = 0; c < nu; ++c) A[(size_t)r * cap + c] = 1;
+  const int nu = *nu_dev, n = nu + aug;
+  if (nu < 0 || n > ld) {              // more unknowns than the system has room for
+    if (r == 0) set_status(status, IIM_ERR_CAPACITY);
     return;
   }
-  if (r >= nu) {
-    A[(size_t)r * cap + r] = 1;
+  if (r >= n) return;
+  for (int c = 0; c < n; ++c) A[(size_t)r * ld + c] = (aug && c == nu && r < nu) ? (T)1 : (T)0;
+  if (r == nu) {                       // the augmentation row
+    for (int c = 0; c < nu; ++c) A[(size_t)r * ld + c] = 1;
     return;
   }
-  if (aug) A[(size_t)r * cap + ia] = 1;
   int64_t i = map[r];
   int a = L.aux[i];
   int m[3];
   idx3(L.g, i, m);
-  A[(size_t)r * cap + r] = (T)diag_of(L, -2.0 * L.g.dim / (L.g.h * L.g.h), a);
+  A[(size_t)r * ld + r] = (T)diag_of(L, -2.0 * L.g.dim / (L.g.h * L.g.h), a);
   const GridView& g = L.g;
   for (int ax = 0; ax < g.dim; ++ax) {
     int64_t st = ax == 0 ? 1 : (ax == 1 ? (int64_t)g.n : (int64_t)g.n * g.n);
@@ -234,7 +233,7 @@ __global__ void k_coarse_assemble(LevelView<double> L, const int32_t* __restrict
       double cf = a == -1 ? 1.0 / (g.h * g.h) : tabv(L, a, (s < 0 ? 1 : 2) + 2 * ax);
       if (cf == 0.0) continue;
       int col = inv[i + s * st];
-      if (col >= 0) A[(size_t)r * cap + col] = (T)cf;
+      if (col >= 0) A[(size_t)r * ld + col] = (T)cf;
     }
   }
 }
@@ -254,25 +253,32 @@ __global__ void k_unknown_flag(GridView g, const int32_t* __restrict__ aux, int3
   if (i < g.N) flag[i] = aux[i] != -2;
 }
 
-// LU with partial pivoting (one CTA; the matrix is staged in shared memory when it
-// fits), then the explicit inverse, one warp per column.
+// LU with partial pivoting (one CTA), then the explicit inverse, of the leading n x n block
+// (n read on the device) of the stride-ld array Ag; the inverse goes to inv with stride ld.
+// With room for it (smem_elems elements of dynamic shared memory) the matrix, and then also
+// the inverse, are worked on in shared memory (stride n).
 template <typename T>
-__global__ void k_coarse_lu(T* __restrict__ Ag, int nu, int32_t* __restrict__ piv, T* __restrict__ inv, int* status,
-                            int in_smem) {
+__global__ void k_coarse_lu(T* __restrict__ Ag, int ld, const int* __restrict__ nu_dev, int aug,
+                            int32_t* __restrict__ piv, T* __restrict__ inv, int* status, size_t smem_elems) {
   extern __shared__ unsigned char smraw[];
   __shared__ int s_p;
   __shared__ T s_best[32];
   __shared__ int s_bi[32];
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int nu = *nu_dev + aug;           // the system's dimension (the name of the loops below)
+  if (nu <= 0 || nu > ld) return;         // out of range: reported by k_coarse_assemble
+  const size_t nn = (size_t)nu * nu;
+  const int in_smem = 2 * nn <= smem_elems ? 2 : (nn <= smem_elems ? 1 : 0);
+  const int la = in_smem ? nu : ld;       // stride of the working copy
   T* A = in_smem ? (T*)smraw : Ag;
   if (in_smem)
-    for (int e = tid; e < nu * nu; e += nt) A[e] = Ag[e];
+    for (size_t e = tid; e < nn; e += nt) A[e] = Ag[(e / nu) * ld + e % nu];
   __syncthreads();
   for (int k = 0; k < nu; ++k) {
     T best = -1;
     int bi = k;
     for (int r = k + tid; r < nu; r += nt) {
-      T v = fabs(A[(size_t)r * nu + k]);
+      T v = fabs(A[(size_t)r * la + k]);
       if (v > best) { best = v; bi = r; }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -295,29 +301,29 @@ __global__ void k_coarse_lu(T* __restrict__ Ag, int nu, int32_t* __restrict__ pi
     const int p = s_p;
     if (p != k)
       for (int c = tid; c < nu; c += nt) {
-        T t = A[(size_t)k * nu + c];
-        A[(size_t)k * nu + c] = A[(size_t)p * nu + c];
-        A[(size_t)p * nu + c] = t;
+        T t = A[(size_t)k * la + c];
+        A[(size_t)k * la + c] = A[(size_t)p * la + c];
+        A[(size_t)p * la + c] = t;
       }
     __syncthreads();
-    const T d = A[(size_t)k * nu + k];
+    const T d = A[(size_t)k * la + k];
     const int rem = nu - k - 1;
-    for (int r = k + 1 + tid; r < nu; r += nt) A[(size_t)r * nu + k] /= d;
+    for (int r = k + 1 + tid; r < nu; r += nt) A[(size_t)r * la + k] /= d;
     __syncthreads();
     for (int e = tid; e < rem * rem; e += nt) {
       int r = k + 1 + e / rem, c = k + 1 + e % rem;
-      A[(size_t)r * nu + c] -= A[(size_t)r * nu + k] * A[(size_t)k * nu + c];
+      A[(size_t)r * la + c] -= A[(size_t)r * la + k] * A[(size_t)k * la + c];
     }
     __syncthreads();
   }
   if (in_smem)
-    for (int e = tid; e < nu * nu; e += nt) Ag[e] = A[e];
+    for (size_t e = tid; e < nn; e += nt) Ag[(e / nu) * ld + e % nu] = A[e];
   __syncthreads();
   if (in_smem == 2) {
     // inverse in shared memory: X = U^-1 L^-1 P, all columns at once, one row per step.
     // Column j is handled by G consecutive lanes that split the row's dot product.
-    T* X = A + (size_t)nu * nu;
-    for (int e = tid; e < nu * nu; e += nt) X[e] = 0;
+    T* X = A + nn;
+    for (size_t e = tid; e < nn; e += nt) X[e] = 0;
     __syncthreads();
     for (int j = tid; j < nu; j += nt) {
       // P applied to e_j: follow the row swaps in factorisation order
@@ -354,33 +360,33 @@ __global__ void k_coarse_lu(T* __restrict__ Ag, int nu, int32_t* __restrict__ pi
       }
       __syncthreads();
     }
-    for (int e = tid; e < nu * nu; e += nt) inv[e] = X[e];
+    for (size_t e = tid; e < nn; e += nt) inv[(e / nu) * ld + e % nu] = X[e];
     return;
   }
-  // inverse from global memory: solve L U x = P e_j, one warp per column
+  // inverse from the factors in global memory (stride ld): solve L U x = P e_j, one warp per column
   const int lane = tid & 31, wid = tid >> 5, nw = nt / 32;
   for (int j = wid; j < nu; j += nw) {
-    T* x = inv + (size_t)j;      // column j of the (row major) inverse, stride nu
-    for (int r = lane; r < nu; r += 32) x[(size_t)r * nu] = (r == j) ? (T)1 : (T)0;
+    T* x = inv + (size_t)j;      // column j of the (row major, stride ld) inverse
+    for (int r = lane; r < nu; r += 32) x[(size_t)r * ld] = (r == j) ? (T)1 : (T)0;
     __syncwarp();
     if (lane == 0)
       for (int k = 0; k < nu; ++k) {
         int p = piv[k];
-        if (p != k) { T t = x[(size_t)k * nu]; x[(size_t)k * nu] = x[(size_t)p * nu]; x[(size_t)p * nu] = t; }
+        if (p != k) { T t = x[(size_t)k * ld]; x[(size_t)k * ld] = x[(size_t)p * ld]; x[(size_t)p * ld] = t; }
       }
     __syncwarp();
     for (int r = 0; r < nu; ++r) {                 // forward, unit lower
       T part = 0;
-      for (int c = lane; c < r; c += 32) part += A[(size_t)r * nu + c] * x[(size_t)c * nu];
+      for (int c = lane; c < r; c += 32) part += Ag[(size_t)r * ld + c] * x[(size_t)c * ld];
       for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-      if (lane == 0) x[(size_t)r * nu] -= part;
+      if (lane == 0) x[(size_t)r * ld] -= part;
       __syncwarp();
     }
     for (int r = nu - 1; r >= 0; --r) {            // backward
       T part = 0;
-      for (int c = r + 1 + lane; c < nu; c += 32) part += A[(size_t)r * nu + c] * x[(size_t)c * nu];
+      for (int c = r + 1 + lane; c < nu; c += 32) part += Ag[(size_t)r * ld + c] * x[(size_t)c * ld];
       for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-      if (lane == 0) x[(size_t)r * nu] = (x[(size_t)r * nu] - part) / A[(size_t)r * nu + r];
+      if (lane == 0) x[(size_t)r * ld] = (x[(size_t)r * ld] - part) / Ag[(size_t)r * ld + r];
       __syncwarp();
     }
   }
@@ -440,7 +446,10 @@ TailParams<T> make_tail_params(Problem& P, size_t l0, T* u_out, size_t smem_limi
   tp.top_visits = 1;
   tp.neumann = P.desc.bc == IIM_BC_NEUMANN;
   tp.ld = P.coarse_n;
+  tp.nu_dev = P.d_counts + kCountCoarse;
+  tp.aug = P.aug;
   tp.map = P.coarse_map;
+  tp.status = P.d_status + 1;
   const T* inv = (const T*)(sizeof(T) == 8 ? (void*)P.coarse_lu64 : (void*)P.coarse_lu32);
   tp.inv = inv + (size_t)P.coarse_n * P.coarse_n;
   tp.v = nullptr;
@@ -465,8 +474,13 @@ static void launch_tail(Problem& P, size_t l0, const double* v, const double* vs
   tp.v = v;
   tp.vscale = vscale;
   tp.z = z;
-  if (smem > 48 * 1024) smem_optin((const void*)k_vcycle_tail<T>);
-  IIM_LAUNCH(k_vcycle_tail<T>, 1, kTailThreads, smem, s, tp);
+  if (P.g.dim == 2) {
+    if (smem > 48 * 1024) smem_optin((const void*)k_vcycle_tail<T, 2>);
+    IIM_LAUNCH((k_vcycle_tail<T, 2>), 1, kTailThreads, smem, s, tp);
+  } else {
+    if (smem > 48 * 1024) smem_optin((const void*)k_vcycle_tail<T, 3>);
+    IIM_LAUNCH((k_vcycle_tail<T, 3>), 1, kTailThreads, smem, s, tp);
+  }
 }
 
 template <typename T, int TX, int TY>
@@ -723,24 +737,20 @@ void mg_coarse_factor(Problem& P, cudaStream_t s) {
   IIM_LAUNCH(k_coarse_map, ceil_div(C.g.N, Tn), Tn, 0, s, C.g, C.aux, C.idx, P.coarse_map, inv);
   LevelView<double> V = view<double>(C);
   const int* nu = P.d_counts + kCountCoarse;
+  // dynamic shared memory of the factorisation: the matrix and its inverse when they fit
+  auto factor = [&](auto* A, auto* kernel, size_t esz) {
+    size_t sm = std::min((size_t)2 * cn * cn * esz, (size_t)200 * 1024);
+    smem_optin((const void*)kernel);
+    IIM_LAUNCH(kernel, 1, 1024, sm, s, A, cn, nu, P.aug, P.coarse_piv, A + (size_t)cn * cn, P.d_status, sm / esz);
+  };
   if (P.opt.mg_precision == IIM_MG_FP64) {
     IIM_LAUNCH(k_coarse_assemble<double>, ceil_div(cn, 128), 128, 0, s, V, P.coarse_map, nu, cn, inv, P.coarse_lu64,
-               P.aug);
-    size_t sm = sizeof(double) * (size_t)cn * cn;
-    int in_smem = sm <= 200 * 1024;
-    if (2 * sm <= 200 * 1024) { in_smem = 2; sm *= 2; }
-    if (in_smem) smem_optin((const void*)k_coarse_lu<double>);
-    IIM_LAUNCH(k_coarse_lu<double>, 1, 1024, in_smem ? sm : 0, s, P.coarse_lu64, cn, P.coarse_piv,
-               P.coarse_lu64 + (size_t)cn * cn, P.d_status, in_smem);
+               P.aug, P.d_status);
+    factor(P.coarse_lu64, k_coarse_lu<double>, sizeof(double));
   } else {
     IIM_LAUNCH(k_coarse_assemble<float>, ceil_div(cn, 128), 128, 0, s, V, P.coarse_map, nu, cn, inv, P.coarse_lu32,
-               P.aug);
-    size_t sm = sizeof(float) * (size_t)cn * cn;
-    int in_smem = sm <= 200 * 1024;
-    if (2 * sm <= 200 * 1024) { in_smem = 2; sm *= 2; }
-    if (in_smem) smem_optin((const void*)k_coarse_lu<float>);
-    IIM_LAUNCH(k_coarse_lu<float>, 1, 1024, in_smem ? sm : 0, s, P.coarse_lu32, cn, P.coarse_piv,
-               P.coarse_lu32 + (size_t)cn * cn, P.d_status, in_smem);
+               P.aug, P.d_status);
+    factor(P.coarse_lu32, k_coarse_lu<float>, sizeof(float));
   }
 }
 
@@ -786,7 +796,11 @@ __global__ void __launch_bounds__(kTailThreads) k_eng_tail(EngArgs A) {
     const SlotDev& s = A.slots[si];
     if (s.role != kRoleIter) return;
     const bool top = s.nfine == 0;
-    vcycle_tail_body<float>(s.tail, top ? eng_vj(s) : nullptr, top ? &s.sc->inv_norm[s.j] : nullptr,
+    if (s.dim == 2)
+      vcycle_tail_body<float, 2>(s.tail, top ? eng_vj(s) : nullptr, top ? &s.sc->inv_norm[s.j] : nullptr,
+                            top ? eng_zj(s) : nullptr);
+    else
+      vcycle_tail_body<float, 3>(s.tail, top ? eng_vj(s) : nullptr, top ? &s.sc->inv_norm[s.j] : nullptr,
                             top ? eng_zj(s) : nullptr);
   });
 }

@@ -917,56 +917,22 @@ __global__ void __launch_bounds__(32) k_fit_quad(FitParams P, QuadFitSmem Lq, in
       beta[k] = bk;
     }
     __syncwarp();
-    // The lane's trailing columns j = k + 1 + ql + 8 i (i < NJ) are updated together: each
-    // element of the reflector is loaded once for all of them, and the 2 NJ products run as
-    // independent chains.  Every column keeps its own order of operations (even rows into
-    // d0, odd rows into d1), so the result does not depend on how many columns a lane has.
-    constexpr int NJ = (M + 7) / 8;
-    double* vj[NJ];
-    bool on[NJ];
-    double d0[NJ], d1[NJ];
-#pragma unroll
-    for (int i = 0; i < NJ; ++i) {
-      const int j = k + 1 + ql + 8 * i;
-      on[i] = j < M;
-      vj[i] = V + (size_t)(on[i] ? j : k) * LDQ;
-      d0[i] = 0.0;
-      d1[i] = 0.0;
-    }
-    int r = k;
-    for (; r + 1 < m; r += 2) {
-      const double a0 = vk[r], a1 = vk[r + 1];
-#pragma unroll
-      for (int i = 0; i < NJ; ++i)
-        if (on[i]) {
-          d0[i] = fma(a0, vj[i][r], d0[i]);
-          d1[i] = fma(a1, vj[i][r + 1], d1[i]);
-        }
-    }
-    if (r < m) {
-      const double a0 = vk[r];
-#pragma unroll
-      for (int i = 0; i < NJ; ++i)
-        if (on[i]) d0[i] = fma(a0, vj[i][r], d0[i]);
-    }
-    double sc[NJ];
-#pragma unroll
-    for (int i = 0; i < NJ; ++i) sc[i] = (d0[i] + d1[i]) * bk;
-    r = k;
-    for (; r + 1 < m; r += 2) {
-      const double a0 = vk[r], a1 = vk[r + 1];
-#pragma unroll
-      for (int i = 0; i < NJ; ++i)
-        if (on[i]) {
-          vj[i][r] = fma(-sc[i], a0, vj[i][r]);
-          vj[i][r + 1] = fma(-sc[i], a1, vj[i][r + 1]);
-        }
-    }
-    if (r < m) {
-      const double a0 = vk[r];
-#pragma unroll
-      for (int i = 0; i < NJ; ++i)
-        if (on[i]) vj[i][r] = fma(-sc[i], a0, vj[i][r]);
+    for (int j = k + 1 + ql; j < M; j += 8) {
+      double* vj = V + (size_t)j * LDQ;
+      double d0 = 0.0, d1 = 0.0;
+      int r = k;
+      for (; r + 1 < m; r += 2) {
+        d0 = fma(vk[r], vj[r], d0);
+        d1 = fma(vk[r + 1], vj[r + 1], d1);
+      }
+      if (r < m) d0 = fma(vk[r], vj[r], d0);
+      const double sc = (d0 + d1) * bk;
+      r = k;
+      for (; r + 1 < m; r += 2) {
+        vj[r] = fma(-sc, vk[r], vj[r]);
+        vj[r + 1] = fma(-sc, vk[r + 1], vj[r + 1]);
+      }
+      if (r < m) vj[r] = fma(-sc, vk[r], vj[r]);
     }
     __syncwarp();
   }
