@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--ticks-per-run", type=int, default=4, help="serve: engine ticks between admissions")
     ap.add_argument("--slots", type=int, default=256, help="serve: problems resident at once at most")
     ap.add_argument("--create-threads", type=int, default=16, help="serve: host threads creating requests")
+    ap.add_argument("--data-threads", type=int, default=8,
+                    help="serve: client threads preparing request data (0: on the loop's thread)")
     ap.add_argument("--serve-deadline", type=float, default=300.0,
                     help="serve: fail (with the requests' states) when requests are outstanding after this many s")
     ap.add_argument("--serve-mode", type=int, default=1, choices=[0, 1],
@@ -345,7 +347,7 @@ def run_batch(args):
 
 
 def serve_run(iim, torch, count, rate, seed, slots=256, ticks_per_run=4, mode=1, create_threads=16,
-              deadline_s=300.0, note=None):
+              deadline_s=300.0, note=None, data_threads=8):
     """A Poisson request stream (mean rate ``rate``/s, ``count`` requests, seeded): 2D n
     128..1024 (stars, ellipses), 3D n 64..192 (ellipsoids, perturbed spheres), interior
     Dirichlet / exterior Neumann, admitted by a budget of 60% of free device memory into
@@ -373,7 +375,8 @@ def serve_run(iim, torch, count, rate, seed, slots=256, ticks_per_run=4, mode=1,
                    create_threads=create_threads)
     arrivals = [(t, iim.desc_from_spec(sp), sp) for t, sp in trace]
     host = {}
-    out, wall = iim.serve(S, arrivals, set_data, realtime=True, timings=host, deadline_s=deadline_s, progress=note)
+    out, wall = iim.serve(S, arrivals, set_data, realtime=True, timings=host, deadline_s=deadline_s, progress=note,
+                          data_threads=data_threads)
     stats = S.stats()
     S.close()
     lat = np.array([o[2] for o in out.values()])
@@ -385,7 +388,8 @@ def serve_run(iim, torch, count, rate, seed, slots=256, ticks_per_run=4, mode=1,
         "requests": count, "rate_per_s": rate, "seed": seed, "offered_rate": count / trace[-1][0],
         "completed": len(ok), "failed": len(err), "failures": err[:10], "budget_bytes": budget,
         "peak_bytes": stats["peak_bytes"], "solver": "batched engine" if mode == 0 else
-        "per-request solve graphs on streams", "create_threads": create_threads,
+        "per-request solve graphs on streams", "create_threads": create_threads, "client_data_threads": data_threads,
+        "problem_reuse": False,
         "host_seconds": {"loop_step": host["step_s"], "client_set_data": host["set_data_s"], "take": host["take_s"],
                          "server_copy_out": stats["host_copy_s"], "server_create_threads": stats["host_create_s"]},
         "requests_2d": sum(1 for _, sp in trace if sp.dim == 2), "requests_3d": sum(1 for _, sp in trace if sp.dim == 3),
@@ -409,7 +413,8 @@ def run_serve(args):
     clocks = Clocks(local)
     clocks.start()
     r = serve_run(iim, torch, count, args.rate, 22455 + rank, slots=args.slots, ticks_per_run=args.ticks_per_run,
-                  mode=args.serve_mode, create_threads=args.create_threads, deadline_s=args.serve_deadline, note=note)
+                  mode=args.serve_mode, create_threads=args.create_threads, deadline_s=args.serve_deadline, note=note,
+                  data_threads=args.data_threads)
     clk = clocks.stop()
     res = {
         "metric": "IIM serving: solves/s and p50/p99 latency (s), rel. resid 1e-10", "value": r["solves_per_s"],
@@ -742,6 +747,9 @@ def run_ours(args):
                                                 timeout_s=420)
         other["serve_poisson_400"] = child_line(["--workload", "serve", "--count", "400", "--serve-deadline", "240"],
                                                 timeout_s=420)
+        # the same request mix offered below the loop's capacity: latency when it is not overloaded
+        other["serve_poisson_400_rate20"] = child_line(["--workload", "serve", "--count", "400", "--rate", "20",
+                                                        "--serve-deadline", "120"], timeout_s=300)
     e2e = None
     if not args.no_e2e:
         e2e = e2e_run(probs, torch, inputs, Wm, K, world, main)

@@ -366,13 +366,15 @@ void iim_server_destroy(iim_server* s);
  * and independent of the other requests. */
 iim_status iim_server_set_mode(iim_server* s, int mode);
 
-/* Reuse of retired problems (on by default): a finished request's problem (its allocation,
+/* Reuse of retired problems (off by default): a finished request's problem (its allocation,
  * stream and solve graph) is kept, its bytes still counted against the budget, and a later
  * request of the same kind (dimension, n, conditions, outer box, order, geometry kind, side,
  * beta+, beta-; closed-form bodies only) takes it and re-runs its set-up in place with its own
  * geometry parameters, instead of creating a problem.  Kept problems are freed, oldest first,
  * when a new request needs their memory, or when reuse is switched off.  Results are those of
- * a fresh problem (the set-up leaves nothing of the earlier geometry behind). */
+ * a fresh problem (the set-up leaves nothing of the earlier geometry behind).  Off by default:
+ * serving streams with many reuses have stalled (kernels stopped completing on most streams,
+ * one of them a reused problem's set-up), and the cause is not known. */
 iim_status iim_server_set_pooling(iim_server* s, int on);
 /* Requests that took a kept problem, requests created afresh, kept problems freed for room,
  * and problems kept now.  Any pointer may be NULL. */

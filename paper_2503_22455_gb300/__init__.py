@@ -343,6 +343,9 @@ class Problem:
     def set_data(self, f, g=None, j0=None, j1=None, box=None):
         self._foreign_stream_sync(True)
         _check(load().iim_set_data(self.h, _ptr(f), _ptr(g), _ptr(j0), _ptr(j1), _ptr(box)), "iim_set_data")
+        # a view's problem reads the tensors on a stream torch does not order: wait for the
+        # reads, so that the caller may free or reuse them (from any thread) on return
+        self._foreign_stream_sync(False)
 
     def apply(self, u, include_data=False, out=None):
         w = out if out is not None else self._empty(self.N)
@@ -523,7 +526,7 @@ class Server:
     """Request loop over an engine (see iim.h): submit, step, set data, take."""
 
     def __init__(self, options: Options | None = None, budget_bytes: int = 1 << 34, max_slots: int = 64,
-                 ticks_per_run: int = 4, cap: int = 4096, create_threads: int = 8, mode: int = 0, pooling=True):
+                 ticks_per_run: int = 4, cap: int = 4096, create_threads: int = 8, mode: int = 0, pooling=False):
         lib = load()
         self.options = options or default_options()
         h = ctypes.c_void_p()
@@ -601,7 +604,7 @@ SERVER_STATES = ("queued", "creating", "need_data", "ready", "running", "retired
 
 
 def serve(server: Server, arrivals, set_data, realtime=True, idle_sleep=0.0, timings=None, deadline_s=None,
-          progress=None, progress_every_s=5.0):
+          progress=None, progress_every_s=5.0, data_threads=0):
     """Drive a server through a stream of requests.
 
     arrivals: list of (arrival time in seconds from now, Desc, user object), sorted by time;
@@ -611,9 +614,15 @@ def serve(server: Server, arrivals, set_data, realtime=True, idle_sleep=0.0, tim
     seconds spent in step, set_data and take.  With deadline_s, a TimeoutError naming the
     requests' states is raised when requests are still outstanding after that many
     seconds; progress(elapsed_s, taken, outstanding, server stats) is called every
-    progress_every_s seconds.
+    progress_every_s seconds.  With data_threads > 0, set_data runs on that many client
+    threads (each call touches only its own request's problem) and the loop marks a request
+    ready once its call has returned, so the loop keeps admitting and collecting meanwhile;
+    an exception raised by set_data is raised here.
     """
     import time
+    from concurrent.futures import ThreadPoolExecutor
+    workers = ThreadPoolExecutor(data_threads) if data_threads > 0 else None
+    busy = {}                     # request id -> its set_data call on a client thread
     t0 = time.perf_counter()
     pending = list(arrivals)
     k = 0
@@ -639,7 +648,14 @@ def serve(server: Server, arrivals, set_data, realtime=True, idle_sleep=0.0, tim
         need, fin = server.step()
         b = time.perf_counter()
         for rid in need:
-            set_data(server.problem(rid), users[rid])
+            if workers is None:
+                set_data(server.problem(rid), users[rid])
+                server.data_ready(rid)
+            else:
+                busy[rid] = workers.submit(set_data, server.problem(rid), users[rid])
+        done = [rid for rid, fu in busy.items() if fu.done()]
+        for rid in done:
+            busy.pop(rid).result()
             server.data_ready(rid)
         c = time.perf_counter()
         for rid in fin:
@@ -650,8 +666,13 @@ def serve(server: Server, arrivals, set_data, realtime=True, idle_sleep=0.0, tim
         t_step += b - a
         t_data += c - b
         t_take += d - c
-        if idle_sleep and not need and not fin:
-            time.sleep(idle_sleep)
+        if not need and not fin and not done:
+            if idle_sleep:
+                time.sleep(idle_sleep)
+            elif busy:
+                time.sleep(2e-4)          # leave the interpreter to the client threads
+    if workers is not None:
+        workers.shutdown(wait=True)
     if timings is not None:
         timings.update({"step_s": t_step, "set_data_s": t_data, "take_s": t_take})
     return out, time.perf_counter() - t0

@@ -154,7 +154,7 @@ struct Problem {
   int red_blocks = 0;
   // multigrid
   std::vector<Level> lv;
-  int coarse_nu = 0;              // unknowns on the coarsest level at creation (information only)
+  int coarse_nu = 0;              // unknowns on the coarsest level at creation (sizes the LU's shared memory)
   int coarse_n = 0;               // size of the padded coarse system: the coarsest level's nodes (+1 when augmented)
   int aug = 0;                    // pure Neumann: the augmented system of Sec. 2.3 (one more unknown)
   int32_t* coarse_map = nullptr;  // [coarse_n] node of each slot of the coarse system, -1 if none

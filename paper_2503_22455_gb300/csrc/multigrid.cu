@@ -737,9 +737,13 @@ void mg_coarse_factor(Problem& P, cudaStream_t s) {
   IIM_LAUNCH(k_coarse_map, ceil_div(C.g.N, Tn), Tn, 0, s, C.g, C.aux, C.idx, P.coarse_map, inv);
   LevelView<double> V = view<double>(C);
   const int* nu = P.d_counts + kCountCoarse;
-  // dynamic shared memory of the factorisation: the matrix and its inverse when they fit
+  // dynamic shared memory of the factorisation: room for the matrix and its inverse at the
+  // unknown count of the creation's geometry with a quarter more (a later set-up with more
+  // unknowns than that works on them in global memory instead); never more than the padded
+  // system or 200 KB, so that small factorisations leave the SM to other kernels
   auto factor = [&](auto* A, auto* kernel, size_t esz) {
-    size_t sm = std::min((size_t)2 * cn * cn * esz, (size_t)200 * 1024);
+    const size_t nb = std::min((size_t)cn, (size_t)P.coarse_nu + P.coarse_nu / 4 + 8 + P.aug);
+    size_t sm = std::min((size_t)2 * nb * nb * esz, (size_t)200 * 1024);
     smem_optin((const void*)kernel);
     IIM_LAUNCH(kernel, 1, 1024, sm, s, A, cn, nu, P.aug, P.coarse_piv, A + (size_t)cn * cn, P.d_status, sm / esz);
   };

@@ -95,7 +95,7 @@ struct Server {
   iim_options opt;
   std::vector<PoolEntry> pool;   // retired problems (their bytes stay counted in in_use)
   int64_t pool_stamp = 0, pool_hits = 0, pool_misses = 0, pool_evicted = 0;
-  bool pooling = true;
+  bool pooling = false;          // reuse of retired problems: off unless the caller asks
   size_t budget = 0, in_use = 0, peak = 0;
   int max_slots = 0, ticks_per_run = 1;
   iim_engine* engine = nullptr;

@@ -25,11 +25,12 @@ def env():
     return need_gpu()
 
 
-def _serve(iim, specs, budget, ticks_per_run=3, mode=0, pooling=True, pool_stats=None):
+def _serve(iim, specs, budget, ticks_per_run=3, mode=0, pooling=True, pool_stats=None, data_threads=0):
     S = iim.Server(iim.default_options(), budget_bytes=budget, max_slots=8, ticks_per_run=ticks_per_run, mode=mode,
                    pooling=pooling)
     arrivals = [(0.0, iim.desc_from_spec(sp), sp) for sp in specs]
-    out, wall = iim.serve(S, arrivals, lambda view, sp: set_gpu_data(view, sp), realtime=False)
+    out, wall = iim.serve(S, arrivals, lambda view, sp: set_gpu_data(view, sp), realtime=False,
+                          data_threads=data_threads)
     stats = S.stats()
     if pool_stats is not None:
         pool_stats.update(S.pool_stats())
@@ -126,3 +127,17 @@ def test_kept_problems_give_the_results_of_fresh_ones(env, mode):
     for (xa, ia, _, sa, sp), (xb, ib, _, sb, _) in zip(kept, fresh):
         assert sa == 0 and sb == 0 and ia.converged and ib.converged, sp.name
         assert ia.iters == ib.iters and np.array_equal(xa, xb), (sp.geometry, ia.as_dict(), ib.as_dict())
+
+
+@pytest.mark.parametrize("mode", [1, 0])
+def test_client_data_threads_give_the_same_results(env, mode):
+    """Request data set on four client threads while the loop keeps stepping: every result
+    equals, bit for bit, the result with the data set on the loop's own thread."""
+    torch, iim = env
+    specs = [sp for _, sp in _trace()]
+    threaded, _ = _serve(iim, specs, 1 << 36, mode=mode, data_threads=4)
+    inline, _ = _serve(iim, specs, 1 << 36, mode=mode, data_threads=0)
+    assert len(threaded) == len(inline) == len(specs)
+    for (xa, ia, _, sa, sp), (xb, ib, _, sb, _) in zip(threaded, inline):
+        assert sa == 0 and sb == 0 and ia.converged, sp.name
+        assert ia.iters == ib.iters and np.array_equal(xa, xb), sp.name
