@@ -288,14 +288,19 @@ __global__ void k_coarse_lu(T* __restrict__ Ag, int ld, const int* __restrict__ 
     }
     if ((tid & 31) == 0) { s_best[tid >> 5] = best; s_bi[tid >> 5] = bi; }
     __syncthreads();
-    if (tid == 0) {
-      T b0 = s_best[0];
-      int i0 = s_bi[0];
-      for (int w = 1; w < nt / 32; ++w)
-        if (s_best[w] > b0 || (s_best[w] == b0 && s_bi[w] < i0)) { b0 = s_best[w]; i0 = s_bi[w]; }
-      s_p = i0;
-      piv[k] = i0;
-      if (!(b0 > 0)) set_status(status, IIM_ERR_SINGULAR);
+    if (tid < 32) {                     // the warps' candidates, reduced by the first warp
+      T b0 = tid < nt / 32 ? s_best[tid] : (T)-1;
+      int i0 = tid < nt / 32 ? s_bi[tid] : nu;
+      for (int o = 16; o > 0; o >>= 1) {
+        T ob = __shfl_xor_sync(0xffffffffu, b0, o);
+        int oi = __shfl_xor_sync(0xffffffffu, i0, o);
+        if (ob > b0 || (ob == b0 && oi < i0)) { b0 = ob; i0 = oi; }
+      }
+      if (tid == 0) {
+        s_p = i0;
+        piv[k] = i0;
+        if (!(b0 > 0)) set_status(status, IIM_ERR_SINGULAR);
+      }
     }
     __syncthreads();
     const int p = s_p;

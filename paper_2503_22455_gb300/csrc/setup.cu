@@ -1218,7 +1218,9 @@ iim_status setup_geometry(Problem& P, bool size_only) {
   if (size_only) return IIM_OK;
   IIM_LAUNCH(k_compact, ceil_div(g.N * g.dim, T), T, 0, s, P.edge_flag, P.edge_id, g.N * g.dim, P.K_cap, P.cr_edge,
              P.d_status);
-  IIM_LAUNCH(k_crossings, ceil_div(P.K_cap, 128), 128, 0, s, P.geom, g, P.cr_edge, P.d_counts + 0, P.K_cap, P.phase,
+  // one warp per block: the root solves are FP64-pipe bound (16 clocks per warp instruction
+  // per SM), so a few thousand control points run fastest spread one warp per SM
+  IIM_LAUNCH(k_crossings, ceil_div(P.K_cap, 32), 32, 0, s, P.geom, g, P.cr_edge, P.d_counts + 0, P.K_cap, P.phase,
              P.cr_axis, P.cr_lo, P.cr_loplus, P.cr_t, P.cr_x, P.cr_n, P.cr_kappa, P.d_status);
   IIM_LAUNCH(k_curvature_check, ceil_div(P.K_cap, T), T, 0, s, P.cr_kappa, P.d_counts + 0, g.h, P.d_status);
   WalkParams W{g, P.w, P.q, P.desc.bc == IIM_BC_INTERFACE, P.desc.box_bc};
@@ -1327,7 +1329,7 @@ iim_status setup_levels(Problem& P, bool size_only) {
     if (size_only) continue;
     IIM_LAUNCH(k_compact, ceil_div(L.g.N, T), T, 0, P.stream, L.flag, L.idx, L.g.N, L.irr_cap, L.irr_node,
                P.d_status);
-    IIM_LAUNCH(k_sw_fill, ceil_div(L.irr_cap, 128), 128, 0, P.stream, S, L.phase, L.irr_node, P.d_counts + 2 + (int)l,
+    IIM_LAUNCH(k_sw_fill, ceil_div(L.irr_cap, 32), 32, 0, P.stream, S, L.phase, L.irr_node, P.d_counts + 2 + (int)l,
                L.irr_cap, L.aux, L.tab64, L.tab32, P.d_status);
   }
   return IIM_OK;
