@@ -25,6 +25,10 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# Many problems run on their own streams at once (8 solve graphs, 16 pool streams, up to 256
+# requests): more hardware work queues than the default 8 keep independent streams from
+# waiting on one another.  A per-process setting, read when CUDA starts.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 METRIC = "IIM solves/s to rel. resid 1e-10 (FP32-MG form)"
 WORKLOAD = "star_interface_1024_o6"
