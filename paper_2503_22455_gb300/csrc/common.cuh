@@ -497,4 +497,30 @@ void note_launches(int64_t k);         // a graph launch that runs k kernels
     ::iim::note_launch();                                                 \
   } while (0)
 
+// A launch that may begin before the previous kernel on the stream has finished
+// (programmatic dependent launch): the kernel must run pdl_wait() before it reads anything
+// the previous kernels write, and before it writes anything they read.  Used for the chain
+// of multigrid level kernels, whose prologues read only set-up data.
+#define IIM_LAUNCH_PDL(kernel_, grid_, block_, smem_, stream_, ...)                       \
+  do {                                                                                     \
+    cudaLaunchConfig_t cfg_ = {};                                                          \
+    cfg_.gridDim = dim3(grid_);                                                            \
+    cfg_.blockDim = dim3(block_);                                                          \
+    cfg_.dynamicSmemBytes = (smem_);                                                       \
+    cfg_.stream = (stream_);                                                               \
+    cudaLaunchAttribute at_[1];                                                            \
+    at_[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;                        \
+    at_[0].val.programmaticStreamSerializationAllowed = 1;                                 \
+    cfg_.attrs = at_;                                                                      \
+    cfg_.numAttrs = 1;                                                                     \
+    cudaLaunchKernelEx(&cfg_, kernel_, __VA_ARGS__);                                       \
+    ::iim::note_launch();                                                                  \
+  } while (0)
+
+// wait until the kernels this one depends on have finished and their writes are visible
+// (returns at once for a kernel launched without the programmatic attribute)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// let the next kernel on the stream start its prologue (it still waits for this one to finish)
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 }  // namespace iim

@@ -404,6 +404,10 @@ __device__ __forceinline__ void vcycle_tail_body(const TailParams<T>& P, const d
     }
   }
   auto table = [&](int k) -> const T* { return P.stage_tables ? st + P.toff[k] : P.L[k].tab; };
+  // the staging above reads set-up data only; the right-hand side below is written by the
+  // kernels before this one
+  pdl_trigger();
+  pdl_wait();
   {
     const LevelK<T>& L = P.L[0];
     const T vs = v_in ? (T)(vscale ? *vscale : 1.0) : (T)1;

@@ -109,69 +109,29 @@ __global__ void __launch_bounds__(NW * 32, RW == 2 ? 1536 / (NW * 32) : 1024 / (
   if (threadIdx.x == 0) s_nirr = 0;
 
   // ---------------------------------------------------------------- load
-  // every global load of the lane is issued before any of them is used
+  // Set-up data first (class codes, irregular rows and their table entries): this runs while
+  // the previous level kernel may still be finishing.  Then the data the previous kernels
+  // write (right-hand side, u), after pdl_wait().
   const int gx = x0 + 2 * lane;
   uchar2 cc[RW];
-  T f0[RW], f1[RW], u0[RW], u1[RW];
 #pragma unroll
   for (int j = 0; j < RW; ++j) {
     const int gy = y0 + warp * RW + j;
     const bool in = gy >= 0 && gy < n && gx >= 0 && gx < n;    // n even: gx + 1 < n too
-    const int64_t g = (int64_t)gy * n + gx;
-    cc[j] = make_uchar2(0, 0);
-    f0[j] = f1[j] = u0[j] = u1[j] = (T)0;
-    if (in) {
-      cc[j] = __ldg((const uchar2*)(cls + g));
-      if (finest_in) {
-        const double2 vv = __ldg((const double2*)(P.v + g));
-        f0[j] = (T)vv.x;
-        f1[j] = (T)vv.y;
-      } else {
-        const T2 ff = load_f2(P.f_in, g, P.f_bf16);
-        f0[j] = ff.x;
-        f1[j] = ff.y;
-      }
-      if (UP) {
-        const T2 uu = *(const T2*)(P.u_in + g);
-        u0[j] = uu.x;
-        u1[j] = uu.y;
-      }
-    }
+    cc[j] = in ? __ldg((const uchar2*)(cls + (int64_t)gy * n + gx)) : make_uchar2(0, 0);
   }
-  const T vs = finest_in ? (T)(P.vscale ? *P.vscale : 1.0) : (T)1;
-  __syncthreads();                    // s_nirr
-  T fr[RW], fb[RW], ur[RW], ub[RW];
   unsigned unk = 0, irr = 0;          // bit 2 j + c: cell of row j, colour c (0 red, 1 black)
 #pragma unroll
   for (int j = 0; j < RW; ++j) {
-    const int y = warp * RW + j, p = j & 1;
-    const uint8_t c0 = cc[j].x, c1 = cc[j].y;
-    T a0 = f0[j], a1 = f1[j];
-    if (finest_in) {
-      a0 = mul_rn(a0, mul_rn(vs, one_beta || (c0 & kClsPlus) ? P.inv_bp : P.inv_bm));
-      a1 = mul_rn(a1, mul_rn(vs, one_beta || (c1 & kClsPlus) ? P.inv_bp : P.inv_bm));
-    }
-    T b0 = u0[j], b1 = u1[j];
-    if (!(c0 & kClsUnknown)) a0 = b0 = 0;
-    if (!(c1 & kClsUnknown)) a1 = b1 = 0;
+    const int p = j & 1;
     // x = 2 lane is red when p = 0
-    const uint8_t cr = p ? c1 : c0, cb = p ? c0 : c1;
-    fr[j] = p ? a1 : a0;
-    fb[j] = p ? a0 : a1;
-    ur[j] = p ? b1 : b0;
-    ub[j] = p ? b0 : b1;
+    const uint8_t cr = p ? cc[j].y : cc[j].x, cb = p ? cc[j].x : cc[j].y;
     unk |= ((cr & kClsUnknown) ? 1u : 0u) << (2 * j);
     unk |= ((cb & kClsUnknown) ? 1u : 0u) << (2 * j + 1);
     irr |= ((cr & kClsIrregular) ? 1u : 0u) << (2 * j);
     irr |= ((cb & kClsIrregular) ? 1u : 0u) << (2 * j + 1);
-    if (finest_in && in_tile(y) && y0 + y < n && gx < n) {
-      // the finest level's right-hand side, for the up step
-      T2 st;
-      st.x = a0;
-      st.y = a1;
-      *(T2*)(P.f_out + (int64_t)(y0 + y) * n + gx) = st;
-    }
   }
+  __syncthreads();                    // s_nirr
   // irregular cells: a slot each (code < 0: past the staging capacity, read from the table)
 #pragma unroll
   for (int j = 0; j < RW; ++j) {
@@ -195,6 +155,59 @@ __global__ void __launch_bounds__(NW * 32, RW == 2 ? 1536 / (NW * 32) : 1024 / (
       const int a = __ldg(P.aux + sList[r]);
 #pragma unroll
       for (int k = 0; k < 5; ++k) sTab[r * 5 + k] = P.tab[(size_t)a * 5 + k];
+    }
+  }
+  pdl_trigger();
+  pdl_wait();
+  // every load of the lane's right-hand side and u is issued before any of them is used
+  T f0[RW], f1[RW], u0[RW], u1[RW];
+#pragma unroll
+  for (int j = 0; j < RW; ++j) {
+    const int gy = y0 + warp * RW + j;
+    const bool in = gy >= 0 && gy < n && gx >= 0 && gx < n;
+    const int64_t g = (int64_t)gy * n + gx;
+    f0[j] = f1[j] = u0[j] = u1[j] = (T)0;
+    if (in) {
+      if (finest_in) {
+        const double2 vv = __ldg((const double2*)(P.v + g));
+        f0[j] = (T)vv.x;
+        f1[j] = (T)vv.y;
+      } else {
+        const T2 ff = load_f2(P.f_in, g, P.f_bf16);
+        f0[j] = ff.x;
+        f1[j] = ff.y;
+      }
+      if (UP) {
+        const T2 uu = *(const T2*)(P.u_in + g);
+        u0[j] = uu.x;
+        u1[j] = uu.y;
+      }
+    }
+  }
+  const T vs = finest_in ? (T)(P.vscale ? *P.vscale : 1.0) : (T)1;
+  T fr[RW], fb[RW], ur[RW], ub[RW];
+#pragma unroll
+  for (int j = 0; j < RW; ++j) {
+    const int y = warp * RW + j, p = j & 1;
+    const uint8_t c0 = cc[j].x, c1 = cc[j].y;
+    T a0 = f0[j], a1 = f1[j];
+    if (finest_in) {
+      a0 = mul_rn(a0, mul_rn(vs, one_beta || (c0 & kClsPlus) ? P.inv_bp : P.inv_bm));
+      a1 = mul_rn(a1, mul_rn(vs, one_beta || (c1 & kClsPlus) ? P.inv_bp : P.inv_bm));
+    }
+    T b0 = u0[j], b1 = u1[j];
+    if (!(c0 & kClsUnknown)) a0 = b0 = 0;
+    if (!(c1 & kClsUnknown)) a1 = b1 = 0;
+    fr[j] = p ? a1 : a0;
+    fb[j] = p ? a0 : a1;
+    ur[j] = p ? b1 : b0;
+    ub[j] = p ? b0 : b1;
+    if (finest_in && in_tile(y) && y0 + y < n && gx < n) {
+      // the finest level's right-hand side, for the up step
+      T2 st;
+      st.x = a0;
+      st.y = a1;
+      *(T2*)(P.f_out + (int64_t)(y0 + y) * n + gx) = st;
     }
   }
   auto coef_of = [&](int j, int c, T* cf) {

@@ -481,10 +481,10 @@ static void launch_tail(Problem& P, size_t l0, const double* v, const double* vs
   tp.z = z;
   if (P.g.dim == 2) {
     if (smem > 48 * 1024) smem_optin((const void*)k_vcycle_tail<T, 2>);
-    IIM_LAUNCH((k_vcycle_tail<T, 2>), 1, kTailThreads, smem, s, tp);
+    IIM_LAUNCH_PDL((k_vcycle_tail<T, 2>), 1, kTailThreads, smem, s, tp);
   } else {
     if (smem > 48 * 1024) smem_optin((const void*)k_vcycle_tail<T, 3>);
-    IIM_LAUNCH((k_vcycle_tail<T, 3>), 1, kTailThreads, smem, s, tp);
+    IIM_LAUNCH_PDL((k_vcycle_tail<T, 3>), 1, kTailThreads, smem, s, tp);
   }
 }
 
@@ -557,11 +557,11 @@ static void launch_rb(Problem& P, size_t l, int mode, const double* v, const dou
   if (mode == 5) {
     constexpr size_t sm = rb_smem_bytes<T, NW, RW, false>();
     if (sm > 48 * 1024) smem_optin((const void*)k_mg2d_rb<T, NW, RW, false>);
-    IIM_LAUNCH((k_mg2d_rb<T, NW, RW, false>), grid, NW * 32, sm, s, rp);
+    IIM_LAUNCH_PDL((k_mg2d_rb<T, NW, RW, false>), grid, NW * 32, sm, s, rp);
   } else {
     constexpr size_t sm = rb_smem_bytes<T, NW, RW, true>();
     if (sm > 48 * 1024) smem_optin((const void*)k_mg2d_rb<T, NW, RW, true>);
-    IIM_LAUNCH((k_mg2d_rb<T, NW, RW, true>), grid, NW * 32, sm, s, rp);
+    IIM_LAUNCH_PDL((k_mg2d_rb<T, NW, RW, true>), grid, NW * 32, sm, s, rp);
   }
 }
 
