@@ -400,6 +400,14 @@ iim_problem* iim_server_problem(iim_server* s, int64_t id);
  * the request's stream, so the caller's data buffers are free when it returns. */
 iim_status iim_server_data_ready(iim_server* s, int64_t id);
 
+/* End a request without a solution.  A queued request leaves the queue, and one waiting for
+ * data or ready to run is freed, at once; one being created is freed when its creation ends;
+ * a running one stops at the end of the engine's current run (mode 0) or when its solve graph
+ * ends (mode 1: a graph launch is not interrupted).  The request is then reported finished
+ * by a step, and iim_server_take returns IIM_ERR_TIMEOUT for it.  IIM_ERR_INVALID_ARG for an
+ * unknown id or a request that has already ended.  Host only; does not wait. */
+iim_status iim_server_cancel(iim_server* s, int64_t id);
+
 /* Result of a finished request (x_host: n^d doubles, may be NULL), then forget
  * it.  Returns the request's final status; IIM_ERR_TIMEOUT while it is not finished. */
 iim_status iim_server_take(iim_server* s, int64_t id, double* x_host, iim_solve_info* info, double* latency_s);

@@ -115,6 +115,7 @@ SIGNATURES = {
                                        ctypes.POINTER(ctypes.c_int)]),
     "iim_server_problem": (ctypes.c_void_p, [ctypes.c_void_p, ctypes.c_int64]),
     "iim_server_data_ready": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "iim_server_cancel": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "iim_server_take": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(SolveInfo),
                                        ctypes.POINTER(ctypes.c_double)]),
     "iim_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t),
@@ -578,6 +579,11 @@ class Server:
 
     def data_ready(self, rid: int):
         _check(load().iim_server_data_ready(self.h, ctypes.c_int64(rid)), "iim_server_data_ready")
+
+    def cancel(self, rid: int):
+        """End a request without a solution (see iim_server_cancel); take() then reports
+        IIM_ERR_TIMEOUT for it."""
+        _check(load().iim_server_cancel(self.h, ctypes.c_int64(rid)), "iim_server_cancel")
 
     def take(self, rid: int):
         """(x on the host, SolveInfo, latency seconds, status) of a finished request."""

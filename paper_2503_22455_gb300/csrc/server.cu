@@ -49,6 +49,7 @@ struct Request {
   iim_problem_desc desc;
   std::vector<double> geom_coef;  // the request's own copy of a Fourier curve's coefficients
   bool reuse = false;             // takes a retired problem of the same kind from the pool
+  bool cancel = false;            // cancelled while being created or running: ends without a solution
   size_t freed_bytes = 0;         // a pooled problem the worker had to destroy (reuse failed)
   double t_submit = 0, t_done = 0;
   int state = kQueued;
@@ -220,6 +221,38 @@ static void pool_evict(Server& S, size_t need) {
   }
 }
 
+// a request that holds no running work ends now, without a solution (IIM_ERR_TIMEOUT)
+static void cancel_now(Server& S, Request* r) {
+  if (r->state == kQueued) {
+    for (auto it = S.queue.begin(); it != S.queue.end(); ++it)
+      if (*it == r) { S.queue.erase(it); break; }
+  }
+  if (r->state == kNeedData) {
+    for (auto it = S.note_need.begin(); it != S.note_need.end(); ++it)
+      if (*it == r->id) { S.note_need.erase(it); break; }
+  }
+  free_problem(S, r);
+  r->state = kFailed;
+  r->error = IIM_ERR_TIMEOUT;
+  r->info.status = IIM_ERR_TIMEOUT;
+  r->t_done = S.now();
+  S.note_fin.push_back(r->id);
+}
+
+// batched engine, no run in flight: release the cancelled slots (their solves stop here)
+static void release_cancelled(Server& S, std::vector<Request*>& retired) {
+  for (Request*& sr : S.slot_req) {
+    Request* r = sr;
+    if (!r || !r->cancel) continue;
+    iim_engine_release(S.engine, r->slot, nullptr, &r->info);
+    sr = nullptr;
+    r->slot = -1;
+    r->state = kRetired;
+    --S.resident;
+    retired.push_back(r);
+  }
+}
+
 extern "C" {
 
 iim_status iim_server_create(const iim_options* opt, size_t hbm_budget, int max_slots, int ticks_per_run,
@@ -372,10 +405,12 @@ iim_status iim_server_step(iim_server* H, int64_t* need_data, int cap_need, int*
         --S.resident;
         retired.push_back(r);
       }
+      release_cancelled(S, retired);
     } else if (st != IIM_ERR_TIMEOUT) {
       return st;
     }
   }
+  if (S.mode == 0 && !S.run_in_flight) release_cancelled(S, retired);
   // 2 (streams mode). launch the solves of ready requests while slots are free
   if (S.mode == 1) {
     for (auto& kv : S.reqs) {
@@ -425,6 +460,16 @@ iim_status iim_server_step(iim_server* H, int64_t* need_data, int cap_need, int*
   }
   // 3. solutions of the retired requests to the host (beside the new run), then free
   for (Request* r : retired) {
+    if (r->cancel) {
+      r->info.status = IIM_ERR_TIMEOUT;
+      r->info.converged = 0;
+      r->t_done = S.now();
+      r->state = kFailed;
+      r->error = IIM_ERR_TIMEOUT;
+      free_problem(S, r);
+      S.note_fin.push_back(r->id);
+      continue;
+    }
     Problem& P = r->prob->P;
     const auto tc = Clock::now();
     r->x.resize((size_t)P.g.N);
@@ -489,6 +534,9 @@ iim_status iim_server_step(iim_server* H, int64_t* need_data, int cap_need, int*
     r->state = kNeedData;
     S.note_need.push_back(r->id);
   }
+  // requests cancelled while they were being created
+  for (Request* r : got)
+    if (r->cancel && (r->state == kNeedData || r->state == kQueued)) cancel_now(S, r);
   // 5. admission by budget, in submission order: reserve and hand to the workers
   while (!S.queue.empty()) {
     Request* r = S.queue.front();
@@ -583,6 +631,28 @@ iim_status iim_server_data_ready(iim_server* H, int64_t id) {
   }
   it->second->state = kReady;
   return IIM_OK;
+}
+
+iim_status iim_server_cancel(iim_server* H, int64_t id) {
+  if (!H) return IIM_ERR_INVALID_ARG;
+  Server& S = H->S;
+  auto it = S.reqs.find(id);
+  if (it == S.reqs.end()) return IIM_ERR_INVALID_ARG;
+  Request* r = it->second;
+  switch (r->state) {
+    case kQueued:
+    case kNeedData:
+    case kReady:
+      cancel_now(S, r);
+      return IIM_OK;
+    case kCreating:
+    case kRunning:
+    case kRetired:
+      r->cancel = true;               // ends at the step that sees its creation or its solve end
+      return IIM_OK;
+    default:
+      return IIM_ERR_INVALID_ARG;     // already finished or failed
+  }
 }
 
 iim_status iim_server_take(iim_server* H, int64_t id, double* x_host, iim_solve_info* info, double* latency_s) {

@@ -141,3 +141,53 @@ def test_client_data_threads_give_the_same_results(env, mode):
     for (xa, ia, _, sa, sp), (xb, ib, _, sb, _) in zip(threaded, inline):
         assert sa == 0 and sb == 0 and ia.converged, sp.name
         assert ia.iters == ib.iters and np.array_equal(xa, xb), sp.name
+
+
+@pytest.mark.parametrize("mode", [1, 0])
+def test_cancel_in_every_state(env, mode):
+    """A request cancelled while queued, one cancelled instead of receiving its data, and a
+    larger one cancelled right after the step that starts its solve: each is reported with
+    IIM_ERR_TIMEOUT and no solution, every other request converges, nothing is left held."""
+    torch, iim = env
+    specs = [sp for _, sp in _trace()][:5]
+    big = W.star_interface_1024(512)
+    S = iim.Server(iim.default_options(), budget_bytes=1 << 36, max_slots=8, ticks_per_run=2, mode=mode)
+    ids = [S.submit(iim.desc_from_spec(sp)) for sp in specs]
+    big_id = S.submit(iim.desc_from_spec(big))
+    users = dict(zip(ids + [big_id], specs + [big]))
+    S.cancel(ids[0])                                   # queued
+    cancelled = {ids[0], ids[1], big_id}
+    out, started_big = {}, False
+    need_q, fin_q = [], []
+    import time
+    t0 = time.perf_counter()
+    while len(out) < len(users):
+        assert time.perf_counter() - t0 < 120, S.stats()
+        need, fin = S.step()
+        need_q += need
+        fin_q += fin
+        while need_q:
+            rid = need_q.pop(0)
+            if rid == ids[1]:
+                S.cancel(rid)                          # waiting for its data
+                continue
+            set_gpu_data(S.problem(rid), users[rid])
+            S.data_ready(rid)
+            if rid == big_id:
+                need, fin = S.step()                   # its solve starts (mode 1) or joins a run (mode 0)
+                need_q += need
+                fin_q += fin
+                S.cancel(big_id)                       # running
+                started_big = True
+        while fin_q:
+            rid = fin_q.pop(0)
+            out[rid] = S.take(rid)
+    st = S.stats()
+    S.close()
+    assert started_big
+    for rid, (x, info, lat, status) in out.items():
+        if rid in cancelled:
+            assert status == iim.IIM_ERR_TIMEOUT and not info.converged, users[rid].name
+        else:
+            assert status == 0 and info.converged, users[rid].name
+    assert sum(st["states"].values()) == 0 and st["bytes_in_use"] == 0
